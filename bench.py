@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of balanced / unbalanced butterfly counting on GB300.
+
+One step = one pass of the whole path over one synthetic graph already
+resident in HBM: build (validate, keep-latest dedup, degrees, Def. 3 ranks,
+sign-packed CSR, accepted-wedge work and tiers) + count (light / medium / hub
+wedge aggregation, Lemma 1 finalisation, reduction) + free. The metric is
+accepted wedges of Algorithm 1 per second (G wedges/s), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl dbbc|reference]
+
+With N > 1 (launched by torchrun) every rank counts its own replica of the
+graph (one GPU per rank, no collective on the data path; "replicas only").
+``--impl reference`` times the CPU oracle (Algorithm 1 as written, all host
+cores) on pivot samples of the same graph instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "G wedges/s and graphs/s, batched vs per-graph launches, bit-exact counts"
+UNIT = "G wedges/s"
+L2_BYTES = 129 * 2**20
+
+# Algorithmic bytes per unit of work (fixed before tuning):
+#   per accepted wedge   : 4 B CSR entry (+ 16 B u64 counter read+write in the hub tier)
+#   per lower neighbour  : 4 B entry + 16 B row offsets + 8 B end-of-row probe
+#   per touched endpoint : 4 B touched-list write in the aggregate kernel;
+#                          4 B list read + 16 B counter read/reset in the finalize kernel
+B_WEDGE, B_WEDGE_HUB, B_LOWER, B_TOUCH_AGG, B_TOUCH_FIN = 4, 20, 28, 4, 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["dbbc", "reference"], default="dbbc")
+    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the host-buffer end-to-end timing")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def expected_counts(name):
+    path = os.path.join(ROOT, "tests", "golden", "expected_counts.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split("#", 1)[0].split()
+        if len(f) == 4 and f[0] == name:
+            return tuple(int(x) for x in f[1:])
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def known_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (profiles/traffic.txt: kernel workload sha bytes)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2609_21848_gb300", "csrc", "count.cu")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    for line in open(path):
+        f = line.split("#", 1)[0].split()
+        if len(f) == 4 and f[0] == kernel and f[1] == workload and f[2] == sha:
+            return float(f[3])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def run_reference(a):
+    """The reference arm: the CPU oracle (Algorithm 1) on the host cores, each
+    step a strided pivot sample of the same graph."""
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g = synth.workload(a.workload)
+    nc = cores()
+    t0 = time.perf_counter()
+    bg = oracle.BuiltGraph(g.u, g.v, g.s, g.n_u, g.n_v)
+    build_s = time.perf_counter() - t0
+    # calibrate the stride so all warm-up + timed steps take about 2 minutes
+    per_step = 120.0 / max(1, a.steps + a.warmup)
+    probe = max(1, bg.n // 4096)
+    t0 = time.perf_counter()
+    bg.count_sample(0, probe, nc)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    step = max(1, int(probe * dt / per_step))
+    for k in range(a.warmup):
+        bg.count_sample(k % step, step, nc)
+    wedges = 0
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        wedges += bg.count_sample((a.warmup + k) % step, step, nc)[2]
+    t = time.perf_counter() - t0
+    value = wedges / t / 1e9
+    sample = (f"Algorithm 1 on every {step}-th pivot (unified id order) of {a.workload}, {nc} threads, "
+              f"graph built once untimed ({build_s:.1f} s)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": a.workload, "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nc, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(g, target_s: float) -> dict:
+    import oracle
+    nc = cores()
+    t0 = time.perf_counter()
+    bg = oracle.BuiltGraph(g.u, g.v, g.s, g.n_u, g.n_v)
+    build_s = time.perf_counter() - t0
+    probe = max(1, bg.n // 4096)
+    t0 = time.perf_counter()
+    w0 = bg.count_sample(0, probe, nc)[2]
+    dt = max(time.perf_counter() - t0, 1e-3)
+    step = max(1, int(probe * dt / target_s))
+    t0 = time.perf_counter()
+    w = bg.count_sample(1 % step, step, nc)[2]
+    t = time.perf_counter() - t0
+    bg.close()
+    del w0
+    return {"value": w / t / 1e9, "unit": UNIT, "cores": nc, "kind": "oracle",
+            "sample": f"Algorithm 1 on every {step}-th pivot of the same graph ({w} accepted wedges, {t:.1f} s, "
+                      f"{nc} threads; oracle graph build {build_s:.1f} s untimed)"}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import paper_2609_21848_gb300 as dbbc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    g = synth.workload(a.workload)
+    du, dv, ds = (torch.from_numpy(x).to(dev) for x in (g.u, g.v, g.s))
+    torch.cuda.synchronize(dev)
+
+    def step(prof_acc=None):
+        h = dbbc.dbbc_graph_from_coo(du, dv, ds, g.n_u, g.n_v, stream=stream)
+        bal, unb, prof = dbbc.dbbc_count_profiled(h, stream=stream)
+        info = h.info
+        h.free()
+        if prof_acc is not None:
+            for k, val in prof.items():
+                prof_acc[k] = prof_acc.get(k, 0) + val
+        return bal, unb, info
+
+    for _ in range(a.warmup):
+        bal, unb, info = step()
+    want = expected_counts(a.workload)
+    verified = None if want is None else ((bal, unb, info["wedges"]) == want)
+
+    # per-tier work of this graph (for the roofline bytes)
+    h = dbbc.dbbc_graph_from_coo(du, dv, ds, g.n_u, g.n_v, stream=stream)
+    ex = dbbc.dbbc_graph_export(h, stream=stream) if g.m <= 50_000_000 else None
+    info = h.info
+    h.free()
+    if ex is not None:
+        work, lower = ex["work"].astype(np.float64), ex["lower"].astype(np.float64)
+        piv = lower >= 2
+        hub = piv & (work > 4096)
+        L_hub = float(lower[hub].sum())
+    else:
+        L_hub = float("nan")
+
+    sampler = ClockSampler(local)
+    prof = {}
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = dbbc.dbbc_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step(prof)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = dbbc.dbbc_kernel_launches() - launches0
+    clocks = sampler.stop()
+    barrier()
+    t_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    t_ms = float(t_ms.item())
+    wedges = info["wedges"]
+    value = world * wedges * a.steps / (t_ms / 1e3) / 1e9
+
+    # end to end through the public API with host buffers (pinned), H2D + D2H inside
+    e2e_steps = a.e2e_steps or a.steps
+    hu, hv, hs = (torch.from_numpy(x).pin_memory() for x in (g.u, g.v, g.s))
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r = dbbc.count_coo(hu, hv, hs, g.n_u, g.n_v, stream=stream)
+    torch.cuda.synchronize(dev)
+    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = world * wedges * e2e_steps / float(t_e2e.item()) / 1e9
+    e2e_ok = r == (bal, unb)
+
+    # roofline of the dominant kernel (hub aggregation), from the live events
+    peaks, peak_kind = measured_peaks()
+    n_agg = max(1, int(prof.get("launches_hub_aggregate", 0)))
+    agg_s = prof.get("ms_hub_aggregate", 0.0) / 1e3
+    touched = prof.get("hub_touched", 0) / a.steps
+    bytes_agg_step = B_WEDGE_HUB * info["wedges_hub"] + B_LOWER * L_hub + B_TOUCH_AGG * touched
+    per_launch_bytes = bytes_agg_step * a.steps / n_agg
+    per_launch_s = agg_s / n_agg
+    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
+    peak = float(peaks["hbm_gbs"])
+    roofline = {"bound": "hbm", "kernel": "hub_aggregate_kernel", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": known_traffic("hub_aggregate_kernel", a.workload),
+                "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
+                f"of {peak_kind}",
+                "bytes_per_launch": per_launch_bytes, "launches_per_step": n_agg / a.steps,
+                "ms_per_launch": 1e3 * per_launch_s}
+    tiers_ms = {k: prof.get(k, 0.0) / a.steps for k in ("ms_light", "ms_medium", "ms_hub_aggregate",
+                                                         "ms_hub_finalize", "ms_total")}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": a.workload, "n_u": g.n_u, "n_v": g.n_v, "edges": g.m,
+                       "wedges_per_step": wedges, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (COO %.0f MB, CSR %.0f MB > 129 MB)" % (
+                           g.m * 9 / 1e6, (2 * g.m * 4 + (g.n_u + g.n_v) * 8) / 1e6)},
+            "verified": verified, "counts": {"balanced": bal, "unbalanced": unb},
+            "count_ms_per_step": tiers_ms,
+            "count_only_gwedges_per_s": wedges / (tiers_ms["ms_total"] / 1e3) / 1e9 if tiers_ms["ms_total"] else None,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 9 * g.m, "d2h_bytes_per_step": 16,
+                    "steps": e2e_steps, "bit_exact": e2e_ok},
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * dbbc.h -- balanced / unbalanced butterfly counting in signed bipartite graphs
+ * on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Problem (Section III, "Problem Statement"; Def. 1 and Def. 2): a signed
+ * bipartite graph G = (U, V, E = E+ u E-) has a butterfly for every
+ * {u, u'} in U and {v, v'} in V whose four edges all exist. The butterfly is
+ * balanced when the number of negative edges among the four is even and
+ * unbalanced when it is odd. This library returns both totals as exact 64-bit
+ * integers.
+ *
+ * Method (Section IV-A, Algorithm 1, Phase 5; Lemma 1): vertices are ordered by
+ * the Def. 3 priority (degree, then id, over U u V with unified ids
+ * id(u) = u, id(v) = |U| + v). Every wedge u-v-w with p(v) < p(u) and
+ * p(w) < p(u) adds one to a symmetric counter of w when s(u,v) = s(v,w) and to
+ * an asymmetric counter otherwise; each (u, w) then contributes
+ * C(sym,2) + C(asym,2) balanced and sym * asym unbalanced butterflies.
+ *
+ * Conventions shared by every entry point:
+ *   - Vertex ids are per side: 0 <= u < n_u and 0 <= v < n_v, int32.
+ *   - Signs are int8, +1 (positive) or -1 (negative). The paper writes a
+ *     negative edge as sign 0 (Def. 2); here -1 is used instead.
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Work is ordered on that stream.
+ *   - The library copies its inputs; the caller keeps ownership of every
+ *     array it passes. A graph handle is owned by the caller until
+ *     dbbc_graph_free.
+ *   - On error, output parameters are left untouched and a status other than
+ *     DBBC_OK is returned. No C++ exception crosses this interface.
+ *   - Device memory is taken from the allocator set with dbbc_set_allocator,
+ *     else from cudaMallocAsync on the call's stream.
+ *   - A handle may be read by several counts at once (each count allocates its
+ *     own scratch); it must not be freed while a count on it is in flight.
+ */
+#ifndef DBBC_H
+#define DBBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__) || defined(__clang__)
+#define DBBC_API __attribute__((visibility("default")))
+#else
+#define DBBC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dbbc_graph dbbc_graph; /* opaque: device CSR, buckets, hub plan */
+
+typedef enum {
+  DBBC_OK = 0,
+  DBBC_EINVAL = 1,    /* bad argument or input (id out of range, sign not +-1, m < 0, duplicate under DUP_REJECT) */
+  DBBC_ENOMEM = 2,    /* a device allocation failed */
+  DBBC_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  DBBC_ETIMEOUT = 4,  /* a bounded device wait gave up (status word set by a kernel) */
+  DBBC_EOVERFLOW = 5, /* a count or an internal capacity exceeded its type */
+  DBBC_EINTERNAL = 6  /* an internal consistency check failed (a bug: please report) */
+} dbbc_status;
+
+enum {
+  DBBC_INPUT_HOST = 0,   /* u, v, sign are host pointers (pageable or pinned) */
+  DBBC_INPUT_DEVICE = 1, /* u, v, sign are device pointers */
+  DBBC_DUP_KEEP_LAST = 0, /* repeated (u, v) pairs keep the sign of the last occurrence (Section V) */
+  DBBC_DUP_REJECT = 2     /* repeated (u, v) pairs make the call fail with DBBC_EINVAL */
+};
+
+/* Build a graph from COO arrays (Def. 1 input; duplicates per Section V,
+ * dataset preprocessing: the latest occurrence of a pair wins).
+ *   u, v, sign : m entries each, host or device memory per `flags`.
+ *   m          : number of input edges, 0 <= m < 2^31.
+ *   n_u, n_v   : side sizes, 0 <= n_u, n_v and n_u + n_v < 2^31.
+ *   flags      : DBBC_INPUT_* | DBBC_DUP_*.
+ *   out        : receives a new handle on success.
+ * Synchronous with respect to `cuda_stream` (it reads sizes back to the host).
+ * Errors: DBBC_EINVAL (any id out of range, any sign not +-1, bad sizes or
+ * flags, duplicates under DBBC_DUP_REJECT), DBBC_ENOMEM, DBBC_ECUDA. */
+DBBC_API dbbc_status dbbc_graph_from_coo(const int32_t* u, const int32_t* v, const int8_t* sign, int64_t m, int32_t n_u,
+                                int32_t n_v, uint32_t flags, void* cuda_stream, dbbc_graph** out);
+
+/* Count balanced and unbalanced butterflies of one graph (Algorithm 1,
+ * Phase 5, with the Lemma 1 unbalanced count). Host out-parameters; the call
+ * returns after the counts are on the host. Either pointer may be NULL. */
+DBBC_API dbbc_status dbbc_count(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced, uint64_t* unbalanced);
+
+/* Same as dbbc_count but asynchronous: writes {balanced, unbalanced} to the
+ * DEVICE array d_out[2] in stream order and returns after enqueueing. */
+DBBC_API dbbc_status dbbc_count_async(const dbbc_graph* g, void* cuda_stream, uint64_t* d_out);
+
+/* Per-tier timings of one count, measured with CUDA events on the call's
+ * stream around the tier's kernels (milliseconds), with launch counts and the
+ * number of endpoints the hub tier touched (each read and reset once). */
+typedef struct {
+  float ms_light, ms_medium, ms_hub_aggregate, ms_hub_finalize, ms_total;
+  int64_t launches_light, launches_medium, launches_hub_aggregate, launches_hub_finalize;
+  uint64_t hub_touched;
+} dbbc_count_profile;
+
+/* dbbc_count plus per-tier timings in *prof (may be NULL). Synchronous. */
+DBBC_API dbbc_status dbbc_count_profiled(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced,
+                                         uint64_t* unbalanced, dbbc_count_profile* prof);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (graph builds and counts). */
+DBBC_API uint64_t dbbc_kernel_launches(void);
+
+/* Count several resident graphs in one launch sequence. balanced[i] and
+ * unbalanced[i] (host arrays of n_graphs entries) receive graph i's counts.
+ * Synchronous. */
+DBBC_API dbbc_status dbbc_count_batch(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream, uint64_t* balanced,
+                             uint64_t* unbalanced);
+
+/* Asynchronous batch: d_out is a DEVICE array [n_graphs][2] of
+ * {balanced, unbalanced}. Returns after enqueueing. */
+DBBC_API dbbc_status dbbc_count_batch_async(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream,
+                                   uint64_t* d_out);
+
+typedef struct {
+  int32_t n_u, n_v;
+  int64_t m_input;     /* edges passed in */
+  int64_t m;           /* distinct edges kept */
+  uint64_t wedges;     /* accepted wedges of Algorithm 1 (sum over all pivots) */
+  int64_t n_pivots;    /* pivots with at least two lower neighbours and one accepted wedge */
+  int64_t n_light, n_medium, n_hub; /* pivots per counting tier */
+  uint64_t wedges_light, wedges_medium, wedges_hub;
+  size_t device_bytes; /* device memory held by the handle */
+} dbbc_graph_info;
+
+/* Sizes and the per-tier wedge split of a built graph. */
+DBBC_API dbbc_status dbbc_graph_get_info(const dbbc_graph* g, dbbc_graph_info* info);
+
+/* Device bytes held by a handle (for admission control). 0 for NULL. */
+DBBC_API size_t dbbc_graph_device_bytes(const dbbc_graph* g);
+
+/* Upper estimate of the peak device bytes dbbc_graph_from_coo needs for a
+ * graph of this size (handle plus build scratch). */
+DBBC_API size_t dbbc_estimate_bytes(int64_t m, int32_t n_u, int32_t n_v);
+
+/* Release a handle (NULL is a no-op). Frees in stream order on the stream the
+ * handle was built on. */
+DBBC_API void dbbc_graph_free(dbbc_graph* g);
+
+/* Export the device CSR for inspection (tests and tools). All arrays are HOST
+ * buffers sized by the caller from dbbc_graph_get_info:
+ *   row_ptr[n_u + n_v + 1] (int64), col[2m] (uint32 (side_rank << 1) | negative),
+ *   lower[n_u + n_v] (uint32, lower-priority neighbours per row),
+ *   vertex[n_u + n_v] (int32 unified id of each row), work[n_u + n_v]
+ *   (uint64 accepted wedges with that row as pivot).
+ * Rows 0..n_u-1 are U vertices in ascending Def. 3 priority, rows n_u..n-1
+ * are V vertices in ascending priority; any pointer may be NULL. */
+DBBC_API dbbc_status dbbc_graph_export(const dbbc_graph* g, void* cuda_stream, int64_t* row_ptr, uint32_t* col,
+                              uint32_t* lower, int32_t* vertex, uint64_t* work);
+
+/* Device allocator hook (e.g. a framework's caching allocator). alloc returns
+ * NULL on failure. Passing NULL for both restores cudaMallocAsync/cudaFreeAsync.
+ * Not thread-safe against concurrent library calls. */
+DBBC_API void dbbc_set_allocator(void* (*alloc_fn)(size_t bytes, void* cuda_stream, void* ctx),
+                        void (*free_fn)(void* ptr, void* cuda_stream, void* ctx), void* ctx);
+
+/* Static description of a status code. */
+DBBC_API const char* dbbc_status_string(dbbc_status s);
+
+/* Library version as "major.minor.patch". */
+DBBC_API const char* dbbc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBBC_H */

@@ -66,6 +66,12 @@ def _load():
         lib.oracle_brute_force.argtypes = graph_args + [P, P]
         lib.oracle_workload_eq1.argtypes = graph_args + [P]
         lib.oracle_lpt.argtypes = [P, ctypes.c_int64, ctypes.c_int32, P, P]
+        lib.oracle_graph_new.argtypes = graph_args + [ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_graph_new.restype = P
+        lib.oracle_graph_count_sample.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, P, P, P]
+        lib.oracle_graph_count_sample.restype = ctypes.c_int
+        lib.oracle_graph_free.argtypes = [P]
+        lib.oracle_graph_free.restype = None
         for f in (lib.oracle_count, lib.oracle_count_per_pivot, lib.oracle_brute_force, lib.oracle_workload_eq1,
                   lib.oracle_lpt):
             f.restype = ctypes.c_int
@@ -113,6 +119,36 @@ def count_per_pivot(u, v, s, n_u: int, n_v: int, threads: int = 1):
                                         threads, b.ctypes.data, ub.ctypes.data, w.ctypes.data)
     _check(rc)
     return b, ub, w
+
+
+class BuiltGraph:
+    """A graph built once by the oracle and counted on pivot samples (for
+    timing Algorithm 1 alone). Pivots are unified ids first, first+step, ..."""
+
+    def __init__(self, u, v, s, n_u: int, n_v: int):
+        u, v, s = _coo(u, v, s)
+        st = ctypes.c_int(0)
+        self._h = _load().oracle_graph_new(u.ctypes.data, v.ctypes.data, s.ctypes.data, u.shape[0], n_u, n_v,
+                                           ctypes.byref(st))
+        _check(st.value)
+        self.n = n_u + n_v
+
+    def count_sample(self, first: int = 0, step: int = 1, threads: int = 1) -> tuple[int, int, int]:
+        out = (ctypes.c_uint64 * 3)()
+        base = ctypes.addressof(out)
+        _check(_load().oracle_graph_count_sample(self._h, first, step, threads, base, base + 8, base + 16))
+        return int(out[0]), int(out[1]), int(out[2])
+
+    def close(self):
+        if self._h:
+            _load().oracle_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def brute_force(u, v, s, n_u: int, n_v: int) -> tuple[int, int]:

@@ -87,19 +87,28 @@ struct Totals {
   u128 balanced = 0, unbalanced = 0, wedges = 0;
 };
 
-// Algorithm 1, Phase 5, for pivots taken from `next` until exhausted.
-// Optional per-pivot outputs are indexed by unified id.
-void count_pivots(const SignedGraph& g, std::atomic<int64_t>* next, int64_t chunk, Totals* out,
+// Pivots visited by one run: first, first + step, first + 2*step, ... below n.
+struct PivotSample {
+  int64_t first = 0, step = 1;
+  int64_t count(int64_t n) const { return first >= n ? 0 : (n - first + step - 1) / step; }
+};
+
+// Algorithm 1, Phase 5, for the sample's pivots taken from `next` (an index
+// into the sample) until exhausted. Optional per-pivot outputs are indexed by
+// unified id.
+void count_pivots(const SignedGraph& g, PivotSample ps, std::atomic<int64_t>* next, int64_t chunk, Totals* out,
                   uint64_t* bal_pp, uint64_t* unb_pp, uint64_t* wed_pp) {
   std::vector<uint32_t> B1(static_cast<size_t>(g.n), 0), B2(static_cast<size_t>(g.n), 0);
   std::vector<int32_t> touched;
   std::vector<uint8_t> seen(static_cast<size_t>(g.n), 0);
   Totals t;
+  const int64_t total = ps.count(g.n);
   for (;;) {
     int64_t begin = next->fetch_add(chunk);
-    if (begin >= g.n) break;
-    int64_t end = std::min(begin + chunk, g.n);
-    for (int64_t u = begin; u < end; u++) {
+    if (begin >= total) break;
+    int64_t end = std::min(begin + chunk, total);
+    for (int64_t k = begin; k < end; k++) {
+      const int64_t u = ps.first + k * ps.step;
       for (const auto& uv : g.adj[u]) {
         int32_t v = uv.first;
         if (!lower_priority(g, v, u)) continue;
@@ -131,21 +140,17 @@ void count_pivots(const SignedGraph& g, std::atomic<int64_t>* next, int64_t chun
   *out = t;
 }
 
-int run_algorithm1(const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, int32_t n_u, int32_t n_v,
-                   int threads, uint64_t* balanced, uint64_t* unbalanced, uint64_t* wedges, uint64_t* bal_pp,
-                   uint64_t* unb_pp, uint64_t* wed_pp) {
-  SignedGraph g;
-  int rc = build_graph(u, v, s, m, n_u, n_v, g);
-  if (rc != OK) return rc;
+int count_graph(const SignedGraph& g, PivotSample ps, int threads, uint64_t* balanced, uint64_t* unbalanced,
+                uint64_t* wedges, uint64_t* bal_pp, uint64_t* unb_pp, uint64_t* wed_pp) {
   if (threads < 1) threads = 1;
   std::atomic<int64_t> next{0};
   std::vector<Totals> part(static_cast<size_t>(threads));
   if (threads == 1) {
-    count_pivots(g, &next, g.n > 0 ? g.n : 1, &part[0], bal_pp, unb_pp, wed_pp);
+    count_pivots(g, ps, &next, std::max<int64_t>(ps.count(g.n), 1), &part[0], bal_pp, unb_pp, wed_pp);
   } else {
     std::vector<std::thread> pool;
     for (int t = 0; t < threads; t++)
-      pool.emplace_back(count_pivots, std::cref(g), &next, int64_t{64}, &part[t], bal_pp, unb_pp, wed_pp);
+      pool.emplace_back(count_pivots, std::cref(g), ps, &next, int64_t{64}, &part[t], bal_pp, unb_pp, wed_pp);
     for (auto& th : pool) th.join();
   }
   Totals tot;
@@ -160,6 +165,15 @@ int run_algorithm1(const int32_t* u, const int32_t* v, const int8_t* s, int64_t 
   if (unbalanced) *unbalanced = static_cast<uint64_t>(tot.unbalanced);
   if (wedges) *wedges = static_cast<uint64_t>(tot.wedges);
   return OK;
+}
+
+int run_algorithm1(const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, int32_t n_u, int32_t n_v,
+                   int threads, uint64_t* balanced, uint64_t* unbalanced, uint64_t* wedges, uint64_t* bal_pp,
+                   uint64_t* unb_pp, uint64_t* wed_pp) {
+  SignedGraph g;
+  int rc = build_graph(u, v, s, m, n_u, n_v, g);
+  if (rc != OK) return rc;
+  return count_graph(g, PivotSample{}, threads, balanced, unbalanced, wedges, bal_pp, unb_pp, wed_pp);
 }
 
 }  // namespace
@@ -182,6 +196,33 @@ int oracle_count_per_pivot(const int32_t* u, const int32_t* v, const int8_t* s, 
   uint64_t b, ub, w;
   return run_algorithm1(u, v, s, m, n_u, n_v, threads, &b, &ub, &w, bal_pp, unb_pp, wed_pp);
 }
+
+// A graph built once (validation, keep-latest dedup, adjacency) and counted
+// many times, so that Algorithm 1 can be timed alone on pivot samples.
+void* oracle_graph_new(const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, int32_t n_u, int32_t n_v,
+                       int* status) {
+  SignedGraph* g = new SignedGraph();
+  int rc = build_graph(u, v, s, m, n_u, n_v, *g);
+  if (status) *status = rc;
+  if (rc != OK) {
+    delete g;
+    return nullptr;
+  }
+  return g;
+}
+
+// Algorithm 1 over the pivots first, first + step, ... of a built graph.
+int oracle_graph_count_sample(const void* h, int64_t first, int64_t step, int threads, uint64_t* balanced,
+                              uint64_t* unbalanced, uint64_t* wedges) {
+  if (!h || first < 0 || step < 1) return BAD_INPUT;
+  PivotSample ps;
+  ps.first = first;
+  ps.step = step;
+  return count_graph(*static_cast<const SignedGraph*>(h), ps, threads, balanced, unbalanced, wedges, nullptr, nullptr,
+                     nullptr);
+}
+
+void oracle_graph_free(void* h) { delete static_cast<SignedGraph*>(h); }
 
 // Def. 1-2 enumerated directly: a dense |U| x |V| sign matrix (later edges
 // overwrite earlier ones), every pair u1 < u2 and every pair v1 < v2, parity of

@@ -1,0 +1,281 @@
+// C ABI of the dbbc library (see include/dbbc.h for the contract of every
+// entry point). Each entry point converts internal errors into a status; no
+// C++ exception crosses the interface.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+
+#include "internal.h"
+#include "common.cuh"
+
+namespace dbbc {
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+void* (*g_alloc_fn)(size_t, void*, void*) = nullptr;
+void (*g_free_fn)(void*, void*, void*) = nullptr;
+void* g_alloc_ctx = nullptr;
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+  if (g_alloc_fn) return g_alloc_fn(bytes, (void*)s, g_alloc_ctx);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (!p) return;
+  if (g_free_fn) {
+    g_free_fn(p, (void*)s, g_alloc_ctx);
+    return;
+  }
+  if (cudaFreeAsync(p, s) != cudaSuccess) (void)cudaGetLastError();
+}
+
+template <typename F>
+static dbbc_status guarded(F&& f) {
+  try {
+    f();
+    return DBBC_OK;
+  } catch (const Error& e) {
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    return DBBC_ENOMEM;
+  } catch (...) {
+    return DBBC_EINTERNAL;
+  }
+}
+
+static void check_status_word(const unsigned* d_status, cudaStream_t s) {
+  unsigned h = 0;
+  DBBC_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  DBBC_CUDA(cudaStreamSynchronize(s));
+  if (h & DBBC_DEV_HASH_FULL) throw Error{DBBC_EINTERNAL, "shared hash table overflow"};
+  if (h) throw Error{DBBC_EINTERNAL, "device status"};
+}
+
+}  // namespace dbbc
+
+using namespace dbbc;
+
+extern "C" {
+
+const char* dbbc_version(void) { return "0.1.0"; }
+
+const char* dbbc_status_string(dbbc_status s) {
+  switch (s) {
+    case DBBC_OK: return "ok";
+    case DBBC_EINVAL: return "invalid argument or input graph";
+    case DBBC_ENOMEM: return "device allocation failed";
+    case DBBC_ECUDA: return "CUDA runtime error";
+    case DBBC_ETIMEOUT: return "bounded device wait gave up";
+    case DBBC_EOVERFLOW: return "count or capacity overflow";
+    case DBBC_EINTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+void dbbc_set_allocator(void* (*alloc_fn)(size_t, void*, void*), void (*free_fn)(void*, void*, void*), void* ctx) {
+  if (alloc_fn && free_fn) {
+    g_alloc_fn = alloc_fn;
+    g_free_fn = free_fn;
+    g_alloc_ctx = ctx;
+  } else {
+    g_alloc_fn = nullptr;
+    g_free_fn = nullptr;
+    g_alloc_ctx = nullptr;
+  }
+}
+
+dbbc_status dbbc_graph_from_coo(const int32_t* u, const int32_t* v, const int8_t* sign, int64_t m, int32_t n_u,
+                                int32_t n_v, uint32_t flags, void* cuda_stream, dbbc_graph** out) {
+  if (!out || m < 0 || m >= (int64_t{1} << 31) || n_u < 0 || n_v < 0 ||
+      (int64_t)n_u + (int64_t)n_v >= (int64_t{1} << 31) || (flags & ~3u) != 0)
+    return DBBC_EINVAL;
+  if (m > 0 && (!u || !v || !sign)) return DBBC_EINVAL;
+  dbbc_graph* g = nullptr;
+  try {
+    g = new dbbc_graph();
+  } catch (...) {
+    return DBBC_ENOMEM;
+  }
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  g->n_u = n_u;
+  g->n_v = n_v;
+  const dbbc_status st = guarded([&] {
+    DBBC_CUDA(cudaGetDevice(&g->device));
+    build_graph(g, u, v, sign, m, (flags & DBBC_INPUT_DEVICE) != 0, (flags & DBBC_DUP_REJECT) != 0, g->stream);
+  });
+  if (st != DBBC_OK) {
+    free_graph_memory(g);
+    (void)cudaStreamSynchronize(g->stream);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return DBBC_OK;
+}
+
+void dbbc_graph_free(dbbc_graph* g) {
+  if (!g) return;
+  free_graph_memory(g);
+  delete g;
+}
+
+size_t dbbc_graph_device_bytes(const dbbc_graph* g) { return g ? g->device_bytes : 0; }
+
+size_t dbbc_estimate_bytes(int64_t m, int32_t n_u, int32_t n_v) {
+  if (m < 0 || n_u < 0 || n_v < 0) return 0;
+  const size_t n = (size_t)n_u + (size_t)n_v, mm = (size_t)m;
+  // handle: row_ptr 8(n+1), col 8m, lower/vertex 8n, work 8n, order 4n, items
+  const size_t handle = 8 * (n + 1) + 8 * mm + 8 * n + 8 * n + 4 * n + 16 * (mm / 64 + 16);
+  // build peak: inputs 9m, dedup 24m + flags/pos 8m, edges 9m, CSR keys 32m, vertex keys 16n + 16n
+  const size_t build = 9 * mm + 32 * mm + 9 * mm + 32 * mm + 48 * n + (mm / 4096 + 1) * 1024;
+  return handle + build;
+}
+
+dbbc_status dbbc_graph_get_info(const dbbc_graph* g, dbbc_graph_info* info) {
+  if (!g || !info) return DBBC_EINVAL;
+  dbbc_graph_info r;
+  std::memset(&r, 0, sizeof(r));
+  r.n_u = g->n_u;
+  r.n_v = g->n_v;
+  r.m_input = g->m_input;
+  r.m = g->m;
+  r.wedges = g->wedges;
+  r.n_pivots = g->n_piv;
+  r.n_light = g->n_light;
+  r.n_medium = g->n_medium;
+  r.n_hub = g->n_hub;
+  r.wedges_light = g->wedges_light;
+  r.wedges_medium = g->wedges_medium;
+  r.wedges_hub = g->wedges_hub;
+  r.device_bytes = g->device_bytes;
+  *info = r;
+  return DBBC_OK;
+}
+
+dbbc_status dbbc_count_async(const dbbc_graph* g, void* cuda_stream, uint64_t* d_out) {
+  if (!g || !d_out) return DBBC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  return guarded([&] {
+    Scratch sc(s);
+    unsigned* d_status = sc.get<unsigned>(1);
+    DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
+    DBBC_CUDA(cudaMemsetAsync(d_out, 0, 2 * sizeof(uint64_t), s));
+    enqueue_count(g, s, reinterpret_cast<unsigned long long*>(d_out), d_status, sc);
+  });
+}
+
+dbbc_status dbbc_count(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced, uint64_t* unbalanced) {
+  if (!g) return DBBC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  uint64_t h[2] = {0, 0};
+  const dbbc_status st = guarded([&] {
+    Scratch sc(s);
+    unsigned long long* d_out = sc.get<unsigned long long>(2);
+    unsigned* d_status = sc.get<unsigned>(1);
+    DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
+    DBBC_CUDA(cudaMemsetAsync(d_out, 0, 2 * sizeof(uint64_t), s));
+    enqueue_count(g, s, d_out, d_status, sc);
+    DBBC_CUDA(cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    check_status_word(d_status, s);  // synchronizes
+  });
+  if (st != DBBC_OK) return st;
+  if (balanced) *balanced = h[0];
+  if (unbalanced) *unbalanced = h[1];
+  return DBBC_OK;
+}
+
+dbbc_status dbbc_count_profiled(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced, uint64_t* unbalanced,
+                                dbbc_count_profile* prof) {
+  if (!g) return DBBC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  uint64_t h[2] = {0, 0};
+  dbbc_count_profile p;
+  std::memset(&p, 0, sizeof(p));
+  const dbbc_status st = guarded([&] {
+    Scratch sc(s);
+    CountProfiler cp;
+    unsigned long long* d_out = sc.get<unsigned long long>(2);
+    unsigned* d_status = sc.get<unsigned>(1);
+    DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
+    DBBC_CUDA(cudaMemsetAsync(d_out, 0, 2 * sizeof(uint64_t), s));
+    enqueue_count(g, s, d_out, d_status, sc, &cp);
+    DBBC_CUDA(cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    check_status_word(d_status, s);  // synchronizes
+    cp.summarize(&p);
+  });
+  if (st != DBBC_OK) return st;
+  if (balanced) *balanced = h[0];
+  if (unbalanced) *unbalanced = h[1];
+  if (prof) *prof = p;
+  return DBBC_OK;
+}
+
+uint64_t dbbc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+dbbc_status dbbc_count_batch_async(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream,
+                                   uint64_t* d_out) {
+  if (n_graphs < 0 || (n_graphs > 0 && (!gs || !d_out))) return DBBC_EINVAL;
+  for (int32_t i = 0; i < n_graphs; i++)
+    if (!gs[i]) return DBBC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  return guarded([&] {
+    if (n_graphs == 0) return;
+    Scratch sc(s);
+    unsigned* d_status = sc.get<unsigned>(1);
+    DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
+    DBBC_CUDA(cudaMemsetAsync(d_out, 0, (size_t)n_graphs * 2 * sizeof(uint64_t), s));
+    for (int32_t i = 0; i < n_graphs; i++)
+      enqueue_count(gs[i], s, reinterpret_cast<unsigned long long*>(d_out) + 2 * i, d_status, sc);
+  });
+}
+
+dbbc_status dbbc_count_batch(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream, uint64_t* balanced,
+                             uint64_t* unbalanced) {
+  if (n_graphs < 0 || (n_graphs > 0 && (!gs || !balanced || !unbalanced))) return DBBC_EINVAL;
+  for (int32_t i = 0; i < n_graphs; i++)
+    if (!gs[i]) return DBBC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<uint64_t> h((size_t)n_graphs * 2);
+  const dbbc_status st = guarded([&] {
+    if (n_graphs == 0) return;
+    Scratch sc(s);
+    unsigned long long* d_out = sc.get<unsigned long long>((size_t)n_graphs * 2);
+    unsigned* d_status = sc.get<unsigned>(1);
+    DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
+    DBBC_CUDA(cudaMemsetAsync(d_out, 0, (size_t)n_graphs * 2 * sizeof(uint64_t), s));
+    for (int32_t i = 0; i < n_graphs; i++) enqueue_count(gs[i], s, d_out + 2 * i, d_status, sc);
+    DBBC_CUDA(cudaMemcpyAsync(h.data(), d_out, h.size() * 8, cudaMemcpyDeviceToHost, s));
+    check_status_word(d_status, s);
+  });
+  if (st != DBBC_OK) return st;
+  for (int32_t i = 0; i < n_graphs; i++) {
+    balanced[i] = h[2 * (size_t)i];
+    unbalanced[i] = h[2 * (size_t)i + 1];
+  }
+  return DBBC_OK;
+}
+
+dbbc_status dbbc_graph_export(const dbbc_graph* g, void* cuda_stream, int64_t* row_ptr, uint32_t* col,
+                              uint32_t* lower, int32_t* vertex, uint64_t* work) {
+  if (!g) return DBBC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  return guarded([&] {
+    if (row_ptr) DBBC_CUDA(cudaMemcpyAsync(row_ptr, g->row_ptr, (size_t)(g->n + 1) * 8, cudaMemcpyDeviceToHost, s));
+    if (col && g->nnz) DBBC_CUDA(cudaMemcpyAsync(col, g->col, (size_t)g->nnz * 4, cudaMemcpyDeviceToHost, s));
+    if (lower && g->n) DBBC_CUDA(cudaMemcpyAsync(lower, g->lower, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+    if (vertex && g->n) DBBC_CUDA(cudaMemcpyAsync(vertex, g->vertex, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+    if (work && g->n) DBBC_CUDA(cudaMemcpyAsync(work, g->work, (size_t)g->n * 8, cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+}  // extern "C"

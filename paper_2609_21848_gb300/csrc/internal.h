@@ -1,0 +1,111 @@
+// Internal layout of a built graph and the launch entry points shared by the
+// library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/dbbc.h"
+#include "common.cuh"
+
+namespace dbbc {
+
+// Counting tiers by accepted wedges W(p) of a pivot.
+constexpr uint64_t kLightMaxWork = 512;    // warp per pivot, per-warp shared hash (<= 1024 slots)
+constexpr uint64_t kMediumMaxWork = 4096;  // CTA per pivot, shared hash (<= 8192 slots)
+constexpr int kLightSlots = 1024;
+constexpr int kMediumSlots = 8192;
+constexpr int kMaxHubSlots = 32;           // hubs counted concurrently (one dense counter array each)
+constexpr size_t kHubSlotBudget = size_t(2) << 30;  // bytes of dense counters + touched lists per count
+constexpr uint64_t kHubChunkWork = 1u << 15;        // target accepted wedges per hub work item
+
+// One unit of hub work: lower-neighbour positions [a, b) of hub row `row`,
+// accumulated into dense counter array `slot`.
+struct HubItem {
+  int32_t slot;
+  int32_t row;
+  uint32_t a;
+  uint32_t b;
+};
+
+// Read-only view of the device CSR passed to kernels by value.
+// Rows [0, n_u) are U vertices in ascending Def. 3 priority, rows [n_u, n)
+// V vertices in ascending priority. A row lists its neighbours by ascending
+// priority as (side_rank << 1) | negative; the first lower[r] of them have
+// lower priority than the row's vertex.
+struct CsrView {
+  const int64_t* row_ptr;
+  const uint32_t* col;
+  const uint32_t* lower;
+  int32_t n_u;
+  int64_t n;
+};
+
+}  // namespace dbbc
+
+// Status bits written by kernels (device status word).
+enum : unsigned {
+  DBBC_DEV_HASH_FULL = 1u,  // a shared hash table ran out of slots (tier sizing bug)
+  DBBC_DEV_RANGE = 2u,      // an index left its array (checked paths only)
+};
+
+struct dbbc_graph {
+  int device = 0;
+  cudaStream_t stream = nullptr;  // stream the handle was built on (frees are ordered on it)
+  int32_t n_u = 0, n_v = 0;
+  int64_t n = 0;        // rows = n_u + n_v
+  int64_t m_input = 0;  // edges passed in
+  int64_t m = 0;        // distinct edges
+  int64_t nnz = 0;      // 2m
+  int64_t* row_ptr = nullptr;  // [n + 1]
+  uint32_t* col = nullptr;     // [nnz]
+  uint32_t* lower = nullptr;   // [n]
+  int32_t* vertex = nullptr;   // [n] unified id per row
+  uint64_t* work = nullptr;    // [n] accepted wedges per pivot row
+  int32_t* order = nullptr;    // [n_piv] pivot rows, descending work: hubs | medium | light
+  int64_t n_piv = 0, n_hub = 0, n_medium = 0, n_light = 0;
+  uint64_t wedges = 0, wedges_hub = 0, wedges_medium = 0, wedges_light = 0;
+  // hub plan: waves of up to `hub_slots` hubs; items of wave w are
+  // hub_items[hub_wave_begin[w] .. hub_wave_begin[w+1])
+  int32_t hub_slots = 0;
+  int64_t hub_stride = 0;  // counters per slot (largest side)
+  dbbc::HubItem* hub_items = nullptr;
+  std::vector<int64_t> hub_wave_begin;
+  size_t device_bytes = 0;
+  std::vector<void*> allocations;
+};
+
+namespace dbbc {
+
+// prep.cu
+void build_graph(dbbc_graph* g, const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, bool on_device,
+                 bool reject_duplicates, cudaStream_t stream);
+void free_graph_memory(dbbc_graph* g);
+void* graph_alloc(dbbc_graph* g, size_t bytes);
+
+// Event brackets around tiers of one count (profiled counts only).
+struct CountProfiler {
+  enum Tier { LIGHT = 0, MEDIUM = 1, HUB_AGG = 2, HUB_FIN = 3, TOTAL = 4, NTIERS = 5 };
+  struct Mark {
+    int tier;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<uint32_t> hub_touched;  // filled asynchronously
+  int64_t launches[NTIERS] = {0, 0, 0, 0, 0};
+  cudaEvent_t begin(cudaStream_t s);
+  void end(int tier, cudaEvent_t a, cudaStream_t s);
+  // after the stream has been synchronized
+  void summarize(dbbc_count_profile* out);
+  ~CountProfiler();
+};
+
+// count.cu: enqueue the counting kernels of one graph, accumulating
+// {balanced, unbalanced} into d_out[0..1] (device, must be zeroed by caller).
+void enqueue_count(const dbbc_graph* g, cudaStream_t stream, unsigned long long* d_out, unsigned* d_status,
+                   Scratch& scratch, CountProfiler* prof = nullptr);
+
+}  // namespace dbbc

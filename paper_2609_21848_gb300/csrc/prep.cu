@@ -1,0 +1,512 @@
+// Graph build on the device: validate, keep-latest deduplication, degrees,
+// Def. 3 priority ranks, sign-packed CSR sorted by priority, accepted-wedge
+// work per pivot (Algorithm 1's inner loop bounds), and the counting tiers.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+#include "radix.cuh"
+
+namespace dbbc {
+
+// ------------------------------------------------------------------ kernels
+__global__ void validate_kernel(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                const int8_t* __restrict__ s, int64_t m, int32_t n_u, int32_t n_v, unsigned* err) {
+  unsigned e = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = u[i], b = v[i];
+    const int8_t c = s[i];
+    if (a < 0 || a >= n_u) e |= 1u;
+    if (b < 0 || b >= n_v) e |= 2u;
+    if (c != 1 && c != -1) e |= 4u;
+  }
+  e = __reduce_or_sync(kFullMask, e);
+  if (lane_id() == 0 && e) atomicOr(err, e);
+}
+
+__global__ void edge_keys_kernel(const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t m, int bits_v,
+                                 uint64_t* __restrict__ key, uint32_t* __restrict__ idx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    key[i] = ((uint64_t)(uint32_t)u[i] << bits_v) | (uint32_t)v[i];
+    idx[i] = (uint32_t)i;
+  }
+}
+
+// flag[i] = 1 iff i is the last occurrence of its key (keys sorted stably, so
+// the last of a run is the latest input occurrence).
+__global__ void run_last_kernel(const uint64_t* __restrict__ key, int64_t m, uint32_t* __restrict__ flag,
+                                unsigned* dup) {
+  bool any_dup = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool last = (i == m - 1) || (key[i] != key[i + 1]);
+    flag[i] = last ? 1u : 0u;
+    any_dup |= !last;
+  }
+  if (__any_sync(kFullMask, any_dup) && lane_id() == 0) atomicOr(dup, 8u);
+}
+
+__global__ void compact_edges_kernel(const uint64_t* __restrict__ key, const uint32_t* __restrict__ idx,
+                                     const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                                     const int8_t* __restrict__ sign, int64_t m, int bits_v,
+                                     int32_t* __restrict__ eu, int32_t* __restrict__ ev, uint8_t* __restrict__ eneg) {
+  const uint64_t mask_v = (bits_v >= 64) ? ~0ull : ((1ull << bits_v) - 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[i]) continue;
+    const uint32_t j = pos[i];
+    const uint64_t k = key[i];
+    eu[j] = (int32_t)(k >> bits_v);
+    ev[j] = (int32_t)(k & mask_v);
+    eneg[j] = sign[idx[i]] < 0 ? 1 : 0;
+  }
+}
+
+// Degrees over unified ids; consecutive equal ids (edges are sorted by u) are
+// merged within a warp before the atomic.
+__global__ void degree_kernel(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev, int64_t m,
+                              int32_t n_u, int32_t* __restrict__ deg) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (m + stride - 1) / stride;
+  for (int64_t it = 0; it < iters; it++) {
+    const int64_t i = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = i < m;
+    const int32_t a = ok ? eu[i] : -1;
+    const int32_t b = ok ? n_u + ev[i] : -1;
+    unsigned peers = __match_any_sync(kFullMask, a);
+    if (ok && (int)lane_id() == 31 - __clz(peers)) atomicAdd(&deg[a], __popc(peers));
+    peers = __match_any_sync(kFullMask, b);
+    if (ok && (int)lane_id() == 31 - __clz(peers)) atomicAdd(&deg[b], __popc(peers));
+  }
+}
+
+// Sort key per vertex: (side, degree, side-local id). Ascending order is the
+// Def. 3 priority within each side; V ids follow U ids in the unified space.
+__global__ void vertex_keys_kernel(const int32_t* __restrict__ deg, int64_t n, int32_t n_u, int bits_deg,
+                                   int bits_id, uint64_t* __restrict__ key) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t side = x >= n_u ? 1 : 0;
+    const uint64_t local = side ? (uint64_t)(x - n_u) : (uint64_t)x;
+    key[x] = (side << (bits_deg + bits_id)) | ((uint64_t)deg[x] << bits_id) | local;
+  }
+}
+
+__global__ void ranks_kernel(const uint64_t* __restrict__ skey, int64_t n, int32_t n_u, int bits_deg, int bits_id,
+                             int32_t* __restrict__ vertex, int32_t* __restrict__ side_rank,
+                             int32_t* __restrict__ rowdeg) {
+  const uint64_t id_mask = (1ull << bits_id) - 1, deg_mask = (1ull << bits_deg) - 1;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = skey[r];
+    const bool side = (k >> (bits_deg + bits_id)) & 1;
+    const int32_t local = (int32_t)(k & id_mask);
+    const int32_t x = side ? n_u + local : local;
+    vertex[r] = x;
+    side_rank[x] = side ? (int32_t)(r - n_u) : (int32_t)r;
+    rowdeg[r] = (int32_t)((k >> bits_id) & deg_mask);
+  }
+}
+
+// Two CSR entries per edge: key = (row << (bits_col + 1)) | (col << 1) | negative.
+__global__ void csr_keys_kernel(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                                const uint8_t* __restrict__ eneg, int64_t m, int32_t n_u,
+                                const int32_t* __restrict__ side_rank, int bits_col, uint64_t* __restrict__ key) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t ru = (uint32_t)side_rank[eu[i]];
+    const uint64_t rv = (uint32_t)side_rank[n_u + ev[i]];
+    const uint64_t neg = eneg[i];
+    key[2 * i] = (ru << (bits_col + 1)) | (rv << 1) | neg;
+    key[2 * i + 1] = (((uint64_t)n_u + rv) << (bits_col + 1)) | (ru << 1) | neg;
+  }
+}
+
+__global__ void csr_cols_kernel(const uint64_t* __restrict__ key, int64_t nnz, int bits_col,
+                                uint32_t* __restrict__ col) {
+  const uint64_t mask = (1ull << (bits_col + 1)) - 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
+    col[i] = (uint32_t)(key[i] & mask);
+}
+
+template <typename T>
+__device__ __forceinline__ int64_t lower_bound_dev(const T* a, int64_t n, T x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+template <typename T>
+__device__ __forceinline__ int64_t upper_bound_dev(const T* a, int64_t n, T x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// lower[r] = neighbours of row r with lower Def. 3 priority. A U vertex of
+// degree d is above a V vertex iff deg(v) < d (equal degree: the V id is
+// larger); a V vertex of degree d is above a U vertex iff deg(u) <= d.
+// Rows list neighbours by ascending side rank, so the lower ones are a prefix.
+__global__ void lower_kernel(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                             const int32_t* __restrict__ rowdeg, int64_t n, int32_t n_u,
+                             uint32_t* __restrict__ lower) {
+  const int32_t n_v = (int32_t)(n - n_u);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = rowdeg[r];
+    int64_t t;  // side rank threshold in the other side
+    if (r < n_u) t = lower_bound_dev<int32_t>(rowdeg + n_u, n_v, d);
+    else t = upper_bound_dev<int32_t>(rowdeg, n_u, d);
+    const int64_t b = row_ptr[r];
+    lower[r] = (uint32_t)lower_bound_dev<uint32_t>(col + b, row_ptr[r + 1] - b, (uint32_t)(t << 1));
+  }
+}
+
+// work[p] = sum over lower neighbours v of p of |{w in row(v) : rank(w) < rank(p)}|,
+// i.e. the wedges Algorithm 1 accepts at pivot p. One thread per CSR entry;
+// entries of a row are contiguous, so a segmented warp sum merges them.
+__global__ void work_kernel(const uint64_t* __restrict__ key, const int64_t* __restrict__ row_ptr,
+                            const uint32_t* __restrict__ col, const uint32_t* __restrict__ lower, int64_t nnz,
+                            int32_t n_u, int bits_col, unsigned long long* __restrict__ work) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (nnz + stride - 1) / stride;
+  const unsigned lane = lane_id();
+  for (int64_t it = 0; it < iters; it++) {
+    const int64_t i = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t r = -1;
+    uint64_t acc = 0;
+    if (i < nnz) {
+      r = (int64_t)(key[i] >> (bits_col + 1));
+      if ((uint64_t)(i - row_ptr[r]) < lower[r]) {
+        const uint32_t e = col[i];
+        const bool is_u = r < n_u;
+        const uint32_t sp = is_u ? (uint32_t)r : (uint32_t)(r - n_u);
+        const int64_t vrow = (is_u ? (int64_t)n_u : 0) + (e >> 1);
+        const int64_t b = row_ptr[vrow];
+        acc = (uint64_t)lower_bound_dev<uint32_t>(col + b, row_ptr[vrow + 1] - b, sp << 1);
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_down_sync(kFullMask, acc, o);
+      const int64_t r2 = __shfl_down_sync(kFullMask, r, o);
+      if (lane + o < 32 && r2 == r) acc += y;
+    }
+    const int64_t rp = __shfl_up_sync(kFullMask, r, 1);
+    if (r >= 0 && acc && (lane == 0 || rp != r)) atomicAdd(&work[r], (unsigned long long)acc);
+  }
+}
+
+struct PrepStats {
+  unsigned long long wedges, wedges_hub, wedges_medium, wedges_light, max_work;
+  unsigned long long n_piv, n_hub, n_medium;
+};
+
+// Pivots that can close a butterfly: at least two lower neighbours and at
+// least one accepted wedge. (A pivot with a single lower neighbour v reaches
+// every endpoint w at most once, so all its buckets stay below 2.)
+__global__ void pivot_flags_kernel(const uint64_t* __restrict__ work, const uint32_t* __restrict__ lower, int64_t n,
+                                   uint32_t* __restrict__ flag, PrepStats* st) {
+  uint64_t w_all = 0, w_hub = 0, w_med = 0, w_light = 0, mx = 0, np = 0, nh = 0, nm = 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t w = work[r];
+    w_all += w;
+    const bool piv = lower[r] >= 2 && w > 0;
+    flag[r] = piv ? 1u : 0u;
+    if (piv) {
+      np++;
+      mx = w > mx ? w : mx;
+      if (w > kMediumMaxWork) { nh++; w_hub += w; }
+      else if (w > kLightMaxWork) { nm++; w_med += w; }
+      else w_light += w;
+    }
+  }
+  w_all = warp_sum_u64(w_all);
+  w_hub = warp_sum_u64(w_hub);
+  w_med = warp_sum_u64(w_med);
+  w_light = warp_sum_u64(w_light);
+  np = warp_sum_u64(np);
+  nh = warp_sum_u64(nh);
+  nm = warp_sum_u64(nm);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t y = __shfl_xor_sync(kFullMask, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if (lane_id() == 0) {
+    if (w_all) atomicAdd(&st->wedges, (unsigned long long)w_all);
+    if (w_hub) atomicAdd(&st->wedges_hub, (unsigned long long)w_hub);
+    if (w_med) atomicAdd(&st->wedges_medium, (unsigned long long)w_med);
+    if (w_light) atomicAdd(&st->wedges_light, (unsigned long long)w_light);
+    if (mx) atomicMax(&st->max_work, (unsigned long long)mx);
+    if (np) atomicAdd(&st->n_piv, (unsigned long long)np);
+    if (nh) atomicAdd(&st->n_hub, (unsigned long long)nh);
+    if (nm) atomicAdd(&st->n_medium, (unsigned long long)nm);
+  }
+}
+
+// Descending-work sort key for pivot rows: (2^bits - 1 - work) ascending.
+__global__ void pivot_keys_kernel(const uint64_t* __restrict__ work, const uint32_t* __restrict__ flag,
+                                  const uint32_t* __restrict__ pos, int64_t n, int bits, uint64_t* __restrict__ key,
+                                  uint32_t* __restrict__ row) {
+  const uint64_t top = bits >= 64 ? ~0ull : ((1ull << bits) - 1);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[r]) continue;
+    const uint32_t j = pos[r];
+    key[j] = top - work[r];
+    row[j] = (uint32_t)r;
+  }
+}
+
+__global__ void gather_u32_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n,
+                                  uint32_t* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+__global__ void gather_u64_kernel(const uint64_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n,
+                                  uint64_t* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+
+// ------------------------------------------------------------------ host
+static unsigned grid_for(int64_t n, int threads = 256) {
+  int64_t b = ceil_div<int64_t>(n > 0 ? n : 1, threads);
+  const int64_t cap = (int64_t)kNumSMs * 16;
+  return (unsigned)(b < cap ? b : cap);
+}
+
+void* graph_alloc(dbbc_graph* g, size_t bytes) {
+  void* p = dev_alloc(bytes ? bytes : 16, g->stream);
+  if (!p) throw Error{DBBC_ENOMEM, "graph_alloc"};
+  g->allocations.push_back(p);
+  g->device_bytes += bytes;
+  return p;
+}
+
+void free_graph_memory(dbbc_graph* g) {
+  for (void* p : g->allocations) dev_free(p, g->stream);
+  g->allocations.clear();
+  g->device_bytes = 0;
+}
+
+template <typename T>
+static T read_back(const T* d, cudaStream_t s) {
+  T h;
+  DBBC_CUDA(cudaMemcpyAsync(&h, d, sizeof(T), cudaMemcpyDeviceToHost, s));
+  DBBC_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
+  if (g->n_hub == 0) return;
+  std::vector<uint32_t> rows((size_t)g->n_hub), lows((size_t)g->n_hub);
+  std::vector<uint64_t> works((size_t)g->n_hub);
+  {
+    Scratch sc(s);
+    uint32_t* d_low = sc.get<uint32_t>((size_t)g->n_hub);
+    uint64_t* d_work = sc.get<uint64_t>((size_t)g->n_hub);
+    const uint32_t* d_rows = reinterpret_cast<const uint32_t*>(g->order);
+    gather_u32_kernel<<<grid_for(g->n_hub), 256, 0, s>>>(g->lower, d_rows, g->n_hub, d_low);
+    DBBC_LAUNCH_CHECK();
+    gather_u64_kernel<<<grid_for(g->n_hub), 256, 0, s>>>(g->work, d_rows, g->n_hub, d_work);
+    DBBC_LAUNCH_CHECK();
+    DBBC_CUDA(cudaMemcpyAsync(rows.data(), d_rows, rows.size() * 4, cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaMemcpyAsync(lows.data(), d_low, lows.size() * 4, cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaMemcpyAsync(works.data(), d_work, works.size() * 8, cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaStreamSynchronize(s));
+  }
+  g->hub_stride = std::max<int64_t>(g->n_u, g->n - g->n_u);
+  const size_t per_slot = (size_t)g->hub_stride * 12;
+  int64_t slots = (int64_t)(kHubSlotBudget / std::max<size_t>(per_slot, 1));
+  slots = std::max<int64_t>(1, std::min<int64_t>({slots, kMaxHubSlots, g->n_hub}));
+  g->hub_slots = (int32_t)slots;
+  std::vector<HubItem> items;
+  g->hub_wave_begin.clear();
+  for (int64_t h0 = 0; h0 < g->n_hub; h0 += slots) {
+    g->hub_wave_begin.push_back((int64_t)items.size());
+    const int64_t h1 = std::min<int64_t>(g->n_hub, h0 + slots);
+    for (int64_t h = h0; h < h1; h++) {
+      const uint64_t W = works[(size_t)h];
+      const uint32_t L = lows[(size_t)h];
+      uint64_t chunks = (W + kHubChunkWork - 1) / kHubChunkWork;
+      chunks = std::max<uint64_t>(1, std::min<uint64_t>(chunks, L));
+      for (uint64_t c = 0; c < chunks; c++) {
+        HubItem it;
+        it.slot = (int32_t)(h - h0);
+        it.row = (int32_t)rows[(size_t)h];
+        it.a = (uint32_t)((uint64_t)L * c / chunks);
+        it.b = (uint32_t)((uint64_t)L * (c + 1) / chunks);
+        if (it.b > it.a) items.push_back(it);
+      }
+    }
+  }
+  g->hub_wave_begin.push_back((int64_t)items.size());
+  g->hub_items = static_cast<HubItem*>(graph_alloc(g, items.size() * sizeof(HubItem)));
+  DBBC_CUDA(cudaMemcpyAsync(g->hub_items, items.data(), items.size() * sizeof(HubItem), cudaMemcpyHostToDevice, s));
+  DBBC_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const int8_t* s_in, int64_t m,
+                 bool on_device, bool reject_duplicates, cudaStream_t s) {
+  const int32_t n_u = g->n_u, n_v = g->n_v;
+  const int64_t n = (int64_t)n_u + n_v;
+  g->n = n;
+  g->m_input = m;
+  Scratch sc(s);
+
+  // ---- inputs on the device
+  const int32_t* du = u_in;
+  const int32_t* dv = v_in;
+  const int8_t* ds = s_in;
+  if (!on_device && m > 0) {
+    int32_t* tu = sc.get<int32_t>((size_t)m);
+    int32_t* tv = sc.get<int32_t>((size_t)m);
+    int8_t* ts = sc.get<int8_t>((size_t)m);
+    DBBC_CUDA(cudaMemcpyAsync(tu, u_in, (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    DBBC_CUDA(cudaMemcpyAsync(tv, v_in, (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    DBBC_CUDA(cudaMemcpyAsync(ts, s_in, (size_t)m, cudaMemcpyHostToDevice, s));
+    du = tu;
+    dv = tv;
+    ds = ts;
+  }
+  unsigned* d_flags = sc.get<unsigned>(4);
+  DBBC_CUDA(cudaMemsetAsync(d_flags, 0, 4 * sizeof(unsigned), s));
+
+  // ---- a1: validate
+  if (m > 0) {
+    validate_kernel<<<grid_for(m), 256, 0, s>>>(du, dv, ds, m, n_u, n_v, d_flags);
+    DBBC_LAUNCH_CHECK();
+    if (read_back(d_flags, s) != 0) throw Error{DBBC_EINVAL, "invalid edge id or sign"};
+  }
+
+  // ---- a1: keep-latest deduplication (stable sort on (u, v))
+  const int bits_u = bits_for(n_u > 0 ? (uint64_t)(n_u - 1) : 0);
+  const int bits_v = bits_for(n_v > 0 ? (uint64_t)(n_v - 1) : 0);
+  int32_t* eu = nullptr;
+  int32_t* ev = nullptr;
+  uint8_t* eneg = nullptr;
+  int64_t mu = 0;
+  if (m > 0) {
+    uint64_t* k0 = sc.get<uint64_t>((size_t)m);
+    uint64_t* k1 = sc.get<uint64_t>((size_t)m);
+    uint32_t* i0 = sc.get<uint32_t>((size_t)m);
+    uint32_t* i1 = sc.get<uint32_t>((size_t)m);
+    edge_keys_kernel<<<grid_for(m), 256, 0, s>>>(du, dv, m, bits_v, k0, i0);
+    DBBC_LAUNCH_CHECK();
+    const bool alt = radix_sort<uint64_t, uint32_t, true>(k0, k1, i0, i1, m, 0, bits_u + bits_v, s, sc);
+    const uint64_t* ks = alt ? k1 : k0;
+    const uint32_t* is = alt ? i1 : i0;
+    uint32_t* flag = alt ? i0 : i1;  // the free index buffer
+    uint32_t* pos = sc.get<uint32_t>((size_t)m);
+    run_last_kernel<<<grid_for(m), 256, 0, s>>>(ks, m, flag, d_flags + 1);
+    DBBC_LAUNCH_CHECK();
+    exclusive_scan<uint32_t, uint32_t>(flag, pos, m, s, sc, reinterpret_cast<uint32_t*>(d_flags + 2));
+    unsigned hf[4];
+    DBBC_CUDA(cudaMemcpyAsync(hf, d_flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaStreamSynchronize(s));
+    if (reject_duplicates && hf[1]) throw Error{DBBC_EINVAL, "duplicate edge under DBBC_DUP_REJECT"};
+    mu = hf[2];
+    eu = sc.get<int32_t>((size_t)mu);
+    ev = sc.get<int32_t>((size_t)mu);
+    eneg = sc.get<uint8_t>((size_t)mu);
+    compact_edges_kernel<<<grid_for(m), 256, 0, s>>>(ks, is, flag, pos, ds, m, bits_v, eu, ev, eneg);
+    DBBC_LAUNCH_CHECK();
+  }
+  g->m = mu;
+  g->nnz = 2 * mu;
+
+  // ---- a2: degrees and Def. 3 ranks per side
+  int32_t* deg = sc.get<int32_t>((size_t)n);
+  DBBC_CUDA(cudaMemsetAsync(deg, 0, (size_t)n * 4, s));
+  if (mu > 0) {
+    degree_kernel<<<grid_for(mu), 256, 0, s>>>(eu, ev, mu, n_u, deg);
+    DBBC_LAUNCH_CHECK();
+  }
+  const int64_t max_side = std::max<int64_t>(n_u, n_v);
+  const int bits_id = std::max(1, bits_for(max_side > 0 ? (uint64_t)(max_side - 1) : 0));
+  const int bits_deg = std::max(1, bits_for((uint64_t)max_side));
+  int32_t* side_rank = sc.get<int32_t>((size_t)n);
+  int32_t* rowdeg = sc.get<int32_t>((size_t)n);
+  g->vertex = static_cast<int32_t*>(graph_alloc(g, (size_t)n * 4));
+  if (n > 0) {
+    uint64_t* vk0 = sc.get<uint64_t>((size_t)n);
+    uint64_t* vk1 = sc.get<uint64_t>((size_t)n);
+    vertex_keys_kernel<<<grid_for(n), 256, 0, s>>>(deg, n, n_u, bits_deg, bits_id, vk0);
+    DBBC_LAUNCH_CHECK();
+    const bool alt = radix_sort<uint64_t, uint32_t, false>(vk0, vk1, nullptr, nullptr, n, 0, 1 + bits_deg + bits_id,
+                                                           s, sc);
+    ranks_kernel<<<grid_for(n), 256, 0, s>>>(alt ? vk1 : vk0, n, n_u, bits_deg, bits_id, g->vertex, side_rank,
+                                             rowdeg);
+    DBBC_LAUNCH_CHECK();
+  }
+
+  // ---- a3: CSR sorted by (row, priority of neighbour), sign in bit 0
+  g->row_ptr = static_cast<int64_t*>(graph_alloc(g, (size_t)(n + 1) * 8));
+  g->col = static_cast<uint32_t*>(graph_alloc(g, (size_t)g->nnz * 4));
+  g->lower = static_cast<uint32_t*>(graph_alloc(g, (size_t)n * 4));
+  g->work = static_cast<uint64_t*>(graph_alloc(g, (size_t)n * 8));
+  exclusive_scan<int32_t, int64_t>(rowdeg, g->row_ptr, n, s, sc, g->row_ptr + n);
+  DBBC_CUDA(cudaMemsetAsync(g->work, 0, (size_t)n * 8, s));
+  const int bits_col = bits_id;
+  const int bits_row = std::max(1, bits_for(n > 0 ? (uint64_t)(n - 1) : 0));
+  if (bits_row + bits_col + 1 > 64) throw Error{DBBC_EINVAL, "graph too large for 64-bit CSR keys"};
+  uint64_t* ck = nullptr;
+  if (g->nnz > 0) {
+    uint64_t* ck0 = sc.get<uint64_t>((size_t)g->nnz);
+    uint64_t* ck1 = sc.get<uint64_t>((size_t)g->nnz);
+    csr_keys_kernel<<<grid_for(mu), 256, 0, s>>>(eu, ev, eneg, mu, n_u, side_rank, bits_col, ck0);
+    DBBC_LAUNCH_CHECK();
+    // neighbours are unique within a row, so bit 0 (the sign) needs no sorting
+    const bool alt = radix_sort<uint64_t, uint32_t, false>(ck0, ck1, nullptr, nullptr, g->nnz, 1,
+                                                           bits_row + bits_col + 1, s, sc);
+    ck = alt ? ck1 : ck0;
+    csr_cols_kernel<<<grid_for(g->nnz), 256, 0, s>>>(ck, g->nnz, bits_col, g->col);
+    DBBC_LAUNCH_CHECK();
+  }
+  if (n > 0) {
+    lower_kernel<<<grid_for(n), 256, 0, s>>>(g->row_ptr, g->col, rowdeg, n, n_u, g->lower);
+    DBBC_LAUNCH_CHECK();
+  }
+
+  // ---- a4: accepted wedges per pivot and the counting tiers
+  if (g->nnz > 0) {
+    work_kernel<<<grid_for(g->nnz), 256, 0, s>>>(ck, g->row_ptr, g->col, g->lower, g->nnz, n_u, bits_col,
+                                                 reinterpret_cast<unsigned long long*>(g->work));
+    DBBC_LAUNCH_CHECK();
+  }
+  PrepStats* d_st = sc.get<PrepStats>(1);
+  DBBC_CUDA(cudaMemsetAsync(d_st, 0, sizeof(PrepStats), s));
+  uint32_t* pflag = sc.get<uint32_t>((size_t)std::max<int64_t>(n, 1));
+  if (n > 0) {
+    pivot_flags_kernel<<<grid_for(n), 256, 0, s>>>(g->work, g->lower, n, pflag, d_st);
+    DBBC_LAUNCH_CHECK();
+  }
+  const PrepStats st = read_back(d_st, s);
+  g->wedges = st.wedges;
+  g->wedges_hub = st.wedges_hub;
+  g->wedges_medium = st.wedges_medium;
+  g->wedges_light = st.wedges_light;
+  g->n_piv = (int64_t)st.n_piv;
+  g->n_hub = (int64_t)st.n_hub;
+  g->n_medium = (int64_t)st.n_medium;
+  g->n_light = g->n_piv - g->n_hub - g->n_medium;
+  g->order = static_cast<int32_t*>(graph_alloc(g, (size_t)std::max<int64_t>(g->n_piv, 1) * 4));
+  if (g->n_piv > 0) {
+    uint32_t* ppos = sc.get<uint32_t>((size_t)n);
+    exclusive_scan<uint32_t, uint32_t>(pflag, ppos, n, s, sc);
+    const int wbits = std::max(1, bits_for(st.max_work));
+    uint64_t* pk0 = sc.get<uint64_t>((size_t)g->n_piv);
+    uint64_t* pk1 = sc.get<uint64_t>((size_t)g->n_piv);
+    uint32_t* pr0 = reinterpret_cast<uint32_t*>(g->order);
+    uint32_t* pr1 = sc.get<uint32_t>((size_t)g->n_piv);
+    pivot_keys_kernel<<<grid_for(n), 256, 0, s>>>(g->work, pflag, ppos, n, wbits, pk0, pr0);
+    DBBC_LAUNCH_CHECK();
+    const bool alt = radix_sort<uint64_t, uint32_t, true>(pk0, pk1, pr0, pr1, g->n_piv, 0, wbits, s, sc);
+    if (alt)
+      DBBC_CUDA(cudaMemcpyAsync(pr0, pr1, (size_t)g->n_piv * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  plan_hubs(g, s);
+  DBBC_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace dbbc

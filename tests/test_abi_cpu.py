@@ -1,0 +1,75 @@
+"""The C-ABI library builds for sm_103a, loads on a machine without a GPU and
+exports every entry point that include/dbbc.h declares. Only calls that touch
+no CUDA state are made here (argument checks, strings, size estimates)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2609_21848_gb300 as dbbc
+from paper_2609_21848_gb300 import buildlib
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "dbbc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    buildlib.build()
+    return dbbc.lib()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^DBBC_API [^(]*?\b(dbbc_\w+)\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for want in ("dbbc_graph_from_coo", "dbbc_count", "dbbc_count_batch", "dbbc_count_batch_async",
+                 "dbbc_graph_device_bytes", "dbbc_estimate_bytes", "dbbc_graph_free", "dbbc_set_allocator",
+                 "dbbc_status_string"):
+        assert want in names
+    assert set(names) == set(dbbc.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", dbbc.LIB_PATH], capture_output=True, text=True, check=True)
+    exported = set(re.findall(r"\bT (dbbc_\w+)", out.stdout))
+    for name in declared_symbols():
+        assert name in exported, name
+        assert hasattr(lib, name)
+
+
+def test_status_strings_and_version(lib):
+    assert dbbc.dbbc_status_string(dbbc.DBBC_OK) == "ok"
+    for code in range(1, 7):
+        assert dbbc.dbbc_status_string(code) not in ("", "ok", "unknown status")
+    assert dbbc.dbbc_status_string(99) == "unknown status"
+    assert re.fullmatch(r"\d+\.\d+\.\d+", dbbc.dbbc_version())
+
+
+def test_argument_errors_need_no_gpu(lib):
+    h = ctypes.c_void_p()
+    L = dbbc.lib()
+    assert L.dbbc_graph_from_coo(None, None, None, -1, 2, 2, 0, None, ctypes.byref(h)) == dbbc.DBBC_EINVAL
+    assert L.dbbc_graph_from_coo(None, None, None, 5, 2, 2, 0, None, ctypes.byref(h)) == dbbc.DBBC_EINVAL
+    assert L.dbbc_graph_from_coo(None, None, None, 0, -1, 2, 0, None, ctypes.byref(h)) == dbbc.DBBC_EINVAL
+    assert L.dbbc_graph_from_coo(None, None, None, 0, 2, 2, 0x10, None, ctypes.byref(h)) == dbbc.DBBC_EINVAL
+    assert L.dbbc_graph_from_coo(None, None, None, 0, 2, 2, 0, None, None) == dbbc.DBBC_EINVAL
+    assert L.dbbc_graph_from_coo(None, None, None, 1 << 31, 2, 2, 0, None, ctypes.byref(h)) == dbbc.DBBC_EINVAL
+    assert L.dbbc_count(None, None, None, None) == dbbc.DBBC_EINVAL
+    assert L.dbbc_count_async(None, None, None) == dbbc.DBBC_EINVAL
+    assert L.dbbc_count_batch(None, -1, None, None, None) == dbbc.DBBC_EINVAL
+    assert L.dbbc_graph_get_info(None, None) == dbbc.DBBC_EINVAL
+    assert L.dbbc_graph_export(None, None, None, None, None, None, None) == dbbc.DBBC_EINVAL
+    assert L.dbbc_graph_device_bytes(None) == 0
+    L.dbbc_graph_free(None)
+
+
+def test_estimate_bytes_grows_with_size(lib):
+    a = dbbc.dbbc_estimate_bytes(1_000, 100, 100)
+    b = dbbc.dbbc_estimate_bytes(1_000_000, 100_000, 100_000)
+    assert 0 < a < b
+    assert dbbc.dbbc_estimate_bytes(-1, 1, 1) == 0

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+bit-exact, on worked examples, closed forms, edge cases, seeded synthetic
+graphs that span every counting tier, and the full-size Chung-Lu workload."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2609_21848_gb300 as dbbc
+from conftest import read_golden
+from gpu_util import assert_parity, gpu_count, host_csr
+
+pytestmark = pytest.mark.gpu
+
+NCPU = max(1, len(os.sched_getaffinity(0)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    dbbc.lib()
+
+
+def _rand(rng, n_u, n_v, m, p_plus=0.5):
+    pairs = rng.choice(n_u * n_v, size=min(m, n_u * n_v), replace=False)
+    return (pairs // n_v).astype(np.int32), (pairs % n_v).astype(np.int32), \
+        np.where(rng.random(pairs.shape[0]) < p_plus, 1, -1).astype(np.int8)
+
+
+def _kab(a, b, sign=None):
+    u, v = np.meshgrid(np.arange(a), np.arange(b), indexing="ij")
+    u, v = u.ravel().astype(np.int32), v.ravel().astype(np.int32)
+    s = np.ones(u.shape[0], np.int8) if sign is None else sign(u, v).astype(np.int8)
+    return u, v, s
+
+
+# ------------------------------------------------------------- paper examples
+def test_worked_example():
+    g = read_golden("worked_example_k22.txt")
+    e = np.array(g["edge"])
+    bal, unb, info = gpu_count(e[:, 0], e[:, 1], e[:, 2], g["n_u"][0][0], g["n_v"][0][0])
+    assert (bal, unb) == (1, 0)
+    assert info["wedges"] == g["expect"][3][1]
+
+
+def test_all_sign_patterns_of_k22():
+    u, v = np.array([0, 0, 1, 1]), np.array([0, 1, 0, 1])
+    for bits in range(16):
+        s = np.array([-1 if bits >> i & 1 else 1 for i in range(4)])
+        k = bin(bits).count("1")
+        assert gpu_count(u, v, s, 2, 2)[:2] == ((1, 0) if k % 2 == 0 else (0, 1))
+
+
+@pytest.mark.parametrize("a,b", [(2, 3), (9, 7), (40, 60), (120, 90), (300, 200)])
+def test_complete_bipartite(a, b):
+    u, v, s = _kab(a, b)
+    bal, unb, info = gpu_count(u, v, s, a, b)
+    assert (bal, unb) == (math.comb(a, 2) * math.comb(b, 2), 0)
+    assert info["wedges"] == (b * math.comb(a, 2) if b > a else a * math.comb(b, 2))
+
+
+def test_complete_bipartite_camp_signs_spans_tiers():
+    rng = np.random.default_rng(5)
+    a, b = 260, 180
+    cu, cv = rng.choice([-1, 1], size=a), rng.choice([-1, 1], size=b)
+    u, v, s = _kab(a, b, lambda x, y: cu[x] * cv[y])
+    bal, unb, info = gpu_count(u, v, s, a, b)
+    assert (bal, unb) == (math.comb(a, 2) * math.comb(b, 2), 0)
+    assert info["n_light"] > 0 and info["n_medium"] > 0 and info["n_hub"] > 0
+
+
+# ------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("edges,n_u,n_v", [
+    ([], 0, 0), ([], 5, 3), ([(0, 0, 1)], 1, 1), ([(0, j, 1) for j in range(50)], 1, 50),
+    ([(i, 0, -1) for i in range(70)], 70, 1), ([(0, 0, 1), (1, 0, -1), (1, 1, 1), (2, 1, -1)], 3, 2),
+])
+def test_degenerate(edges, n_u, n_v):
+    e = np.array(edges, np.int64).reshape(-1, 3)
+    bal, unb, info = gpu_count(e[:, 0], e[:, 1], e[:, 2], n_u, n_v)
+    assert (bal, unb) == (0, 0)
+
+
+@pytest.mark.parametrize("bad", ["u", "v", "sign0", "sign2", "neg_u"])
+def test_invalid_input_is_einval(bad):
+    u, v, s = np.array([0, 1, 1]), np.array([0, 0, 1]), np.array([1, -1, 1])
+    if bad == "u":
+        u[1] = 2
+    elif bad == "v":
+        v[0] = 7
+    elif bad == "sign0":
+        s[2] = 0
+    elif bad == "sign2":
+        s[0] = 2
+    else:
+        u[0] = -3
+    with pytest.raises(dbbc.DbbcError) as ei:
+        dbbc.dbbc_graph_from_coo(u, v, s, 2, 2)
+    assert ei.value.status == dbbc.DBBC_EINVAL
+
+
+def test_duplicates_keep_latest_and_reject_flag():
+    rng = np.random.default_rng(9)
+    u, v, s = _rand(rng, 50, 40, 900)
+    pick = rng.choice(u.shape[0], 200, replace=False)
+    u2, v2 = np.concatenate([u, u[pick]]), np.concatenate([v, v[pick]])
+    s2 = np.concatenate([s, -s[pick]]).astype(np.int8)
+    info = assert_parity(u2, v2, s2, 50, 40)
+    assert info["m"] == 900 and info["m_input"] == 1100
+    with pytest.raises(dbbc.DbbcError) as ei:
+        dbbc.dbbc_graph_from_coo(u2, v2, s2, 50, 40, reject_duplicates=True)
+    assert ei.value.status == dbbc.DBBC_EINVAL
+    with dbbc.dbbc_graph_from_coo(u, v, s, 50, 40, reject_duplicates=True) as g:
+        assert dbbc.dbbc_count(g) == oracle.count(u, v, s, 50, 40)[:2]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_small_vs_brute_force(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n_u, n_v = int(rng.integers(2, 30)), int(rng.integers(2, 30))
+    u, v, s = _rand(rng, n_u, n_v, int(rng.integers(1, n_u * n_v + 1)), float(rng.random()))
+    assert gpu_count(u, v, s, n_u, n_v)[:2] == oracle.brute_force(u, v, s, n_u, n_v)
+
+
+# ------------------------------------------------------------- seeded workloads
+@pytest.mark.parametrize("device_input", [False, True])
+def test_uniform_2k_3k_20k(device_input):
+    g = synth.workload("uniform-2k-3k-20k")
+    assert_parity(g.u, g.v, g.s, g.n_u, g.n_v, device_input=device_input)
+
+
+@pytest.mark.parametrize("scale", [0.002, 0.01, 0.05])
+def test_chunglu_scaled(scale):
+    g = synth.workload("chunglu-1m-200k-20m", scale=scale)
+    info = assert_parity(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)
+    assert info["n_pivots"] > 0
+
+
+@pytest.mark.parametrize("scale", [0.0005, 0.002])
+def test_polarized_scaled(scale):
+    g = synth.workload("polarized-20m-2m-300m", scale=scale)
+    assert_parity(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)
+
+
+def test_dense_hub_graph_ragged_sizes():
+    # a few dense hubs over a sparse background: hub tier with many chunks,
+    # side sizes that are not multiples of any tile
+    rng = np.random.default_rng(77)
+    n_u, n_v = 3001, 1777
+    hubs = rng.choice(n_u, 7, replace=False)
+    u = [np.repeat(hubs, n_v)]
+    v = [np.tile(np.arange(n_v), hubs.shape[0])]
+    bu, bv, _ = _rand(rng, n_u, n_v, 30_000)
+    u = np.concatenate(u + [bu]).astype(np.int32)
+    v = np.concatenate(v + [bv]).astype(np.int32)
+    s = np.where(rng.random(u.shape[0]) < 0.6, 1, -1).astype(np.int8)
+    info = assert_parity(u, v, s, n_u, n_v, threads=NCPU)
+    assert info["n_hub"] > 0
+
+
+# ------------------------------------------------------------- CSR export
+@pytest.mark.parametrize("which", ["uniform", "chunglu"])
+def test_csr_export_matches_host_build(which):
+    if which == "uniform":
+        g = synth.workload("uniform-2k-3k-20k")
+    else:
+        g = synth.workload("chunglu-1m-200k-20m", scale=0.005)
+    want = host_csr(g.u, g.v, g.s, g.n_u, g.n_v)
+    _, _, wed = oracle.count_per_pivot(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)
+    with dbbc.dbbc_graph_from_coo(g.u, g.v, g.s, g.n_u, g.n_v) as h:
+        got = dbbc.dbbc_graph_export(h)
+    assert np.array_equal(got["row_ptr"], want["row_ptr"])
+    assert np.array_equal(got["col"], want["col"])
+    assert np.array_equal(got["vertex"], want["vertex"])
+    assert np.array_equal(got["lower"].astype(np.int64), want["lower"])
+    assert np.array_equal(got["work"], wed[got["vertex"]])
+
+
+# ------------------------------------------------------------- batch / async / allocator
+def test_batch_and_async_match_single_counts():
+    import torch
+    graphs = [synth.batch_graph(i) for i in range(12)]
+    want = [oracle.count(g.u, g.v, g.s, g.n_u, g.n_v)[:2] for g in graphs]
+    handles = [dbbc.dbbc_graph_from_coo(g.u, g.v, g.s, g.n_u, g.n_v) for g in graphs]
+    try:
+        bal, unb = dbbc.dbbc_count_batch(handles)
+        assert list(zip(bal.tolist(), unb.tolist())) == want
+        d_out = torch.zeros((len(handles), 2), dtype=torch.int64, device="cuda")
+        dbbc.dbbc_count_batch_async(handles, d_out)
+        got = d_out.cpu().numpy().astype(np.uint64)
+        assert [tuple(map(int, r)) for r in got] == want
+        one = torch.zeros(2, dtype=torch.int64, device="cuda")
+        dbbc.dbbc_count_async(handles[3], one)
+        assert tuple(map(int, one.cpu().tolist())) == want[3]
+    finally:
+        for h in handles:
+            h.free()
+
+
+def test_torch_allocator_hook():
+    g = synth.workload("chunglu-1m-200k-20m", scale=0.003)
+    want = oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[:2]
+    dbbc.dbbc_set_allocator(True)
+    try:
+        assert gpu_count(g.u, g.v, g.s, g.n_u, g.n_v)[:2] == want
+    finally:
+        dbbc.dbbc_set_allocator(False)
+    assert gpu_count(g.u, g.v, g.s, g.n_u, g.n_v)[:2] == want
+
+
+def test_repeated_counts_are_identical():
+    g = synth.workload("chunglu-1m-200k-20m", scale=0.01)
+    with dbbc.dbbc_graph_from_coo(g.u, g.v, g.s, g.n_u, g.n_v) as h:
+        first = dbbc.dbbc_count(h)
+        for _ in range(3):
+            assert dbbc.dbbc_count(h) == first
+
+
+# ------------------------------------------------------------- full size
+def test_chunglu_1m_200k_20m_full_size():
+    g = synth.workload("chunglu-1m-200k-20m")
+    assert_parity(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)
+
+
+def test_invariants_at_full_size_polarized():
+    """Properties that hold at any size, on the 300M-edge polarized graph:
+    balanced + unbalanced equals the unsigned count, and switching (negating
+    every edge at a random vertex set) changes neither count."""
+    if os.environ.get("DBBC_SKIP_HUGE"):
+        pytest.skip("DBBC_SKIP_HUGE set")
+    import torch
+    g = synth.workload("polarized-20m-2m-300m")
+    dev = torch.device("cuda")
+    u, v, s = (torch.from_numpy(x).to(dev) for x in (g.u, g.v, g.s))
+    with dbbc.dbbc_graph_from_coo(u, v, s, g.n_u, g.n_v) as h:
+        bal, unb = dbbc.dbbc_count(h)
+        wedges = h.info["wedges"]
+    with dbbc.dbbc_graph_from_coo(u, v, torch.ones_like(s), g.n_u, g.n_v) as h:
+        assert dbbc.dbbc_count(h) == (bal + unb, 0)
+    rng = np.random.default_rng(3)
+    fu = torch.from_numpy(np.where(rng.random(g.n_u) < 0.5, -1, 1).astype(np.int8)).to(dev)
+    fv = torch.from_numpy(np.where(rng.random(g.n_v) < 0.5, -1, 1).astype(np.int8)).to(dev)
+    s2 = s * fu[u.long()] * fv[v.long()]
+    with dbbc.dbbc_graph_from_coo(u, v, s2, g.n_u, g.n_v) as h:
+        assert dbbc.dbbc_count(h) == (bal, unb)
+        assert h.info["wedges"] == wedges
+    assert bal > unb > 0
