@@ -22,22 +22,36 @@ __device__ __forceinline__ unsigned long long wedge_inc(uint32_t x, uint32_t s1)
   return ((x ^ s1) & 1u) ? (1ull << 32) : 1ull;
 }
 
+// Lemma 1 contribution of one wedge, from its endpoint counter just before the
+// increment (sym = p, asym = q): adding a symmetric wedge to (p, q) closes p
+// new balanced pairs (C(p+1,2) - C(p,2) = p) and q unbalanced ones ((p+1)q - pq);
+// an asymmetric wedge closes q balanced and p unbalanced ones. Summed over all
+// wedges this equals C(p,2) + C(q,2) and p*q per endpoint.
+__device__ __forceinline__ void wedge_contrib(unsigned long long old, unsigned long long inc, uint64_t& bal,
+                                              uint64_t& unb) {
+  const uint64_t p = old & 0xFFFFFFFFull, q = old >> 32;
+  const bool sym = inc == 1ull;
+  bal += sym ? p : q;
+  unb += sym ? q : p;
+}
+
 __device__ __forceinline__ uint32_t hash_slot(uint32_t w, int log_h) {
   return (w * 2654435769u) >> (32 - log_h);
 }
 
-// Insert / find endpoint w in a shared table of 2^log_h slots and add inc.
-// Returns false if the probe sequence ran past the table (cannot happen when
-// the table has more slots than the pivot's accepted wedges).
+// Find or insert endpoint w in a shared table of 2^log_h slots and add inc;
+// returns the counter's previous value through *old. Returns false if the
+// probe sequence ran past the table (cannot happen when the table has more
+// slots than the pivot's accepted wedges).
 __device__ __forceinline__ bool smem_hash_add(uint32_t* keys, unsigned long long* vals, int log_h, uint32_t w,
-                                              unsigned long long inc) {
+                                              unsigned long long inc, unsigned long long* old) {
   const uint32_t mask = (1u << log_h) - 1u;
   uint32_t h = hash_slot(w, log_h);
   for (uint32_t probe = 0; probe <= mask; probe++) {
     uint32_t cur = *reinterpret_cast<volatile uint32_t*>(&keys[h]);
     if (cur == kEmptyKey) cur = atomicCAS(&keys[h], kEmptyKey, w);
     if (cur == kEmptyKey || cur == w) {
-      atomicAdd(&vals[h], inc);
+      *old = atomicAdd(&vals[h], inc);
       return true;
     }
     h = (h + 1u) & mask;
@@ -70,9 +84,11 @@ __device__ __forceinline__ PivotGeom pivot_geom(const CsrView& g, int32_t p) {
 }
 
 // The warp walks lower-neighbour positions [a, b) of the pivot in groups of
-// 32 (`step` = distance between this warp's groups, in positions) and calls
-// visit(w, inc) for every accepted wedge, lanes striding over each v's row.
-template <typename Visit>
+// 32 (`step` = distance between this warp's groups) and, for each lower
+// neighbour v, the accepted prefix of v's row in chunks of 32 * U entries.
+// visit(x[U], s1) is called by all lanes together; lane l holds entries
+// chunk + u*32 + l, with x = 0xFFFFFFFF where nothing is accepted.
+template <int U, typename Visit>
 __device__ __forceinline__ void warp_walk(const CsrView& g, const PivotGeom& q, uint32_t a, uint32_t b,
                                           uint32_t step, Visit&& visit) {
   const unsigned lane = lane_id();
@@ -90,12 +106,23 @@ __device__ __forceinline__ void warp_walk(const CsrView& g, const PivotGeom& q, 
       const uint32_t s1 = __shfl_sync(kFullMask, e, k) & 1u;
       const int64_t jb0 = __shfl_sync(kFullMask, vb, k);
       const int64_t je = __shfl_sync(kFullMask, ve, k);
-      for (int64_t jb = jb0; jb < je; jb += 32) {
-        const int64_t j = jb + lane;
-        const uint32_t x = j < je ? g.col[j] : 0xFFFFFFFFu;
-        const bool ok = x < q.lim;
-        if (ok) visit(x >> 1, wedge_inc(x, s1));
-        if (__ballot_sync(kFullMask, !ok)) break;  // rows ascend: nothing accepted beyond
+      for (int64_t jb = jb0; jb < je; jb += 32 * U) {
+        uint32_t x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int64_t j = jb + u * 32 + lane;
+          x[u] = j < je ? g.col[j] : 0xFFFFFFFFu;
+        }
+        bool stop = false;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          if (x[u] >= q.lim) {
+            x[u] = 0xFFFFFFFFu;
+            stop = true;
+          }
+        }
+        visit(x, s1);
+        if (__any_sync(kFullMask, stop)) break;  // rows ascend: nothing accepted beyond
       }
     }
   }
@@ -127,16 +154,18 @@ __global__ void __launch_bounds__(kLightWarps * 32) count_light_kernel(CsrView g
     const int32_t p = piv[t];
     const int log_h = table_log(work[p], max_log);
     const PivotGeom q = pivot_geom(g, p);
-    warp_walk(g, q, 0, q.L, 32, [&](uint32_t x, unsigned long long inc) {
-      full |= !smem_hash_add(keys, vals, log_h, x, inc);
+    warp_walk<1>(g, q, 0, q.L, 32, [&](const uint32_t (&x)[1], uint32_t s1) {
+      if (x[0] != 0xFFFFFFFFu) {
+        const unsigned long long inc = wedge_inc(x[0], s1);
+        unsigned long long old;
+        if (smem_hash_add(keys, vals, log_h, x[0] >> 1, inc, &old)) wedge_contrib(old, inc, bal, unb);
+        else full = true;
+      }
     });
     __syncwarp();
     for (int i = lane; i < (1 << log_h); i += 32) {
-      if (keys[i] != kEmptyKey) {
-        pair_contrib(vals[i], bal, unb);
-        keys[i] = kEmptyKey;
-        vals[i] = 0;
-      }
+      keys[i] = kEmptyKey;
+      vals[i] = 0;
     }
     __syncwarp();
   }
@@ -168,16 +197,21 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
     const int32_t p = piv[t];
     const int log_h = table_log(work[p], max_log);
     const PivotGeom q = pivot_geom(g, p);
-    warp_walk(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u, [&](uint32_t x, unsigned long long inc) {
-      full |= !smem_hash_add(keys, vals, log_h, x, inc);
+    warp_walk<2>(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u, [&](const uint32_t (&x)[2], uint32_t s1) {
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        if (x[u] != 0xFFFFFFFFu) {
+          const unsigned long long inc = wedge_inc(x[u], s1);
+          unsigned long long old;
+          if (smem_hash_add(keys, vals, log_h, x[u] >> 1, inc, &old)) wedge_contrib(old, inc, bal, unb);
+          else full = true;
+        }
+      }
     });
     __syncthreads();
     for (int i = threadIdx.x; i < (1 << log_h); i += kMediumThreads) {
-      if (keys[i] != kEmptyKey) {
-        pair_contrib(vals[i], bal, unb);
-        keys[i] = kEmptyKey;
-        vals[i] = 0;
-      }
+      keys[i] = kEmptyKey;
+      vals[i] = 0;
     }
     __syncthreads();
   }
@@ -186,53 +220,96 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
 }
 
 // ------------------------------------------------------------------ hub tier
-constexpr int kHubThreads = 256;
-constexpr int kHubWarps = kHubThreads / 32;
+// Window sweep. A hub pivot's accepted endpoints [0, side_rank(p)) are cut
+// into windows of kSweepWindow16 (or kSweepWindow32) consecutive side ranks. A
+// work item is one hub and a span of its windows, owned by one CTA, so the
+// counts of every endpoint in a window are complete inside that CTA: they live
+// in shared memory, and the Lemma 1 contributions come from the value each
+// atomic returns. Each lower neighbour v keeps a cursor into its row; rows
+// ascend, so sweeping the windows in order moves every cursor forward only.
+// Counters pack (asym << 16) | sym when the hub has fewer than 2^16 lower
+// neighbours (no count can exceed that), else (asym << 32) | sym.
+constexpr int kSweepThreads = 1024;
 
-// Pull (hub, lower-neighbour range) items and add every accepted wedge to the
-// hub's dense counter array; the first increment of an endpoint appends it to
-// the slot's touched list.
-__global__ void __launch_bounds__(kHubThreads) hub_aggregate_kernel(CsrView g, const HubItem* __restrict__ items,
-                                                                    int64_t n_items, unsigned long long* __restrict__ ctr,
-                                                                    uint32_t* __restrict__ touched, int64_t stride,
-                                                                    uint32_t* __restrict__ tcount, int* next_item) {
+__device__ __forceinline__ void sweep_contrib16(uint32_t old, bool sym, uint64_t& bal, uint64_t& unb) {
+  const uint64_t p = old & 0xFFFFu, q = old >> 16;
+  bal += sym ? p : q;
+  unb += sym ? q : p;
+}
+
+__global__ void __launch_bounds__(kSweepThreads, 1) hub_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
+                                                                      int64_t n_items, int* next_item,
+                                                                      int64_t* __restrict__ cursors, int64_t cur_cap,
+                                                                      unsigned long long* out) {
+  extern __shared__ __align__(16) unsigned char sweep_smem[];
+  uint32_t* c16 = reinterpret_cast<uint32_t*>(sweep_smem);
+  unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
   __shared__ int item_sh;
-  const int w = threadIdx.x >> 5;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
+  int64_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
+  uint64_t bal = 0, unb = 0;
   for (;;) {
-    if (threadIdx.x == 0) item_sh = atomicAdd(next_item, 1);
-    __syncthreads();
+    if (tid == 0) item_sh = atomicAdd(next_item, 1);
+    __syncthreads();  // also orders the zeroing above / below before reuse
     const int64_t it = item_sh;
     __syncthreads();
     if (it >= n_items) break;
-    const HubItem item = items[it];
+    const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    unsigned long long* c = ctr + (int64_t)item.slot * stride;
-    uint32_t* tl = touched + (int64_t)item.slot * stride;
-    uint32_t* tc = tcount + item.slot;
-    warp_walk(g, q, item.a + (uint32_t)w * 32u, item.b, kHubWarps * 32u, [&](uint32_t x, unsigned long long inc) {
-      const unsigned long long old = atomicAdd(&c[x], inc);
-      if (old == 0ull) tl[atomicAdd(tc, 1u)] = x;
-    });
+    const uint32_t sp = q.lim >> 1;
+    const bool pack16 = q.L < 65536u;
+    const uint32_t H = pack16 ? kSweepWindow16 : kSweepWindow32;
+    // cursors: first entry at or after the span's first window, and row end
+    const uint32_t first = (uint32_t)((uint64_t)item.w0 * H) << 1;
+    for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
+      const uint32_t e = g.col[q.rb + i];
+      const int64_t vrow = q.base + (e >> 1);
+      int64_t b = g.row_ptr[vrow];
+      const int64_t en = g.row_ptr[vrow + 1];
+      if (first) {  // lower_bound of `first` in the row
+        int64_t lo = b, hi = en;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (g.col[mid] < first) lo = mid + 1; else hi = mid;
+        }
+        b = lo;
+      }
+      cur[2 * i] = b;
+      cur[2 * i + 1] = en;
+    }
+    __syncthreads();
+    for (uint32_t wdw = item.w0; wdw < item.w1; wdw++) {
+      const uint32_t lo = wdw * H;
+      const uint32_t hi = min(lo + H, sp);
+      const uint32_t hl = hi << 1;
+      const uint32_t lo2 = lo << 1;
+      for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
+        int64_t c = cur[2 * i];
+        const int64_t en = cur[2 * i + 1];
+        const uint32_t s1 = g.col[q.rb + i] & 1u;
+        while (c < en) {
+          const uint32_t x = g.col[c];
+          if (x >= hl) break;
+          const bool sym = ((x ^ s1) & 1u) == 0;
+          const uint32_t k = (x - lo2) >> 1;
+          if (pack16) {
+            sweep_contrib16(atomicAdd(&c16[k], sym ? 1u : 0x10000u), sym, bal, unb);
+          } else {
+            const unsigned long long inc = sym ? 1ull : (1ull << 32);
+            wedge_contrib(atomicAdd(&c32[k], inc), inc, bal, unb);
+          }
+          c++;
+        }
+        cur[2 * i] = c;
+      }
+      __syncthreads();
+      const uint32_t words = pack16 ? (hi - lo) : 2 * (hi - lo);  // 32-bit words to clear
+      for (uint32_t j = tid; j < words; j += kSweepThreads) c16[j] = 0u;
+      __syncthreads();
+    }
   }
-}
-
-// Finalise one wave: every touched endpoint of every slot adds its Lemma 1
-// contribution and its counter is cleared for the next wave.
-__global__ void __launch_bounds__(kHubThreads) hub_finalize_kernel(unsigned long long* __restrict__ ctr,
-                                                                   const uint32_t* __restrict__ touched,
-                                                                   int64_t stride, const uint32_t* __restrict__ tcount,
-                                                                   unsigned long long* out) {
-  const int slot = blockIdx.y;
-  const uint32_t cnt = tcount[slot];
-  unsigned long long* c = ctr + (int64_t)slot * stride;
-  const uint32_t* tl = touched + (int64_t)slot * stride;
-  uint64_t bal = 0, unb = 0;
-  for (uint32_t i = blockIdx.x * kHubThreads + threadIdx.x; i < cnt; i += gridDim.x * kHubThreads) {
-    const uint32_t x = tl[i];
-    pair_contrib(c[x], bal, unb);
-    c[x] = 0;
-  }
-  block_add_pair<kHubThreads>(bal, unb, out);
+  block_add_pair<kSweepThreads>(bal, unb, out);
 }
 
 // ------------------------------------------------------------------ host
@@ -331,43 +408,19 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
     }
   }
   if (g->n_hub > 0) {
-    const int64_t slots = g->hub_slots, stride = g->hub_stride;
-    const int64_t waves = (int64_t)g->hub_wave_begin.size() - 1;
-    unsigned long long* ctr = sc.get<unsigned long long>((size_t)(slots * stride));
-    uint32_t* touched = sc.get<uint32_t>((size_t)(slots * stride));
-    uint32_t* tcount = sc.get<uint32_t>((size_t)(waves * slots));
-    int* next = sc.get<int>((size_t)waves);
-    DBBC_CUDA(cudaMemsetAsync(ctr, 0, (size_t)(slots * stride) * 8, s));
-    DBBC_CUDA(cudaMemsetAsync(tcount, 0, (size_t)(waves * slots) * 4, s));
-    DBBC_CUDA(cudaMemsetAsync(next, 0, (size_t)waves * 4, s));
-    const int agg_blocks = sms * blocks_per_sm((const void*)hub_aggregate_kernel, kHubThreads, 0);
-    const unsigned fin_x = (unsigned)std::max<int64_t>(1, (int64_t)sms * 4 / slots);
-    for (int64_t wv = 0; wv < waves; wv++) {
-      const int64_t i0 = g->hub_wave_begin[(size_t)wv], i1 = g->hub_wave_begin[(size_t)wv + 1];
-      const int64_t n_items = i1 - i0;
-      const unsigned blocks = (unsigned)std::min<int64_t>(n_items, agg_blocks);
-      if (prof) t0 = prof->begin(s);
-      hub_aggregate_kernel<<<blocks, kHubThreads, 0, s>>>(view, g->hub_items + i0, n_items, ctr, touched, stride,
-                                                         tcount + wv * slots, next + wv);
-      DBBC_LAUNCH_CHECK();
-      if (prof) {
-        prof->end(CountProfiler::HUB_AGG, t0, s);
-        prof->launches[CountProfiler::HUB_AGG]++;
-        t0 = prof->begin(s);
-      }
-      const int64_t wave_slots = std::min<int64_t>(slots, g->n_hub - wv * slots);
-      hub_finalize_kernel<<<dim3(fin_x, (unsigned)wave_slots), kHubThreads, 0, s>>>(ctr, touched, stride,
-                                                                                    tcount + wv * slots, d_out);
-      DBBC_LAUNCH_CHECK();
-      if (prof) {
-        prof->end(CountProfiler::HUB_FIN, t0, s);
-        prof->launches[CountProfiler::HUB_FIN]++;
-      }
-    }
+    const int grid = sms;  // one 1024-thread CTA per SM (the window takes most of shared memory)
+    const size_t smem = (size_t)kSweepWindow16 * 4;
+    DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t* cursors = sc.get<int64_t>((size_t)grid * (size_t)g->sweep_max_lower * 2);
+    int* next = sc.get<int>(1);
+    DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
+    if (prof) t0 = prof->begin(s);
+    hub_sweep_kernel<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, next, cursors,
+                                                       g->sweep_max_lower, d_out);
+    DBBC_LAUNCH_CHECK();
     if (prof) {
-      prof->hub_touched.resize((size_t)(waves * slots));
-      DBBC_CUDA(cudaMemcpyAsync(prof->hub_touched.data(), tcount, (size_t)(waves * slots) * 4,
-                                cudaMemcpyDeviceToHost, s));
+      prof->end(CountProfiler::HUB_AGG, t0, s);
+      prof->launches[CountProfiler::HUB_AGG]++;
     }
   }
   if (prof) prof->end(CountProfiler::TOTAL, t_all, s);

@@ -18,17 +18,17 @@ constexpr uint64_t kLightMaxWork = 512;    // warp per pivot, per-warp shared ha
 constexpr uint64_t kMediumMaxWork = 4096;  // CTA per pivot, shared hash (<= 8192 slots)
 constexpr int kLightSlots = 1024;
 constexpr int kMediumSlots = 8192;
-constexpr int kMaxHubSlots = 32;           // hubs counted concurrently (one dense counter array each)
-constexpr size_t kHubSlotBudget = size_t(2) << 30;  // bytes of dense counters + touched lists per count
-constexpr uint64_t kHubChunkWork = 1u << 15;        // target accepted wedges per hub work item
+// Hub window sweep: shared-memory windows of side ranks (192 KB of counters).
+constexpr uint32_t kSweepWindow16 = 49152;  // 32-bit counters packing two 16-bit halves
+constexpr uint32_t kSweepWindow32 = 24576;  // 64-bit counters packing two 32-bit halves
+constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per work item
 
-// One unit of hub work: lower-neighbour positions [a, b) of hub row `row`,
-// accumulated into dense counter array `slot`.
-struct HubItem {
-  int32_t slot;
+// One unit of hub work: windows [w0, w1) of hub row `row`.
+struct SweepItem {
   int32_t row;
-  uint32_t a;
-  uint32_t b;
+  uint32_t w0;
+  uint32_t w1;
+  uint32_t pad;
 };
 
 // Read-only view of the device CSR passed to kernels by value.
@@ -68,12 +68,10 @@ struct dbbc_graph {
   int32_t* order = nullptr;    // [n_piv] pivot rows, descending work: hubs | medium | light
   int64_t n_piv = 0, n_hub = 0, n_medium = 0, n_light = 0;
   uint64_t wedges = 0, wedges_hub = 0, wedges_medium = 0, wedges_light = 0;
-  // hub plan: waves of up to `hub_slots` hubs; items of wave w are
-  // hub_items[hub_wave_begin[w] .. hub_wave_begin[w+1])
-  int32_t hub_slots = 0;
-  int64_t hub_stride = 0;  // counters per slot (largest side)
-  dbbc::HubItem* hub_items = nullptr;
-  std::vector<int64_t> hub_wave_begin;
+  // hub plan: window-span items in descending estimated work
+  dbbc::SweepItem* sweep_items = nullptr;
+  int64_t n_sweep_items = 0;
+  int64_t sweep_max_lower = 0;  // largest lower-neighbour count of a hub (cursor scratch per CTA)
   size_t device_bytes = 0;
   std::vector<void*> allocations;
 };

@@ -315,34 +315,43 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
     DBBC_CUDA(cudaMemcpyAsync(works.data(), d_work, works.size() * 8, cudaMemcpyDeviceToHost, s));
     DBBC_CUDA(cudaStreamSynchronize(s));
   }
-  g->hub_stride = std::max<int64_t>(g->n_u, g->n - g->n_u);
-  const size_t per_slot = (size_t)g->hub_stride * 12;
-  int64_t slots = (int64_t)(kHubSlotBudget / std::max<size_t>(per_slot, 1));
-  slots = std::max<int64_t>(1, std::min<int64_t>({slots, kMaxHubSlots, g->n_hub}));
-  g->hub_slots = (int32_t)slots;
-  std::vector<HubItem> items;
-  g->hub_wave_begin.clear();
-  for (int64_t h0 = 0; h0 < g->n_hub; h0 += slots) {
-    g->hub_wave_begin.push_back((int64_t)items.size());
-    const int64_t h1 = std::min<int64_t>(g->n_hub, h0 + slots);
-    for (int64_t h = h0; h < h1; h++) {
-      const uint64_t W = works[(size_t)h];
-      const uint32_t L = lows[(size_t)h];
-      uint64_t chunks = (W + kHubChunkWork - 1) / kHubChunkWork;
-      chunks = std::max<uint64_t>(1, std::min<uint64_t>(chunks, L));
-      for (uint64_t c = 0; c < chunks; c++) {
-        HubItem it;
-        it.slot = (int32_t)(h - h0);
-        it.row = (int32_t)rows[(size_t)h];
-        it.a = (uint32_t)((uint64_t)L * c / chunks);
-        it.b = (uint32_t)((uint64_t)L * (c + 1) / chunks);
-        if (it.b > it.a) items.push_back(it);
-      }
+  // Split each hub's windows into spans of roughly equal work; a span that
+  // does not start at window 0 pays one binary search per lower neighbour, so
+  // spans are kept large against the hub's lower-neighbour count.
+  struct Planned {
+    SweepItem it;
+    uint64_t est;
+  };
+  std::vector<Planned> plan;
+  int64_t max_lower = 1;
+  for (size_t h = 0; h < rows.size(); h++) {
+    const int32_t row = (int32_t)rows[h];
+    const uint32_t L = lows[h];
+    const uint64_t W = works[h];
+    const uint64_t sp = row < g->n_u ? (uint64_t)row : (uint64_t)(row - g->n_u);
+    const uint64_t H = L < 65536u ? kSweepWindow16 : kSweepWindow32;
+    const uint64_t R = (sp + H - 1) / H;
+    const uint64_t target = std::max<uint64_t>(kSweepItemWork, 64ull * L);
+    uint64_t spans = std::max<uint64_t>(1, std::min<uint64_t>(R, W / target));
+    max_lower = std::max<int64_t>(max_lower, L);
+    for (uint64_t k = 0; k < spans; k++) {
+      Planned p;
+      p.it.row = row;
+      p.it.w0 = (uint32_t)(R * k / spans);
+      p.it.w1 = (uint32_t)(R * (k + 1) / spans);
+      p.it.pad = 0;
+      p.est = W / spans;
+      if (p.it.w1 > p.it.w0) plan.push_back(p);
     }
   }
-  g->hub_wave_begin.push_back((int64_t)items.size());
-  g->hub_items = static_cast<HubItem*>(graph_alloc(g, items.size() * sizeof(HubItem)));
-  DBBC_CUDA(cudaMemcpyAsync(g->hub_items, items.data(), items.size() * sizeof(HubItem), cudaMemcpyHostToDevice, s));
+  std::stable_sort(plan.begin(), plan.end(), [](const Planned& a, const Planned& b) { return a.est > b.est; });
+  std::vector<SweepItem> items(plan.size());
+  for (size_t i = 0; i < plan.size(); i++) items[i] = plan[i].it;
+  g->n_sweep_items = (int64_t)items.size();
+  g->sweep_max_lower = max_lower;
+  g->sweep_items = static_cast<SweepItem*>(graph_alloc(g, items.size() * sizeof(SweepItem)));
+  DBBC_CUDA(cudaMemcpyAsync(g->sweep_items, items.data(), items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice,
+                            s));
   DBBC_CUDA(cudaStreamSynchronize(s));
 }
 
