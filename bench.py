@@ -36,12 +36,15 @@ METRIC = "G wedges/s and graphs/s, batched vs per-graph launches, bit-exact coun
 UNIT = "G wedges/s"
 L2_BYTES = 129 * 2**20
 
-# Algorithmic bytes per unit of work (fixed before tuning):
-#   per accepted wedge   : 4 B CSR entry (+ 16 B u64 counter read+write in the hub tier)
-#   per lower neighbour  : 4 B entry + 16 B row offsets + 8 B end-of-row probe
-#   per touched endpoint : 4 B touched-list write in the aggregate kernel;
-#                          4 B list read + 16 B counter read/reset in the finalize kernel
-B_WEDGE, B_WEDGE_HUB, B_LOWER, B_TOUCH_AGG, B_TOUCH_FIN = 4, 20, 28, 4, 20
+# Algorithmic bytes per unit of work of the hub window-sweep kernel (the
+# dominant kernel; its counters live in shared memory):
+#   per accepted wedge               : 4 B CSR entry
+#   per (item, lower neighbour) init : 4 B pivot-row entry + 16 B row offsets + 16 B cursor write
+#   per (window, lower neighbour)    : 4 B pivot-row entry (edge sign) + 16 B cursor read
+#                                      + 8 B cursor write + 4 B first entry past the window
+# Light / medium tiers: 4 B per wedge + 28 B per lower neighbour (entry,
+# row offsets, end-of-row probe).
+B_WEDGE, B_CUR_INIT, B_CUR_STEP, B_LOWER = 4, 36, 32, 28
 
 
 def parse():
@@ -225,33 +228,25 @@ def main():
     du, dv, ds = (torch.from_numpy(x).to(dev) for x in (g.u, g.v, g.s))
     torch.cuda.synchronize(dev)
 
+    eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
     def step(prof_acc=None):
+        eb0.record(stream)
         h = dbbc.dbbc_graph_from_coo(du, dv, ds, g.n_u, g.n_v, stream=stream)
+        eb1.record(stream)
         bal, unb, prof = dbbc.dbbc_count_profiled(h, stream=stream)
         info = h.info
         h.free()
         if prof_acc is not None:
             for k, val in prof.items():
                 prof_acc[k] = prof_acc.get(k, 0) + val
+            prof_acc["ms_build"] = prof_acc.get("ms_build", 0.0) + eb0.elapsed_time(eb1)
         return bal, unb, info
 
     for _ in range(a.warmup):
         bal, unb, info = step()
     want = expected_counts(a.workload)
     verified = None if want is None else ((bal, unb, info["wedges"]) == want)
-
-    # per-tier work of this graph (for the roofline bytes)
-    h = dbbc.dbbc_graph_from_coo(du, dv, ds, g.n_u, g.n_v, stream=stream)
-    ex = dbbc.dbbc_graph_export(h, stream=stream) if g.m <= 50_000_000 else None
-    info = h.info
-    h.free()
-    if ex is not None:
-        work, lower = ex["work"].astype(np.float64), ex["lower"].astype(np.float64)
-        piv = lower >= 2
-        hub = piv & (work > 4096)
-        L_hub = float(lower[hub].sum())
-    else:
-        L_hub = float("nan")
 
     sampler = ClockSampler(local)
     prof = {}
@@ -294,25 +289,25 @@ def main():
                "h2d_bytes_per_step": 9 * g.m, "d2h_bytes_per_step": 16, "steps": e2e_steps,
                "bit_exact": r == (bal, unb)}
 
-    # roofline of the dominant kernel (hub aggregation), from the live events
+    # roofline of the dominant kernel (hub window sweep), from the live events
     peaks, peak_kind = measured_peaks()
     n_agg = max(1, int(prof.get("launches_hub_aggregate", 0)))
     agg_s = prof.get("ms_hub_aggregate", 0.0) / 1e3
-    touched = prof.get("hub_touched", 0) / a.steps
-    bytes_agg_step = B_WEDGE_HUB * info["wedges_hub"] + B_LOWER * L_hub + B_TOUCH_AGG * touched
-    per_launch_bytes = bytes_agg_step * a.steps / n_agg
+    bytes_hub_step = (B_WEDGE * info["wedges_hub"] + B_CUR_INIT * info["hub_cursor_inits"]
+                      + B_CUR_STEP * info["hub_cursor_steps"])
+    per_launch_bytes = bytes_hub_step * a.steps / n_agg
     per_launch_s = agg_s / n_agg
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
     peak = float(peaks["hbm_gbs"])
-    roofline = {"bound": "hbm", "kernel": "hub_aggregate_kernel", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": "hub_sweep_kernel", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": known_traffic("hub_aggregate_kernel", a.workload),
-                "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
-                f"of {peak_kind}",
+                "traffic": known_traffic("hub_sweep_kernel", a.workload),
+                "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "bytes_per_launch": per_launch_bytes, "launches_per_step": n_agg / a.steps,
-                "ms_per_launch": 1e3 * per_launch_s}
-    tiers_ms = {k: prof.get(k, 0.0) / a.steps for k in ("ms_light", "ms_medium", "ms_hub_aggregate",
-                                                         "ms_hub_finalize", "ms_total")}
+                "ms_per_launch": 1e3 * per_launch_s,
+                "wedges_per_s_in_kernel": info["wedges_hub"] * a.steps / agg_s if agg_s > 0 else None}
+    tiers_ms = {k: prof.get(k, 0.0) / a.steps for k in ("ms_build", "ms_light", "ms_medium", "ms_hub_aggregate",
+                                                         "ms_total")}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

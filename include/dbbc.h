@@ -125,6 +125,10 @@ typedef struct {
   int64_t n_pivots;    /* pivots with at least two lower neighbours and one accepted wedge */
   int64_t n_light, n_medium, n_hub; /* pivots per counting tier */
   uint64_t wedges_light, wedges_medium, wedges_hub;
+  int64_t lower_light, lower_medium, lower_hub; /* lower neighbours summed over the tier's pivots */
+  int64_t hub_items;         /* hub work items (a hub and a span of its endpoint windows) */
+  int64_t hub_cursor_inits;  /* sum over hub items of the hub's lower neighbours */
+  int64_t hub_cursor_steps;  /* sum over hub items of lower neighbours x windows */
   size_t device_bytes; /* device memory held by the handle */
 } dbbc_graph_info;
 

@@ -21,7 +21,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libdbbc.so")
+LIB_PATH = os.environ.get("DBBC_LIBRARY") or os.path.join(_HERE, "_build", "libdbbc.so")
 
 DBBC_OK, DBBC_EINVAL, DBBC_ENOMEM, DBBC_ECUDA, DBBC_ETIMEOUT, DBBC_EOVERFLOW, DBBC_EINTERNAL = range(7)
 DBBC_INPUT_HOST, DBBC_INPUT_DEVICE, DBBC_DUP_KEEP_LAST, DBBC_DUP_REJECT = 0, 1, 0, 2
@@ -45,7 +45,9 @@ class GraphInfo(ctypes.Structure):
                 ("m", ctypes.c_int64), ("wedges", ctypes.c_uint64), ("n_pivots", ctypes.c_int64),
                 ("n_light", ctypes.c_int64), ("n_medium", ctypes.c_int64), ("n_hub", ctypes.c_int64),
                 ("wedges_light", ctypes.c_uint64), ("wedges_medium", ctypes.c_uint64),
-                ("wedges_hub", ctypes.c_uint64), ("device_bytes", ctypes.c_size_t)]
+                ("wedges_hub", ctypes.c_uint64), ("lower_light", ctypes.c_int64), ("lower_medium", ctypes.c_int64),
+                ("lower_hub", ctypes.c_int64), ("hub_items", ctypes.c_int64), ("hub_cursor_inits", ctypes.c_int64),
+                ("hub_cursor_steps", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
 
 
 class CountProfile(ctypes.Structure):

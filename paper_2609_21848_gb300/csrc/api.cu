@@ -156,6 +156,12 @@ dbbc_status dbbc_graph_get_info(const dbbc_graph* g, dbbc_graph_info* info) {
   r.wedges_light = g->wedges_light;
   r.wedges_medium = g->wedges_medium;
   r.wedges_hub = g->wedges_hub;
+  r.lower_light = g->lower_light;
+  r.lower_medium = g->lower_medium;
+  r.lower_hub = g->lower_hub;
+  r.hub_items = g->n_sweep_items;
+  r.hub_cursor_inits = g->hub_cursor_inits;
+  r.hub_cursor_steps = g->hub_cursor_steps;
   r.device_bytes = g->device_bytes;
   *info = r;
   return DBBC_OK;

@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
 // ascend, so sweeping the windows in order moves every cursor forward only.
 // Counters pack (asym << 16) | sym when the hub has fewer than 2^16 lower
 // neighbours (no count can exceed that), else (asym << 32) | sym.
-constexpr int kSweepThreads = 1024;
+constexpr int kSweepThreads = DBBC_SWEEP_THREADS;
+constexpr int kSweepUnroll = DBBC_SWEEP_UNROLL;
 
 __device__ __forceinline__ void sweep_contrib16(uint32_t old, bool sym, uint64_t& bal, uint64_t& unb) {
   const uint64_t p = old & 0xFFFFu, q = old >> 16;
@@ -237,7 +238,68 @@ __device__ __forceinline__ void sweep_contrib16(uint32_t old, bool sym, uint64_t
   unb += sym ? q : p;
 }
 
-__global__ void __launch_bounds__(kSweepThreads, 1) hub_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
+// One window of one item: every group of G lanes takes lower neighbours
+// gid, gid + groups, ... and walks the neighbour's row from its cursor, G
+// consecutive entries at a time, until an entry leaves the window.
+template <int G, bool PACK16>
+__device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& q, int64_t* cur, uint32_t lo,
+                                             uint32_t hl, uint32_t* c16, unsigned long long* c32, uint64_t& bal,
+                                             uint64_t& unb) {
+  const int tid = threadIdx.x;
+  const int gl = tid & (G - 1);
+  const uint32_t gid = (uint32_t)tid / G;
+  constexpr uint32_t groups = kSweepThreads / G;
+  const unsigned lane = lane_id();
+  const unsigned gmask = G == 32 ? kFullMask : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+  const uint32_t lo2 = lo << 1;
+  for (uint32_t i = gid; i < q.L; i += groups) {
+    int64_t c = cur[2 * i];
+    const int64_t en = cur[2 * i + 1];
+    const uint32_t s1 = g.col[q.rb + i] & 1u;
+    for (;;) {
+      uint32_t x[kSweepUnroll];
+#pragma unroll
+      for (int u = 0; u < kSweepUnroll; u++) {
+        const int64_t pos = c + u * G + gl;
+        x[u] = pos < en ? g.col[pos] : 0xFFFFFFFFu;
+      }
+      int n_ok = 0;
+#pragma unroll
+      for (int u = 0; u < kSweepUnroll; u++) {
+        const bool ok = x[u] < hl;
+        if (ok) {
+          const bool sym = ((x[u] ^ s1) & 1u) == 0;
+          const uint32_t k = (x[u] - lo2) >> 1;
+          if (PACK16) {
+            sweep_contrib16(atomicAdd(&c16[k], sym ? 1u : 0x10000u), sym, bal, unb);
+          } else {
+            const unsigned long long inc = sym ? 1ull : (1ull << 32);
+            wedge_contrib(atomicAdd(&c32[k], inc), inc, bal, unb);
+          }
+        }
+        n_ok += __popc(__ballot_sync(gmask, ok));  // accepted entries are a prefix
+      }
+      c += n_ok;
+      if (n_ok < G * kSweepUnroll) break;
+    }
+    if (gl == 0) cur[2 * i] = c;
+  }
+}
+
+template <bool PACK16>
+__device__ __forceinline__ void sweep_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
+                                                      int64_t* cur, uint32_t lo, uint32_t hl, uint32_t* c16,
+                                                      unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
+  switch (group_log) {
+    case 0: sweep_window<1, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 2: sweep_window<4, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 3: sweep_window<8, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 4: sweep_window<16, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    default: sweep_window<32, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+  }
+}
+
+__global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
                                                                       int64_t n_items, int* next_item,
                                                                       int64_t* __restrict__ cursors, int64_t cur_cap,
                                                                       unsigned long long* out) {
@@ -246,7 +308,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) hub_sweep_kernel(CsrView g, 
   unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
   __shared__ int item_sh;
   const int tid = threadIdx.x;
-  for (int i = tid; i < kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
+  for (int i = tid; i < (int)kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
   int64_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
   uint64_t bal = 0, unb = 0;
   for (;;) {
@@ -282,27 +344,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1) hub_sweep_kernel(CsrView g, 
     for (uint32_t wdw = item.w0; wdw < item.w1; wdw++) {
       const uint32_t lo = wdw * H;
       const uint32_t hi = min(lo + H, sp);
-      const uint32_t hl = hi << 1;
-      const uint32_t lo2 = lo << 1;
-      for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
-        int64_t c = cur[2 * i];
-        const int64_t en = cur[2 * i + 1];
-        const uint32_t s1 = g.col[q.rb + i] & 1u;
-        while (c < en) {
-          const uint32_t x = g.col[c];
-          if (x >= hl) break;
-          const bool sym = ((x ^ s1) & 1u) == 0;
-          const uint32_t k = (x - lo2) >> 1;
-          if (pack16) {
-            sweep_contrib16(atomicAdd(&c16[k], sym ? 1u : 0x10000u), sym, bal, unb);
-          } else {
-            const unsigned long long inc = sym ? 1ull : (1ull << 32);
-            wedge_contrib(atomicAdd(&c32[k], inc), inc, bal, unb);
-          }
-          c++;
-        }
-        cur[2 * i] = c;
-      }
+      if (pack16) sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      else sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
       __syncthreads();
       const uint32_t words = pack16 ? (hi - lo) : 2 * (hi - lo);  // 32-bit words to clear
       for (uint32_t j = tid; j < words; j += kSweepThreads) c16[j] = 0u;
@@ -408,9 +451,9 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
     }
   }
   if (g->n_hub > 0) {
-    const int grid = sms;  // one 1024-thread CTA per SM (the window takes most of shared memory)
     const size_t smem = (size_t)kSweepWindow16 * 4;
     DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = sms * blocks_per_sm((const void*)hub_sweep_kernel, kSweepThreads, smem);
     int64_t* cursors = sc.get<int64_t>((size_t)grid * (size_t)g->sweep_max_lower * 2);
     int* next = sc.get<int>(1);
     DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));

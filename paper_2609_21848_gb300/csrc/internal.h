@@ -18,17 +18,42 @@ constexpr uint64_t kLightMaxWork = 512;    // warp per pivot, per-warp shared ha
 constexpr uint64_t kMediumMaxWork = 4096;  // CTA per pivot, shared hash (<= 8192 slots)
 constexpr int kLightSlots = 1024;
 constexpr int kMediumSlots = 8192;
-// Hub window sweep: shared-memory windows of side ranks (192 KB of counters).
-constexpr uint32_t kSweepWindow16 = 49152;  // 32-bit counters packing two 16-bit halves
-constexpr uint32_t kSweepWindow32 = 24576;  // 64-bit counters packing two 32-bit halves
+// Hub window sweep: shared-memory windows of side ranks (192 KB of counters
+// by default). Build-time overrides exist for tuning.
+#ifndef DBBC_SWEEP_WINDOW16
+#define DBBC_SWEEP_WINDOW16 49152
+#endif
+#ifndef DBBC_SWEEP_THREADS
+#define DBBC_SWEEP_THREADS 1024
+#endif
+#ifndef DBBC_SWEEP_UNROLL
+#define DBBC_SWEEP_UNROLL 2
+#endif
+constexpr uint32_t kSweepWindow16 = DBBC_SWEEP_WINDOW16;     // 32-bit counters packing two 16-bit halves
+constexpr uint32_t kSweepWindow32 = DBBC_SWEEP_WINDOW16 / 2;  // 64-bit counters packing two 32-bit halves
 constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per work item
+// mean (neighbour, window) segment length at which 32 / 16 / 8 / 4 lanes walk a segment
+#ifndef DBBC_GROUP_T32
+#define DBBC_GROUP_T32 40
+#endif
+#ifndef DBBC_GROUP_T16
+#define DBBC_GROUP_T16 16
+#endif
+#ifndef DBBC_GROUP_T8
+#define DBBC_GROUP_T8 6
+#endif
+#ifndef DBBC_GROUP_T4
+#define DBBC_GROUP_T4 2
+#endif
+constexpr double kGroupThreshold[4] = {DBBC_GROUP_T32, DBBC_GROUP_T16, DBBC_GROUP_T8, DBBC_GROUP_T4};
 
-// One unit of hub work: windows [w0, w1) of hub row `row`.
+// One unit of hub work: windows [w0, w1) of hub row `row`, each lower
+// neighbour's segment walked by 2^group_log lanes.
 struct SweepItem {
   int32_t row;
   uint32_t w0;
   uint32_t w1;
-  uint32_t pad;
+  int32_t group_log;
 };
 
 // Read-only view of the device CSR passed to kernels by value.
@@ -68,6 +93,8 @@ struct dbbc_graph {
   int32_t* order = nullptr;    // [n_piv] pivot rows, descending work: hubs | medium | light
   int64_t n_piv = 0, n_hub = 0, n_medium = 0, n_light = 0;
   uint64_t wedges = 0, wedges_hub = 0, wedges_medium = 0, wedges_light = 0;
+  int64_t lower_hub = 0, lower_medium = 0, lower_light = 0;
+  int64_t hub_cursor_inits = 0, hub_cursor_steps = 0;
   // hub plan: window-span items in descending estimated work
   dbbc::SweepItem* sweep_items = nullptr;
   int64_t n_sweep_items = 0;

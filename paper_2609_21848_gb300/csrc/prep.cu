@@ -48,7 +48,7 @@ __global__ void run_last_kernel(const uint64_t* __restrict__ key, int64_t m, uin
 __global__ void compact_edges_kernel(const uint64_t* __restrict__ key, const uint32_t* __restrict__ idx,
                                      const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
                                      const int8_t* __restrict__ sign, int64_t m, int bits_v,
-                                     int32_t* __restrict__ eu, int32_t* __restrict__ ev, uint8_t* __restrict__ eneg) {
+                                     int32_t* __restrict__ eu, int32_t* __restrict__ ev, int8_t* __restrict__ es) {
   const uint64_t mask_v = (bits_v >= 64) ? ~0ull : ((1ull << bits_v) - 1);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     if (!flag[i]) continue;
@@ -56,7 +56,7 @@ __global__ void compact_edges_kernel(const uint64_t* __restrict__ key, const uin
     const uint64_t k = key[i];
     eu[j] = (int32_t)(k >> bits_v);
     ev[j] = (int32_t)(k & mask_v);
-    eneg[j] = sign[idx[i]] < 0 ? 1 : 0;
+    es[j] = sign[idx[i]];
   }
 }
 
@@ -106,15 +106,24 @@ __global__ void ranks_kernel(const uint64_t* __restrict__ skey, int64_t n, int32
 
 // Two CSR entries per edge: key = (row << (bits_col + 1)) | (col << 1) | negative.
 __global__ void csr_keys_kernel(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-                                const uint8_t* __restrict__ eneg, int64_t m, int32_t n_u,
+                                const int8_t* __restrict__ es, int64_t m, int32_t n_u,
                                 const int32_t* __restrict__ side_rank, int bits_col, uint64_t* __restrict__ key) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t ru = (uint32_t)side_rank[eu[i]];
     const uint64_t rv = (uint32_t)side_rank[n_u + ev[i]];
-    const uint64_t neg = eneg[i];
+    const uint64_t neg = es[i] < 0 ? 1 : 0;
     key[2 * i] = (ru << (bits_col + 1)) | (rv << 1) | neg;
     key[2 * i + 1] = (((uint64_t)n_u + rv) << (bits_col + 1)) | (ru << 1) | neg;
   }
+}
+
+// Flags a repeated (row, neighbour) pair: sorted CSR keys that agree in
+// everything but the sign bit are adjacent.
+__global__ void adjacent_dup_kernel(const uint64_t* __restrict__ key, int64_t nnz, unsigned* dup) {
+  bool any = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < nnz; i += (int64_t)gridDim.x * blockDim.x)
+    any |= (key[i] >> 1) == (key[i + 1] >> 1);
+  if (__any_sync(kFullMask, any) && lane_id() == 0) atomicOr(dup, 1u);
 }
 
 __global__ void csr_cols_kernel(const uint64_t* __restrict__ key, int64_t nnz, int bits_col,
@@ -199,6 +208,7 @@ __global__ void work_kernel(const uint64_t* __restrict__ key, const int64_t* __r
 struct PrepStats {
   unsigned long long wedges, wedges_hub, wedges_medium, wedges_light, max_work;
   unsigned long long n_piv, n_hub, n_medium;
+  unsigned long long lower_hub, lower_medium, lower_light;
 };
 
 // Pivots that can close a butterfly: at least two lower neighbours and at
@@ -207,6 +217,7 @@ struct PrepStats {
 __global__ void pivot_flags_kernel(const uint64_t* __restrict__ work, const uint32_t* __restrict__ lower, int64_t n,
                                    uint32_t* __restrict__ flag, PrepStats* st) {
   uint64_t w_all = 0, w_hub = 0, w_med = 0, w_light = 0, mx = 0, np = 0, nh = 0, nm = 0;
+  uint64_t l_hub = 0, l_med = 0, l_light = 0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t w = work[r];
     w_all += w;
@@ -215,9 +226,10 @@ __global__ void pivot_flags_kernel(const uint64_t* __restrict__ work, const uint
     if (piv) {
       np++;
       mx = w > mx ? w : mx;
-      if (w > kMediumMaxWork) { nh++; w_hub += w; }
-      else if (w > kLightMaxWork) { nm++; w_med += w; }
-      else w_light += w;
+      const uint64_t L = lower[r];
+      if (w > kMediumMaxWork) { nh++; w_hub += w; l_hub += L; }
+      else if (w > kLightMaxWork) { nm++; w_med += w; l_med += L; }
+      else { w_light += w; l_light += L; }
     }
   }
   w_all = warp_sum_u64(w_all);
@@ -227,6 +239,9 @@ __global__ void pivot_flags_kernel(const uint64_t* __restrict__ work, const uint
   np = warp_sum_u64(np);
   nh = warp_sum_u64(nh);
   nm = warp_sum_u64(nm);
+  l_hub = warp_sum_u64(l_hub);
+  l_med = warp_sum_u64(l_med);
+  l_light = warp_sum_u64(l_light);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const uint64_t y = __shfl_xor_sync(kFullMask, mx, o);
@@ -241,6 +256,9 @@ __global__ void pivot_flags_kernel(const uint64_t* __restrict__ work, const uint
     if (np) atomicAdd(&st->n_piv, (unsigned long long)np);
     if (nh) atomicAdd(&st->n_hub, (unsigned long long)nh);
     if (nm) atomicAdd(&st->n_medium, (unsigned long long)nm);
+    if (l_hub) atomicAdd(&st->lower_hub, (unsigned long long)l_hub);
+    if (l_med) atomicAdd(&st->lower_medium, (unsigned long long)l_med);
+    if (l_light) atomicAdd(&st->lower_light, (unsigned long long)l_light);
   }
 }
 
@@ -334,14 +352,25 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
     const uint64_t target = std::max<uint64_t>(kSweepItemWork, 64ull * L);
     uint64_t spans = std::max<uint64_t>(1, std::min<uint64_t>(R, W / target));
     max_lower = std::max<int64_t>(max_lower, L);
+    // lanes per (neighbour, window) segment from the hub's mean segment length
+    const double density = (double)W / ((double)L * (double)R);
+    const int32_t group_log = density >= kGroupThreshold[0]   ? 5
+                              : density >= kGroupThreshold[1] ? 4
+                              : density >= kGroupThreshold[2] ? 3
+                              : density >= kGroupThreshold[3] ? 2
+                                                              : 0;
     for (uint64_t k = 0; k < spans; k++) {
       Planned p;
       p.it.row = row;
       p.it.w0 = (uint32_t)(R * k / spans);
       p.it.w1 = (uint32_t)(R * (k + 1) / spans);
-      p.it.pad = 0;
+      p.it.group_log = group_log;
       p.est = W / spans;
-      if (p.it.w1 > p.it.w0) plan.push_back(p);
+      if (p.it.w1 > p.it.w0) {
+        plan.push_back(p);
+        g->hub_cursor_inits += L;
+        g->hub_cursor_steps += (int64_t)L * (p.it.w1 - p.it.w0);
+      }
     }
   }
   std::stable_sort(plan.begin(), plan.end(), [](const Planned& a, const Planned& b) { return a.est > b.est; });
@@ -388,16 +417,68 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
     if (read_back(d_flags, s) != 0) throw Error{DBBC_EINVAL, "invalid edge id or sign"};
   }
 
-  // ---- a1: keep-latest deduplication (stable sort on (u, v))
   const int bits_u = bits_for(n_u > 0 ? (uint64_t)(n_u - 1) : 0);
   const int bits_v = bits_for(n_v > 0 ? (uint64_t)(n_v - 1) : 0);
-  int32_t* eu = nullptr;
-  int32_t* ev = nullptr;
-  uint8_t* eneg = nullptr;
-  int64_t mu = 0;
-  if (m > 0) {
-    uint64_t* k0 = sc.get<uint64_t>((size_t)m);
-    uint64_t* k1 = sc.get<uint64_t>((size_t)m);
+  const int64_t max_side = std::max<int64_t>(n_u, n_v);
+  const int bits_id = std::max(1, bits_for(max_side > 0 ? (uint64_t)(max_side - 1) : 0));
+  const int bits_deg = std::max(1, bits_for((uint64_t)max_side));
+  const int bits_col = bits_id;
+  const int bits_row = std::max(1, bits_for(n > 0 ? (uint64_t)(n - 1) : 0));
+  if (bits_row + bits_col + 1 > 64) throw Error{DBBC_EINVAL, "graph too large for 64-bit CSR keys"};
+  int32_t* deg = sc.get<int32_t>((size_t)n);
+  int32_t* side_rank = sc.get<int32_t>((size_t)n);
+  int32_t* rowdeg = sc.get<int32_t>((size_t)n);
+  uint64_t* vk0 = sc.get<uint64_t>((size_t)n);
+  uint64_t* vk1 = sc.get<uint64_t>((size_t)n);
+  uint64_t* ck0 = sc.get<uint64_t>((size_t)(2 * m));
+  uint64_t* ck1 = sc.get<uint64_t>((size_t)(2 * m));
+  g->vertex = static_cast<int32_t*>(graph_alloc(g, (size_t)n * 4));
+  g->row_ptr = static_cast<int64_t*>(graph_alloc(g, (size_t)(n + 1) * 8));
+
+  // a2 + a3 for an edge list: degrees, Def. 3 ranks per side, CSR keys
+  // sorted by (row, neighbour priority) with the sign in bit 0. Returns the
+  // sorted keys and whether any (u, v) pair occurs twice (adjacent keys).
+  auto csr_from_edges = [&](const int32_t* eu, const int32_t* ev, const int8_t* es, int64_t me,
+                            bool* dup) -> uint64_t* {
+    DBBC_CUDA(cudaMemsetAsync(deg, 0, (size_t)n * 4, s));
+    if (me > 0) {
+      degree_kernel<<<grid_for(me), 256, 0, s>>>(eu, ev, me, n_u, deg);
+      DBBC_LAUNCH_CHECK();
+    }
+    if (n > 0) {
+      vertex_keys_kernel<<<grid_for(n), 256, 0, s>>>(deg, n, n_u, bits_deg, bits_id, vk0);
+      DBBC_LAUNCH_CHECK();
+      const bool alt = radix_sort<uint64_t, uint32_t, false>(vk0, vk1, nullptr, nullptr, n, 0,
+                                                             1 + bits_deg + bits_id, s, sc);
+      ranks_kernel<<<grid_for(n), 256, 0, s>>>(alt ? vk1 : vk0, n, n_u, bits_deg, bits_id, g->vertex, side_rank,
+                                               rowdeg);
+      DBBC_LAUNCH_CHECK();
+    }
+    *dup = false;
+    if (me == 0) return ck0;
+    csr_keys_kernel<<<grid_for(me), 256, 0, s>>>(eu, ev, es, me, n_u, side_rank, bits_col, ck0);
+    DBBC_LAUNCH_CHECK();
+    // the sort skips bit 0 (the sign), so repeated pairs stay in input order
+    const bool alt = radix_sort<uint64_t, uint32_t, false>(ck0, ck1, nullptr, nullptr, 2 * me, 1,
+                                                           bits_row + bits_col + 1, s, sc);
+    uint64_t* ck = alt ? ck1 : ck0;
+    DBBC_CUDA(cudaMemsetAsync(d_flags + 3, 0, sizeof(unsigned), s));
+    adjacent_dup_kernel<<<grid_for(2 * me), 256, 0, s>>>(ck, 2 * me, d_flags + 3);
+    DBBC_LAUNCH_CHECK();
+    *dup = read_back(d_flags + 3, s) != 0;
+    return ck;
+  };
+
+  // ---- a1-a3: build straight from the input; only when some (u, v) pair
+  // repeats, drop all but its latest occurrence (stable sort on (u, v), keep
+  // the last of every run) and build again from the distinct edges.
+  bool dup = false;
+  int64_t mu = m;
+  uint64_t* ck = csr_from_edges(du, dv, ds, m, &dup);
+  if (dup) {
+    if (reject_duplicates) throw Error{DBBC_EINVAL, "duplicate edge under DBBC_DUP_REJECT"};
+    uint64_t* k0 = ck0;  // reuse the CSR key buffers (2m entries each) for the (u, v) sort
+    uint64_t* k1 = ck1;
     uint32_t* i0 = sc.get<uint32_t>((size_t)m);
     uint32_t* i1 = sc.get<uint32_t>((size_t)m);
     edge_keys_kernel<<<grid_for(m), 256, 0, s>>>(du, dv, m, bits_v, k0, i0);
@@ -410,65 +491,23 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
     run_last_kernel<<<grid_for(m), 256, 0, s>>>(ks, m, flag, d_flags + 1);
     DBBC_LAUNCH_CHECK();
     exclusive_scan<uint32_t, uint32_t>(flag, pos, m, s, sc, reinterpret_cast<uint32_t*>(d_flags + 2));
-    unsigned hf[4];
-    DBBC_CUDA(cudaMemcpyAsync(hf, d_flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
-    DBBC_CUDA(cudaStreamSynchronize(s));
-    if (reject_duplicates && hf[1]) throw Error{DBBC_EINVAL, "duplicate edge under DBBC_DUP_REJECT"};
-    mu = hf[2];
-    eu = sc.get<int32_t>((size_t)mu);
-    ev = sc.get<int32_t>((size_t)mu);
-    eneg = sc.get<uint8_t>((size_t)mu);
-    compact_edges_kernel<<<grid_for(m), 256, 0, s>>>(ks, is, flag, pos, ds, m, bits_v, eu, ev, eneg);
+    mu = read_back(d_flags + 2, s);
+    int32_t* eu = sc.get<int32_t>((size_t)mu);
+    int32_t* ev = sc.get<int32_t>((size_t)mu);
+    int8_t* es = sc.get<int8_t>((size_t)mu);
+    compact_edges_kernel<<<grid_for(m), 256, 0, s>>>(ks, is, flag, pos, ds, m, bits_v, eu, ev, es);
     DBBC_LAUNCH_CHECK();
+    ck = csr_from_edges(eu, ev, es, mu, &dup);
+    if (dup) throw Error{DBBC_EINTERNAL, "duplicates left after deduplication"};
   }
   g->m = mu;
   g->nnz = 2 * mu;
-
-  // ---- a2: degrees and Def. 3 ranks per side
-  int32_t* deg = sc.get<int32_t>((size_t)n);
-  DBBC_CUDA(cudaMemsetAsync(deg, 0, (size_t)n * 4, s));
-  if (mu > 0) {
-    degree_kernel<<<grid_for(mu), 256, 0, s>>>(eu, ev, mu, n_u, deg);
-    DBBC_LAUNCH_CHECK();
-  }
-  const int64_t max_side = std::max<int64_t>(n_u, n_v);
-  const int bits_id = std::max(1, bits_for(max_side > 0 ? (uint64_t)(max_side - 1) : 0));
-  const int bits_deg = std::max(1, bits_for((uint64_t)max_side));
-  int32_t* side_rank = sc.get<int32_t>((size_t)n);
-  int32_t* rowdeg = sc.get<int32_t>((size_t)n);
-  g->vertex = static_cast<int32_t*>(graph_alloc(g, (size_t)n * 4));
-  if (n > 0) {
-    uint64_t* vk0 = sc.get<uint64_t>((size_t)n);
-    uint64_t* vk1 = sc.get<uint64_t>((size_t)n);
-    vertex_keys_kernel<<<grid_for(n), 256, 0, s>>>(deg, n, n_u, bits_deg, bits_id, vk0);
-    DBBC_LAUNCH_CHECK();
-    const bool alt = radix_sort<uint64_t, uint32_t, false>(vk0, vk1, nullptr, nullptr, n, 0, 1 + bits_deg + bits_id,
-                                                           s, sc);
-    ranks_kernel<<<grid_for(n), 256, 0, s>>>(alt ? vk1 : vk0, n, n_u, bits_deg, bits_id, g->vertex, side_rank,
-                                             rowdeg);
-    DBBC_LAUNCH_CHECK();
-  }
-
-  // ---- a3: CSR sorted by (row, priority of neighbour), sign in bit 0
-  g->row_ptr = static_cast<int64_t*>(graph_alloc(g, (size_t)(n + 1) * 8));
   g->col = static_cast<uint32_t*>(graph_alloc(g, (size_t)g->nnz * 4));
   g->lower = static_cast<uint32_t*>(graph_alloc(g, (size_t)n * 4));
   g->work = static_cast<uint64_t*>(graph_alloc(g, (size_t)n * 8));
   exclusive_scan<int32_t, int64_t>(rowdeg, g->row_ptr, n, s, sc, g->row_ptr + n);
   DBBC_CUDA(cudaMemsetAsync(g->work, 0, (size_t)n * 8, s));
-  const int bits_col = bits_id;
-  const int bits_row = std::max(1, bits_for(n > 0 ? (uint64_t)(n - 1) : 0));
-  if (bits_row + bits_col + 1 > 64) throw Error{DBBC_EINVAL, "graph too large for 64-bit CSR keys"};
-  uint64_t* ck = nullptr;
   if (g->nnz > 0) {
-    uint64_t* ck0 = sc.get<uint64_t>((size_t)g->nnz);
-    uint64_t* ck1 = sc.get<uint64_t>((size_t)g->nnz);
-    csr_keys_kernel<<<grid_for(mu), 256, 0, s>>>(eu, ev, eneg, mu, n_u, side_rank, bits_col, ck0);
-    DBBC_LAUNCH_CHECK();
-    // neighbours are unique within a row, so bit 0 (the sign) needs no sorting
-    const bool alt = radix_sort<uint64_t, uint32_t, false>(ck0, ck1, nullptr, nullptr, g->nnz, 1,
-                                                           bits_row + bits_col + 1, s, sc);
-    ck = alt ? ck1 : ck0;
     csr_cols_kernel<<<grid_for(g->nnz), 256, 0, s>>>(ck, g->nnz, bits_col, g->col);
     DBBC_LAUNCH_CHECK();
   }
@@ -499,6 +538,9 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
   g->n_hub = (int64_t)st.n_hub;
   g->n_medium = (int64_t)st.n_medium;
   g->n_light = g->n_piv - g->n_hub - g->n_medium;
+  g->lower_hub = (int64_t)st.lower_hub;
+  g->lower_medium = (int64_t)st.lower_medium;
+  g->lower_light = (int64_t)st.lower_light;
   g->order = static_cast<int32_t*>(graph_alloc(g, (size_t)std::max<int64_t>(g->n_piv, 1) * 4));
   if (g->n_piv > 0) {
     uint32_t* ppos = sc.get<uint32_t>((size_t)n);
