@@ -106,6 +106,26 @@ DBBC_API dbbc_status dbbc_count_profiled(const dbbc_graph* g, void* cuda_stream,
  * (graph builds and counts). */
 DBBC_API uint64_t dbbc_kernel_launches(void);
 
+/* Counting without allocating device memory, for callers that cannot call
+ * cudaMalloc while they count (a fixed device-memory budget held by another
+ * allocator, work that must not touch the device allocator, set-up-once
+ * hosts). The paper has no counterpart; this is a deployment entry point.
+ *   d_out : DEVICE array of two uint64 {balanced, unbalanced}, written in
+ *           stream order; the call returns after enqueueing (like
+ *           dbbc_count_async, device-side status bits are not reported).
+ * Scratch comes from one fixed 32 MiB array inside the library, held on
+ * every GPU that loads the library until the process exits. The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress),
+ * so make the first call on each device before any stream capture. All calls
+ * share the array and it keeps the previous call's contents (the parts that
+ * must start at zero are cleared by each call); calls that overlap on the GPU,
+ * on any streams, race on it, so serialize them. Graphs whose largest hub
+ * needs more cursor scratch than the array holds (16 bytes per lower
+ * neighbour of that hub for even one CTA) are rejected with DBBC_EOVERFLOW;
+ * below that limit fewer CTAs run the hub tier when the array cannot hold
+ * cursors for all of them. */
+DBBC_API dbbc_status dbbc_count_noalloc(const dbbc_graph* g, void* cuda_stream, uint64_t* d_out);
+
 /* Count several resident graphs in one launch sequence. balanced[i] and
  * unbalanced[i] (host arrays of n_graphs entries) receive graph i's counts.
  * Synchronous. */

@@ -30,7 +30,7 @@ EXPORTED = (
     "dbbc_graph_from_coo", "dbbc_count", "dbbc_count_async", "dbbc_count_batch", "dbbc_count_batch_async",
     "dbbc_graph_get_info", "dbbc_graph_device_bytes", "dbbc_estimate_bytes", "dbbc_graph_free",
     "dbbc_graph_export", "dbbc_set_allocator", "dbbc_status_string", "dbbc_version", "dbbc_count_profiled",
-    "dbbc_kernel_launches",
+    "dbbc_kernel_launches", "dbbc_count_noalloc",
 )
 
 
@@ -88,6 +88,8 @@ def lib() -> ctypes.CDLL:
         L.dbbc_count_profiled.restype = st
         L.dbbc_kernel_launches.argtypes = []
         L.dbbc_kernel_launches.restype = ctypes.c_uint64
+        L.dbbc_count_noalloc.argtypes = [P, P, P]
+        L.dbbc_count_noalloc.restype = st
         L.dbbc_count_async.argtypes = [P, P, P]
         L.dbbc_count_async.restype = st
         L.dbbc_count_batch.argtypes = [P, I32, P, P, P]
@@ -215,6 +217,13 @@ def dbbc_count_profiled(g: Graph, stream=None) -> tuple[int, int, dict]:
 def dbbc_kernel_launches() -> int:
     """Kernels the library has launched in this process."""
     return int(lib().dbbc_kernel_launches())
+
+
+def dbbc_count_noalloc(g: Graph, d_out, stream=None) -> None:
+    """Enqueue a count that allocates no device memory (scratch comes from a
+    fixed array inside the library; see dbbc.h). ``d_out``: device tensor of
+    at least 2 x 64-bit. Calls must not overlap on the GPU."""
+    _check(lib().dbbc_count_noalloc(g.handle, _stream_ptr(stream), d_out.data_ptr()), "dbbc_count_noalloc")
 
 
 def dbbc_count_async(g: Graph, d_out, stream=None) -> None:

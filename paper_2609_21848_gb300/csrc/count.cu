@@ -470,3 +470,54 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
 }
 
 }  // namespace dbbc
+
+namespace dbbc {
+
+// The kernels of enqueue_count with all device scratch supplied by the caller:
+// d_status (one word) and d_next (one int) are cleared here, and the hub
+// sweep keeps its per-CTA cursors in `cursors` (cursor_bytes long), which
+// bounds how many CTAs it can run. Throws DBBC_EOVERFLOW when not even one
+// CTA's cursors fit.
+void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_out, unsigned* d_status,
+                            int* d_next, int64_t* cursors, size_t cursor_bytes) {
+  DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
+  DBBC_CUDA(cudaMemsetAsync(d_out, 0, 2 * sizeof(unsigned long long), s));
+  if (g->n_piv == 0) return;
+  const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
+  const int sms = num_sms();
+  int64_t hub_grid = 0;
+  if (g->n_hub > 0) {
+    const size_t per_cta = (size_t)g->sweep_max_lower * 2 * sizeof(int64_t);
+    hub_grid = (int64_t)(cursor_bytes / per_cta);
+    if (hub_grid < 1) throw Error{DBBC_EOVERFLOW, "hub cursors exceed the fixed scratch"};
+  }
+  if (g->n_light > 0) {
+    const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
+    DBBC_CUDA(cudaFuncSetAttribute(count_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
+    const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_light_kernel, kLightWarps * 32, smem);
+    count_light_kernel<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
+        view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, d_out, d_status);
+    DBBC_LAUNCH_CHECK();
+  }
+  if (g->n_medium > 0) {
+    const size_t smem = (size_t)kMediumSlots * 12;
+    DBBC_CUDA(cudaFuncSetAttribute(count_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_medium_kernel, kMediumThreads, smem);
+    count_medium_kernel<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
+        view, g->order + g->n_hub, g->work, g->n_medium, d_out, d_status);
+    DBBC_LAUNCH_CHECK();
+  }
+  if (g->n_hub > 0) {
+    const size_t smem = (size_t)kSweepWindow16 * 4;
+    DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t full = (int64_t)sms * blocks_per_sm((const void*)hub_sweep_kernel, kSweepThreads, smem);
+    const int grid = (int)std::min<int64_t>(full, hub_grid);
+    DBBC_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
+    hub_sweep_kernel<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, d_next, cursors,
+                                                       g->sweep_max_lower, d_out);
+    DBBC_LAUNCH_CHECK();
+  }
+}
+
+}  // namespace dbbc

@@ -133,4 +133,8 @@ struct CountProfiler {
 void enqueue_count(const dbbc_graph* g, cudaStream_t stream, unsigned long long* d_out, unsigned* d_status,
                    Scratch& scratch, CountProfiler* prof = nullptr);
 
+// count.cu: the same kernels with caller-supplied scratch (see noalloc.cu).
+void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t stream, unsigned long long* d_out, unsigned* d_status,
+                            int* d_next, int64_t* cursors, size_t cursor_bytes);
+
 }  // namespace dbbc
