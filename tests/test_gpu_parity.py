@@ -227,10 +227,26 @@ def test_chunglu_1m_200k_20m_full_size():
     assert_parity(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)
 
 
+def _expected(name):
+    from conftest import GOLDEN
+    for line in open(os.path.join(GOLDEN, "expected_counts.txt")):
+        f = line.split("#", 1)[0].split()
+        if len(f) == 4 and f[0] == name:
+            return tuple(int(x) for x in f[1:])
+    return None
+
+
+def test_chunglu_full_size_matches_stored_oracle_counts():
+    g = synth.workload("chunglu-1m-200k-20m")
+    bal, unb, info = gpu_count(g.u, g.v, g.s, g.n_u, g.n_v)
+    assert (bal, unb, info["wedges"]) == _expected("chunglu-1m-200k-20m")
+
+
 def test_invariants_at_full_size_polarized():
-    """Properties that hold at any size, on the 300M-edge polarized graph:
-    balanced + unbalanced equals the unsigned count, and switching (negating
-    every edge at a random vertex set) changes neither count."""
+    """The 300M-edge polarized graph: the counts equal the oracle's (stored by
+    tests/golden/make_expected.py); balanced + unbalanced equals the unsigned
+    count; switching (negating every edge at a random vertex set) changes
+    neither count."""
     if os.environ.get("DBBC_SKIP_HUGE"):
         pytest.skip("DBBC_SKIP_HUGE set")
     import torch
@@ -240,6 +256,7 @@ def test_invariants_at_full_size_polarized():
     with dbbc.dbbc_graph_from_coo(u, v, s, g.n_u, g.n_v) as h:
         bal, unb = dbbc.dbbc_count(h)
         wedges = h.info["wedges"]
+    assert (bal, unb, wedges) == _expected("polarized-20m-2m-300m")
     with dbbc.dbbc_graph_from_coo(u, v, torch.ones_like(s), g.n_u, g.n_v) as h:
         assert dbbc.dbbc_count(h) == (bal + unb, 0)
     rng = np.random.default_rng(3)
