@@ -252,10 +252,24 @@ __device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& 
   const unsigned lane = lane_id();
   const unsigned gmask = G == 32 ? kFullMask : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
   const uint32_t lo2 = lo << 1;
+  // the next neighbour's cursor and edge sign are loaded while this one is walked
+  int64_t c_nx = 0, en_nx = 0;
+  uint32_t s1_nx = 0;
+  if (gid < q.L) {
+    c_nx = cur[2 * gid];
+    en_nx = cur[2 * gid + 1];
+    s1_nx = g.col[q.rb + gid] & 1u;
+  }
   for (uint32_t i = gid; i < q.L; i += groups) {
-    int64_t c = cur[2 * i];
-    const int64_t en = cur[2 * i + 1];
-    const uint32_t s1 = g.col[q.rb + i] & 1u;
+    int64_t c = c_nx;
+    const int64_t en = en_nx;
+    const uint32_t s1 = s1_nx;
+    const uint32_t i_nx = i + groups;
+    if (i_nx < q.L) {
+      c_nx = cur[2 * i_nx];
+      en_nx = cur[2 * i_nx + 1];
+      s1_nx = g.col[q.rb + i_nx] & 1u;
+    }
     for (;;) {
       uint32_t x[kSweepUnroll];
 #pragma unroll
@@ -319,11 +333,10 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     if (it >= n_items) break;
     const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    const uint32_t sp = q.lim >> 1;
-    const bool pack16 = q.L < 65536u;
-    const uint32_t H = pack16 ? kSweepWindow16 : kSweepWindow32;
-    // cursors: first entry at or after the span's first window, and row end
-    const uint32_t first = (uint32_t)((uint64_t)item.w0 * H) << 1;
+    const bool wide = item.wide != 0;
+    const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
+    // cursors: first entry at or after rank item.lo, and the row end
+    const uint32_t first = item.lo << 1;
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       const uint32_t e = g.col[q.rb + i];
       const int64_t vrow = q.base + (e >> 1);
@@ -341,13 +354,12 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
       cur[2 * i + 1] = en;
     }
     __syncthreads();
-    for (uint32_t wdw = item.w0; wdw < item.w1; wdw++) {
-      const uint32_t lo = wdw * H;
-      const uint32_t hi = min(lo + H, sp);
-      if (pack16) sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      else sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+    for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
+      const uint32_t hi = min(lo + H, item.hi);
+      if (wide) sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      else sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
       __syncthreads();
-      const uint32_t words = pack16 ? (hi - lo) : 2 * (hi - lo);  // 32-bit words to clear
+      const uint32_t words = wide ? 2 * (hi - lo) : (hi - lo);  // 32-bit words to clear
       for (uint32_t j = tid; j < words; j += kSweepThreads) c16[j] = 0u;
       __syncthreads();
     }

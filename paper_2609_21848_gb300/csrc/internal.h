@@ -18,10 +18,10 @@ constexpr uint64_t kLightMaxWork = 512;    // warp per pivot, per-warp shared ha
 constexpr uint64_t kMediumMaxWork = 4096;  // CTA per pivot, shared hash (<= 8192 slots)
 constexpr int kLightSlots = 1024;
 constexpr int kMediumSlots = 8192;
-// Hub window sweep: shared-memory windows of side ranks (192 KB of counters
+// Hub window sweep: shared-memory windows of side ranks (224 KB of counters
 // by default). Build-time overrides exist for tuning.
 #ifndef DBBC_SWEEP_WINDOW16
-#define DBBC_SWEEP_WINDOW16 49152
+#define DBBC_SWEEP_WINDOW16 57344
 #endif
 #ifndef DBBC_SWEEP_THREADS
 #define DBBC_SWEEP_THREADS 1024
@@ -47,13 +47,20 @@ constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per wor
 #endif
 constexpr double kGroupThreshold[4] = {DBBC_GROUP_T32, DBBC_GROUP_T16, DBBC_GROUP_T8, DBBC_GROUP_T4};
 
-// One unit of hub work: windows [w0, w1) of hub row `row`, each lower
-// neighbour's segment walked by 2^group_log lanes.
+// Counts below this fit the 16-bit halves of a narrow counter.
+constexpr int32_t kNarrowCountLimit = 65536;
+
+// One unit of hub work: endpoints with side ranks [lo, hi) of hub row `row`,
+// swept in windows of kSweepWindow16 (narrow: 16-bit halves) or
+// kSweepWindow32 (wide: 32-bit halves) ranks, each lower neighbour's segment
+// walked by 2^group_log lanes. A count never exceeds the endpoint's degree,
+// so only ranges holding endpoints of degree >= 2^16 need wide counters.
 struct SweepItem {
   int32_t row;
-  uint32_t w0;
-  uint32_t w1;
-  int32_t group_log;
+  uint32_t lo;
+  uint32_t hi;
+  int16_t group_log;
+  int16_t wide;
 };
 
 // Read-only view of the device CSR passed to kernels by value.
@@ -99,6 +106,7 @@ struct dbbc_graph {
   dbbc::SweepItem* sweep_items = nullptr;
   int64_t n_sweep_items = 0;
   int64_t sweep_max_lower = 0;  // largest lower-neighbour count of a hub (cursor scratch per CTA)
+  int64_t narrow_ranks_u = 0, narrow_ranks_v = 0;  // per side: vertices of degree < 2^16 (a rank prefix)
   size_t device_bytes = 0;
   std::vector<void*> allocations;
 };

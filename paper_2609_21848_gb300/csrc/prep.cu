@@ -275,6 +275,12 @@ __global__ void pivot_keys_kernel(const uint64_t* __restrict__ work, const uint3
   }
 }
 
+__global__ void narrow_ranks_kernel(const int32_t* __restrict__ rowdeg, int64_t n, int32_t n_u, int32_t limit,
+                                    int64_t* out) {
+  if (threadIdx.x == 0) out[0] = lower_bound_dev<int32_t>(rowdeg, n_u, limit);
+  if (threadIdx.x == 1) out[1] = lower_bound_dev<int32_t>(rowdeg + n_u, n - n_u, limit);
+}
+
 __global__ void gather_u32_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n,
                                   uint32_t* __restrict__ dst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -333,9 +339,12 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
     DBBC_CUDA(cudaMemcpyAsync(works.data(), d_work, works.size() * 8, cudaMemcpyDeviceToHost, s));
     DBBC_CUDA(cudaStreamSynchronize(s));
   }
-  // Split each hub's windows into spans of roughly equal work; a span that
-  // does not start at window 0 pays one binary search per lower neighbour, so
-  // spans are kept large against the hub's lower-neighbour count.
+  // Split each hub's accepted ranks [0, sp) into items of roughly equal work.
+  // Ranks below the side's first endpoint of degree >= 2^16 use narrow
+  // counters (16-bit halves) unless the hub has < 2^16 lower neighbours, in
+  // which case every count fits 16 bits. An item that does not start at rank
+  // 0 pays one binary search per lower neighbour, so items stay large against
+  // the hub's lower-neighbour count.
   struct Planned {
     SweepItem it;
     uint64_t est;
@@ -346,32 +355,41 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
     const int32_t row = (int32_t)rows[h];
     const uint32_t L = lows[h];
     const uint64_t W = works[h];
-    const uint64_t sp = row < g->n_u ? (uint64_t)row : (uint64_t)(row - g->n_u);
-    const uint64_t H = L < 65536u ? kSweepWindow16 : kSweepWindow32;
-    const uint64_t R = (sp + H - 1) / H;
+    const bool is_u = row < g->n_u;
+    const uint64_t sp = is_u ? (uint64_t)row : (uint64_t)(row - g->n_u);
+    const uint64_t narrow_end =
+        L < (uint32_t)kNarrowCountLimit ? sp : std::min<uint64_t>(sp, (uint64_t)(is_u ? g->narrow_ranks_u
+                                                                                        : g->narrow_ranks_v));
+    const uint64_t Rn = (narrow_end + kSweepWindow16 - 1) / kSweepWindow16;
+    const uint64_t Rw = (sp - narrow_end + kSweepWindow32 - 1) / kSweepWindow32;
     const uint64_t target = std::max<uint64_t>(kSweepItemWork, 64ull * L);
-    uint64_t spans = std::max<uint64_t>(1, std::min<uint64_t>(R, W / target));
     max_lower = std::max<int64_t>(max_lower, L);
     // lanes per (neighbour, window) segment from the hub's mean segment length
-    const double density = (double)W / ((double)L * (double)R);
-    const int32_t group_log = density >= kGroupThreshold[0]   ? 5
+    const double density = (double)W / ((double)L * (double)std::max<uint64_t>(1, Rn + Rw));
+    const int16_t group_log = density >= kGroupThreshold[0]   ? 5
                               : density >= kGroupThreshold[1] ? 4
                               : density >= kGroupThreshold[2] ? 3
                               : density >= kGroupThreshold[3] ? 2
                                                               : 0;
-    for (uint64_t k = 0; k < spans; k++) {
+    auto add = [&](uint64_t lo, uint64_t hi, uint64_t H, int16_t wide, uint64_t est) {
       Planned p;
       p.it.row = row;
-      p.it.w0 = (uint32_t)(R * k / spans);
-      p.it.w1 = (uint32_t)(R * (k + 1) / spans);
+      p.it.lo = (uint32_t)lo;
+      p.it.hi = (uint32_t)hi;
       p.it.group_log = group_log;
-      p.est = W / spans;
-      if (p.it.w1 > p.it.w0) {
-        plan.push_back(p);
-        g->hub_cursor_inits += L;
-        g->hub_cursor_steps += (int64_t)L * (p.it.w1 - p.it.w0);
-      }
+      p.it.wide = wide;
+      p.est = est;
+      plan.push_back(p);
+      g->hub_cursor_inits += L;
+      g->hub_cursor_steps += (int64_t)L * (int64_t)((hi - lo + H - 1) / H);
+    };
+    const uint64_t spans = std::max<uint64_t>(1, std::min<uint64_t>(Rn, W / target));
+    for (uint64_t k = 0; k < spans && Rn > 0; k++) {
+      const uint64_t w0 = Rn * k / spans, w1 = Rn * (k + 1) / spans;
+      if (w1 > w0) add(w0 * kSweepWindow16, std::min<uint64_t>(narrow_end, w1 * kSweepWindow16), kSweepWindow16, 0,
+                       W / spans);
     }
+    if (sp > narrow_end) add(narrow_end, sp, kSweepWindow32, 1, W / (spans + 1));
   }
   std::stable_sort(plan.begin(), plan.end(), [](const Planned& a, const Planned& b) { return a.est > b.est; });
   std::vector<SweepItem> items(plan.size());
@@ -555,6 +573,17 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
     const bool alt = radix_sort<uint64_t, uint32_t, true>(pk0, pk1, pr0, pr1, g->n_piv, 0, wbits, s, sc);
     if (alt)
       DBBC_CUDA(cudaMemcpyAsync(pr0, pr1, (size_t)g->n_piv * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  // per side: how many vertices have degree < 2^16 (ranks ascend by degree)
+  {
+    int64_t* d_t = sc.get<int64_t>(2);
+    narrow_ranks_kernel<<<1, 32, 0, s>>>(rowdeg, n, n_u, kNarrowCountLimit, d_t);
+    DBBC_LAUNCH_CHECK();
+    int64_t ht[2];
+    DBBC_CUDA(cudaMemcpyAsync(ht, d_t, sizeof(ht), cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaStreamSynchronize(s));
+    g->narrow_ranks_u = ht[0];
+    g->narrow_ranks_v = ht[1];
   }
   plan_hubs(g, s);
   DBBC_CUDA(cudaStreamSynchronize(s));
