@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dbbc", "reference"], default="dbbc")
-    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS) + ["batch-4096"])
+    ap.add_argument("--n-graphs", type=int, default=4096, help="graphs in the batch-4096 workload")
     ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the host-buffer end-to-end timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -149,8 +150,36 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    g = synth.workload(a.workload)
     nc = cores()
+    if a.workload == "batch-4096":
+        # graphs of the batch counted one after another by the oracle; each
+        # step a bounded sample of consecutive graphs (about 2 minutes overall)
+        per_step = 120.0 / max(1, a.steps + a.warmup)
+        graphs = [synth.batch_graph(i) for i in range(min(a.n_graphs, 512))]
+        k = 0
+        done, t_total = 0, 0.0
+        for step in range(a.warmup + a.steps):
+            t0 = time.perf_counter()
+            n_step = 0
+            while time.perf_counter() - t0 < per_step:
+                g = graphs[k % len(graphs)]
+                oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=nc)
+                k += 1
+                n_step += 1
+            if step >= a.warmup:
+                done += n_step
+                t_total += time.perf_counter() - t0
+        value = done / t_total
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": a.gpus,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_total / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+                "data": "synthetic", "config": {"workload": "batch-4096", "parallelism": "host threads"},
+                "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": nc, "kind": "oracle",
+                                 "sample": f"{done} batch graphs counted one after another, {nc} threads"},
+                "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    g = synth.workload(a.workload)
     t0 = time.perf_counter()
     bg = oracle.BuiltGraph(g.u, g.v, g.s, g.n_u, g.n_v)
     build_s = time.perf_counter() - t0
@@ -201,6 +230,125 @@ def cpu_baseline(g, target_s: float) -> dict:
                       f"{nc} threads; oracle graph build {build_s:.1f} s untimed)"}
 
 
+def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
+    """The batched form: thousands of uneven resident graphs counted by one
+    replayed CUDA graph (three kernels for all graphs), against the plain path
+    of one synchronous count (one launch sequence) per graph. Metric: graphs/s."""
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    graphs = synth.batch(a.n_graphs)
+    gen_s = time.perf_counter() - t0
+    sizes = [g.m for g in graphs]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    U, V, S = (torch.from_numpy(np.concatenate([getattr(g, k) for g in graphs])).to(dev) for k in ("u", "v", "s"))
+    torch.cuda.synchronize(dev)
+    eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eb0.record(stream)
+    handles = [dbbc.dbbc_graph_from_coo(U[offs[i]:offs[i + 1]], V[offs[i]:offs[i + 1]], S[offs[i]:offs[i + 1]],
+                                        g.n_u, g.n_v, stream=stream) for i, g in enumerate(graphs)]
+    eb1.record(stream)
+    torch.cuda.synchronize(dev)
+    build_ms = eb0.elapsed_time(eb1)
+    infos = [h.info for h in handles]
+    wedges = sum(i["wedges"] for i in infos)
+    # plain: one synchronous count per graph
+    for h in handles[:64]:
+        dbbc.dbbc_count(h, stream)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    plain = [dbbc.dbbc_count(h, stream) for h in handles]
+    torch.cuda.synchronize(dev)
+    plain_s = time.perf_counter() - t0
+    # batched: one plan, replayed
+    plan = dbbc.dbbc_batch_create(handles, stream)
+    d_out = torch.zeros((len(handles), 2), dtype=torch.int64, device=dev)
+    for _ in range(a.warmup):
+        dbbc.dbbc_batch_count_async(plan, d_out, stream)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = dbbc.dbbc_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        dbbc.dbbc_batch_count_async(plan, d_out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = dbbc.dbbc_kernel_launches() - launches0
+    clocks = sampler.stop()
+    barrier()
+    t_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    t_ms = float(t_ms.item())
+    got = [tuple(map(int, r)) for r in d_out.cpu().numpy().astype(np.uint64)]
+    bit_exact_vs_plain = got == plain
+    value = world * len(handles) * a.steps / (t_ms / 1e3)
+    plain_gps = len(handles) / plain_s
+    # end to end: host COO (pinned) -> build every graph -> one batch count -> counts on the host
+    hU, hV, hS = (torch.from_numpy(np.concatenate([getattr(g, k) for g in graphs])).pin_memory()
+                  for k in ("u", "v", "s"))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    hs = [dbbc.dbbc_graph_from_coo(hU[offs[i]:offs[i + 1]], hV[offs[i]:offs[i + 1]], hS[offs[i]:offs[i + 1]],
+                                   g.n_u, g.n_v, stream=stream) for i, g in enumerate(graphs)]
+    bal, unb = dbbc.dbbc_count_batch(hs, stream)
+    e2e_s = time.perf_counter() - t0
+    e2e_exact = list(zip(bal.tolist(), unb.tolist())) == plain
+    for h in hs:
+        h.free()
+    # algorithmic bytes of one batch count (all tiers)
+    nbytes = sum(B_WEDGE * i["wedges"] + B_LOWER * (i["lower_light"] + i["lower_medium"])
+                 + B_CUR_INIT * i["hub_cursor_inits"] + B_CUR_STEP * i["hub_cursor_steps"] for i in infos)
+    peaks, peak_kind = measured_peaks()
+    per_replay_s = t_ms / 1e3 / a.steps
+    achieved = nbytes / per_replay_s / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "batch-4096", "n_graphs": len(handles), "edges_total": int(offs[-1]),
+                       "wedges_per_step": wedges, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (all graphs' CSR %.0f MB > 129 MB)" % (
+                           sum(8 * i["m"] + 24 * (i["n_u"] + i["n_v"]) for i in infos) / 1e6)},
+            "plain_graphs_per_s": plain_gps, "batched_over_plain": value / world / plain_gps,
+            "batched_gwedges_per_s": wedges * a.steps / (t_ms / 1e3) / 1e9,
+            "build_ms_all_graphs": build_ms, "generate_s": gen_s,
+            "bit_exact_vs_plain": bit_exact_vs_plain,
+            "e2e": {"value": world * len(handles) / e2e_s, "unit": "graphs/s",
+                    "h2d_bytes_per_step": 9 * int(offs[-1]), "d2h_bytes_per_step": 16 * len(handles),
+                    "steps": 1, "bit_exact": e2e_exact},
+            "roofline": {"bound": "hbm", "kernel": "batch count (light + medium + hub sweep, one CUDA graph)",
+                         "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                         "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                         "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "bytes_per_launch": nbytes, "ms_per_launch": 1e3 * per_replay_s},
+            "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        nc = cores()
+        t0 = time.perf_counter()
+        done = 0
+        k = 0
+        while time.perf_counter() - t0 < a.cpu_seconds and k < len(graphs):
+            g = graphs[k]
+            oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=nc)
+            done += 1
+            k += 1
+        t = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / t, "unit": "graphs/s", "cores": nc, "kind": "oracle",
+                                "sample": f"the first {done} graphs of the batch, one after another, {nc} threads"}
+    plan.free()
+    for h in handles:
+        h.free()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -221,6 +369,12 @@ def main():
     def barrier():
         if dist is not None:
             dist.barrier()
+
+    if a.workload == "batch-4096":
+        run_batch(a, torch, dbbc, world, rank, local, dist, barrier)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)

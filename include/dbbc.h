@@ -126,9 +126,9 @@ DBBC_API uint64_t dbbc_kernel_launches(void);
  * cursors for all of them. */
 DBBC_API dbbc_status dbbc_count_noalloc(const dbbc_graph* g, void* cuda_stream, uint64_t* d_out);
 
-/* Count several resident graphs in one launch sequence. balanced[i] and
- * unbalanced[i] (host arrays of n_graphs entries) receive graph i's counts.
- * Synchronous. */
+/* Count several resident graphs in one launch sequence (a temporary batch
+ * plan, see dbbc_batch_create). balanced[i] and unbalanced[i] (host arrays of
+ * n_graphs entries) receive graph i's counts. Synchronous. */
 DBBC_API dbbc_status dbbc_count_batch(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream, uint64_t* balanced,
                              uint64_t* unbalanced);
 
@@ -136,6 +136,22 @@ DBBC_API dbbc_status dbbc_count_batch(const dbbc_graph* const* gs, int32_t n_gra
  * {balanced, unbalanced}. Returns after enqueueing. */
 DBBC_API dbbc_status dbbc_count_batch_async(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream,
                                    uint64_t* d_out);
+
+/* Batch plan over resident graphs: their light and medium pivots and their
+ * hub work items (in descending estimated work across all graphs) form one
+ * work list, counted by one kernel per tier for all graphs. The first count
+ * captures that sequence into a CUDA graph; later counts replay it. The graphs
+ * must stay alive and unchanged while the plan exists. Counts of one plan
+ * must not overlap on the GPU (they share the plan's scratch). */
+typedef struct dbbc_batch dbbc_batch;
+DBBC_API dbbc_status dbbc_batch_create(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream,
+                                       dbbc_batch** out);
+/* Replay the plan; d_out (DEVICE [n_graphs][2], may be NULL) receives the
+ * counts in stream order. Returns after enqueueing. */
+DBBC_API dbbc_status dbbc_batch_count_async(dbbc_batch* b, void* cuda_stream, uint64_t* d_out);
+/* Replay the plan and copy the counts to host arrays of n_graphs entries. */
+DBBC_API dbbc_status dbbc_batch_count(dbbc_batch* b, void* cuda_stream, uint64_t* balanced, uint64_t* unbalanced);
+DBBC_API void dbbc_batch_free(dbbc_batch* b);
 
 typedef struct {
   int32_t n_u, n_v;

@@ -30,7 +30,8 @@ EXPORTED = (
     "dbbc_graph_from_coo", "dbbc_count", "dbbc_count_async", "dbbc_count_batch", "dbbc_count_batch_async",
     "dbbc_graph_get_info", "dbbc_graph_device_bytes", "dbbc_estimate_bytes", "dbbc_graph_free",
     "dbbc_graph_export", "dbbc_set_allocator", "dbbc_status_string", "dbbc_version", "dbbc_count_profiled",
-    "dbbc_kernel_launches", "dbbc_count_noalloc",
+    "dbbc_kernel_launches", "dbbc_count_noalloc", "dbbc_batch_create", "dbbc_batch_count_async",
+    "dbbc_batch_count", "dbbc_batch_free",
 )
 
 
@@ -88,6 +89,14 @@ def lib() -> ctypes.CDLL:
         L.dbbc_count_profiled.restype = st
         L.dbbc_kernel_launches.argtypes = []
         L.dbbc_kernel_launches.restype = ctypes.c_uint64
+        L.dbbc_batch_create.argtypes = [P, I32, P, ctypes.POINTER(P)]
+        L.dbbc_batch_create.restype = st
+        L.dbbc_batch_count_async.argtypes = [P, P, P]
+        L.dbbc_batch_count_async.restype = st
+        L.dbbc_batch_count.argtypes = [P, P, P, P]
+        L.dbbc_batch_count.restype = st
+        L.dbbc_batch_free.argtypes = [P]
+        L.dbbc_batch_free.restype = None
         L.dbbc_count_noalloc.argtypes = [P, P, P]
         L.dbbc_count_noalloc.restype = st
         L.dbbc_count_async.argtypes = [P, P, P]
@@ -254,6 +263,61 @@ def dbbc_count_batch_async(graphs, d_out, stream=None) -> None:
         return
     _check(lib().dbbc_count_batch_async(_handles(graphs), len(graphs), _stream_ptr(stream), d_out.data_ptr()),
            "dbbc_count_batch_async")
+
+
+class Batch:
+    """Owning wrapper of a ``dbbc_batch*`` plan; keeps its graphs alive."""
+
+    def __init__(self, handle: int, graphs):
+        self.handle = handle
+        self.graphs = list(graphs)
+
+    def free(self):
+        if self.handle:
+            lib().dbbc_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __len__(self):
+        return len(self.graphs)
+
+
+def dbbc_batch_create(graphs, stream=None) -> Batch:
+    """Plan a batched count of resident graphs (replayed as one CUDA graph)."""
+    h = ctypes.c_void_p()
+    _check(lib().dbbc_batch_create(_handles(graphs), len(graphs), _stream_ptr(stream), ctypes.byref(h)),
+           "dbbc_batch_create")
+    return Batch(h.value, graphs)
+
+
+def dbbc_batch_count_async(b: Batch, d_out=None, stream=None) -> None:
+    """Replay the plan; ``d_out`` (device tensor [n, 2] of 64-bit, optional) receives the counts."""
+    _check(lib().dbbc_batch_count_async(b.handle, _stream_ptr(stream), d_out.data_ptr() if d_out is not None else None),
+           "dbbc_batch_count_async")
+
+
+def dbbc_batch_count(b: Batch, stream=None) -> tuple[np.ndarray, np.ndarray]:
+    n = len(b)
+    bal = np.zeros(n, np.uint64)
+    unb = np.zeros(n, np.uint64)
+    _check(lib().dbbc_batch_count(b.handle, _stream_ptr(stream), bal.ctypes.data, unb.ctypes.data),
+           "dbbc_batch_count")
+    return bal, unb
+
+
+def dbbc_batch_free(b: Batch) -> None:
+    b.free()
 
 
 def dbbc_graph_get_info(g: Graph) -> dict:

@@ -18,6 +18,8 @@ void* g_alloc_ctx = nullptr;
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void* dev_alloc(size_t bytes, cudaStream_t s) {
   if (g_alloc_fn) return g_alloc_fn(bytes, (void*)s, g_alloc_ctx);
@@ -226,49 +228,6 @@ dbbc_status dbbc_count_profiled(const dbbc_graph* g, void* cuda_stream, uint64_t
 }
 
 uint64_t dbbc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
-
-dbbc_status dbbc_count_batch_async(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream,
-                                   uint64_t* d_out) {
-  if (n_graphs < 0 || (n_graphs > 0 && (!gs || !d_out))) return DBBC_EINVAL;
-  for (int32_t i = 0; i < n_graphs; i++)
-    if (!gs[i]) return DBBC_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  return guarded([&] {
-    if (n_graphs == 0) return;
-    Scratch sc(s);
-    unsigned* d_status = sc.get<unsigned>(1);
-    DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
-    DBBC_CUDA(cudaMemsetAsync(d_out, 0, (size_t)n_graphs * 2 * sizeof(uint64_t), s));
-    for (int32_t i = 0; i < n_graphs; i++)
-      enqueue_count(gs[i], s, reinterpret_cast<unsigned long long*>(d_out) + 2 * i, d_status, sc);
-  });
-}
-
-dbbc_status dbbc_count_batch(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream, uint64_t* balanced,
-                             uint64_t* unbalanced) {
-  if (n_graphs < 0 || (n_graphs > 0 && (!gs || !balanced || !unbalanced))) return DBBC_EINVAL;
-  for (int32_t i = 0; i < n_graphs; i++)
-    if (!gs[i]) return DBBC_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  std::vector<uint64_t> h((size_t)n_graphs * 2);
-  const dbbc_status st = guarded([&] {
-    if (n_graphs == 0) return;
-    Scratch sc(s);
-    unsigned long long* d_out = sc.get<unsigned long long>((size_t)n_graphs * 2);
-    unsigned* d_status = sc.get<unsigned>(1);
-    DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
-    DBBC_CUDA(cudaMemsetAsync(d_out, 0, (size_t)n_graphs * 2 * sizeof(uint64_t), s));
-    for (int32_t i = 0; i < n_graphs; i++) enqueue_count(gs[i], s, d_out + 2 * i, d_status, sc);
-    DBBC_CUDA(cudaMemcpyAsync(h.data(), d_out, h.size() * 8, cudaMemcpyDeviceToHost, s));
-    check_status_word(d_status, s);
-  });
-  if (st != DBBC_OK) return st;
-  for (int32_t i = 0; i < n_graphs; i++) {
-    balanced[i] = h[2 * (size_t)i];
-    unbalanced[i] = h[2 * (size_t)i + 1];
-  }
-  return DBBC_OK;
-}
 
 dbbc_status dbbc_graph_export(const dbbc_graph* g, void* cuda_stream, int64_t* row_ptr, uint32_t* col,
                               uint32_t* lower, int32_t* vertex, uint64_t* work) {

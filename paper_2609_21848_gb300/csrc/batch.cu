@@ -1,0 +1,515 @@
+// Batched counting of many resident graphs. A batch plan concatenates the
+// graphs' light and medium pivot lists and their hub items (the latter in
+// descending estimated work across all graphs, i.e. LPT order) into one work
+// list; one light, one medium and one hub-sweep kernel then serve every
+// graph, each adding its sums into that graph's output pair. The sequence is
+// captured into a CUDA graph on the first count and replayed afterwards, so a
+// batch count costs one graph launch however many graphs it holds.
+#include <algorithm>
+#include <numeric>
+
+#include "count_device.cuh"
+
+namespace dbbc {
+
+struct GraphDesc {
+  const int64_t* row_ptr;
+  const uint32_t* col;
+  const uint32_t* lower;
+  const uint64_t* work;
+  int64_t n;
+  int32_t n_u;
+  int32_t pad;
+};
+
+struct BatchPivot {
+  int32_t graph;
+  int32_t row;
+};
+
+struct BatchHubItem {
+  int32_t graph;
+  int32_t pad;
+  SweepItem it;
+};
+
+struct GatherJob {
+  const int32_t* order;
+  int64_t n_hub, n_medium, n_light;
+  int64_t medium_off, light_off;
+};
+
+__device__ __forceinline__ CsrView view_of(const GraphDesc& d) { return CsrView{d.row_ptr, d.col, d.lower, d.n_u, d.n}; }
+
+// One CTA per graph copies its medium and light pivots into the batch lists.
+__global__ void gather_pivots_kernel(const GatherJob* __restrict__ jobs, BatchPivot* __restrict__ med,
+                                     BatchPivot* __restrict__ light) {
+  const int gi = blockIdx.x;
+  const GatherJob j = jobs[gi];
+  for (int64_t i = threadIdx.x; i < j.n_medium; i += blockDim.x)
+    med[j.medium_off + i] = BatchPivot{gi, j.order[j.n_hub + i]};
+  for (int64_t i = threadIdx.x; i < j.n_light; i += blockDim.x)
+    light[j.light_off + i] = BatchPivot{gi, j.order[j.n_hub + j.n_medium + i]};
+}
+
+__device__ __forceinline__ void warp_flush(int graph, uint64_t& bal, uint64_t& unb, unsigned long long* out) {
+  const uint64_t b = warp_sum_u64(bal), u = warp_sum_u64(unb);
+  if (lane_id() == 0 && graph >= 0) {
+    if (b) atomicAdd(&out[2 * graph], (unsigned long long)b);
+    if (u) atomicAdd(&out[2 * graph + 1], (unsigned long long)u);
+  }
+  bal = 0;
+  unb = 0;
+}
+
+// Light tier over all graphs: warps pull chunks of 32 consecutive pivots and
+// flush their sums whenever the graph changes.
+__global__ void __launch_bounds__(kLightWarps * 32) count_light_batch_kernel(
+    const GraphDesc* __restrict__ desc, const BatchPivot* __restrict__ piv, int64_t n_piv, int* next_chunk,
+    unsigned long long* out, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char light_smem[];
+  unsigned long long* vals_all = reinterpret_cast<unsigned long long*>(light_smem);
+  uint32_t* keys_all = reinterpret_cast<uint32_t*>(vals_all + kLightWarps * kLightSlots);
+  const int w = threadIdx.x >> 5;
+  const unsigned lane = lane_id();
+  uint32_t* keys = keys_all + w * kLightSlots;
+  unsigned long long* vals = vals_all + w * kLightSlots;
+  for (int i = lane; i < kLightSlots; i += 32) {
+    keys[i] = kEmptyKey;
+    vals[i] = 0;
+  }
+  __syncwarp();
+  constexpr int max_log = 10;
+  uint64_t bal = 0, unb = 0;
+  bool full = false;
+  int cur_graph = -1;
+  CsrView g{};
+  const uint64_t* work = nullptr;
+  for (;;) {
+    int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(next_chunk, 1);
+    chunk = __shfl_sync(kFullMask, chunk, 0);
+    const int64_t t0 = (int64_t)chunk * 32;
+    if (t0 >= n_piv) break;
+    const int64_t t1 = t0 + 32 < n_piv ? t0 + 32 : n_piv;
+    for (int64_t t = t0; t < t1; t++) {
+      const BatchPivot bp = piv[t];
+      if (bp.graph != cur_graph) {
+        warp_flush(cur_graph, bal, unb, out);
+        cur_graph = bp.graph;
+        const GraphDesc d = desc[bp.graph];
+        g = view_of(d);
+        work = d.work;
+      }
+      const int log_h = table_log(work[bp.row], max_log);
+      const PivotGeom q = pivot_geom(g, bp.row);
+      warp_walk<1>(g, q, 0, q.L, 32, [&](const uint32_t (&x)[1], uint32_t s1) {
+        if (x[0] != 0xFFFFFFFFu) {
+          const unsigned long long inc = wedge_inc(x[0], s1);
+          unsigned long long old;
+          if (smem_hash_add(keys, vals, log_h, x[0] >> 1, inc, &old)) wedge_contrib(old, inc, bal, unb);
+          else full = true;
+        }
+      });
+      __syncwarp();
+      for (int i = lane; i < (1 << log_h); i += 32) {
+        keys[i] = kEmptyKey;
+        vals[i] = 0;
+      }
+      __syncwarp();
+    }
+  }
+  warp_flush(cur_graph, bal, unb, out);
+  if (full) atomicOr(status, DBBC_DEV_HASH_FULL);
+}
+
+// Medium tier over all graphs: one CTA per pivot, sums flushed per pivot.
+__global__ void __launch_bounds__(kMediumThreads) count_medium_batch_kernel(const GraphDesc* __restrict__ desc,
+                                                                            const BatchPivot* __restrict__ piv,
+                                                                            int64_t n_piv, unsigned long long* out,
+                                                                            unsigned* status) {
+  extern __shared__ __align__(16) unsigned char med_smem[];
+  unsigned long long* vals = reinterpret_cast<unsigned long long*>(med_smem);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(vals + kMediumSlots);
+  for (int i = threadIdx.x; i < kMediumSlots; i += kMediumThreads) {
+    keys[i] = kEmptyKey;
+    vals[i] = 0;
+  }
+  __syncthreads();
+  constexpr int max_log = 13;
+  const int w = threadIdx.x >> 5;
+  bool full = false;
+  for (int64_t t = blockIdx.x; t < n_piv; t += gridDim.x) {
+    const BatchPivot bp = piv[t];
+    const GraphDesc d = desc[bp.graph];
+    const CsrView g = view_of(d);
+    const int log_h = table_log(d.work[bp.row], max_log);
+    const PivotGeom q = pivot_geom(g, bp.row);
+    uint64_t bal = 0, unb = 0;
+    warp_walk<2>(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u, [&](const uint32_t (&x)[2], uint32_t s1) {
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        if (x[u] != 0xFFFFFFFFu) {
+          const unsigned long long inc = wedge_inc(x[u], s1);
+          unsigned long long old;
+          if (smem_hash_add(keys, vals, log_h, x[u] >> 1, inc, &old)) wedge_contrib(old, inc, bal, unb);
+          else full = true;
+        }
+      }
+    });
+    __syncthreads();
+    for (int i = threadIdx.x; i < (1 << log_h); i += kMediumThreads) {
+      keys[i] = kEmptyKey;
+      vals[i] = 0;
+    }
+    block_add_pair<kMediumThreads>(bal, unb, out + 2 * bp.graph);  // contains __syncthreads
+  }
+  if (full) atomicOr(status, DBBC_DEV_HASH_FULL);
+}
+
+// Hub sweep over all graphs' hub items (see hub_sweep_kernel); sums are
+// flushed per item.
+__global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const GraphDesc* __restrict__ desc,
+                                                                        const BatchHubItem* __restrict__ items,
+                                                                        int64_t n_items, int* next_item,
+                                                                        int64_t* __restrict__ cursors, int64_t cur_cap,
+                                                                        unsigned long long* out) {
+  extern __shared__ __align__(16) unsigned char sweep_smem[];
+  uint32_t* c16 = reinterpret_cast<uint32_t*>(sweep_smem);
+  unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
+  __shared__ int item_sh;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < (int)kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
+  int64_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
+  for (;;) {
+    if (tid == 0) item_sh = atomicAdd(next_item, 1);
+    __syncthreads();
+    const int64_t it = item_sh;
+    __syncthreads();
+    if (it >= n_items) break;
+    const BatchHubItem bi = items[it];
+    const SweepItem item = bi.it;
+    const CsrView g = view_of(desc[bi.graph]);
+    const PivotGeom q = pivot_geom(g, item.row);
+    const bool wide = item.wide != 0;
+    const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
+    const uint32_t first = item.lo << 1;
+    for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
+      const uint32_t e = g.col[q.rb + i];
+      const int64_t vrow = q.base + (e >> 1);
+      int64_t b = g.row_ptr[vrow];
+      const int64_t en = g.row_ptr[vrow + 1];
+      if (first) {
+        int64_t lo = b, hi = en;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (g.col[mid] < first) lo = mid + 1; else hi = mid;
+        }
+        b = lo;
+      }
+      cur[2 * i] = b;
+      cur[2 * i + 1] = en;
+    }
+    __syncthreads();
+    uint64_t bal = 0, unb = 0;
+    for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
+      const uint32_t hi = min(lo + H, item.hi);
+      if (wide) sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      else sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      __syncthreads();
+      const uint32_t words = wide ? 2 * (hi - lo) : (hi - lo);
+      for (uint32_t j = tid; j < words; j += kSweepThreads) c16[j] = 0u;
+      __syncthreads();
+    }
+    block_add_pair<kSweepThreads>(bal, unb, out + 2 * bi.graph);
+  }
+}
+
+}  // namespace dbbc
+
+struct dbbc_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;   // stream the plan was created on (frees are ordered on it)
+  cudaStream_t capture = nullptr;  // private stream used only to capture the CUDA graph
+  int32_t n_graphs = 0;
+  dbbc::GraphDesc* desc = nullptr;
+  dbbc::BatchPivot* light = nullptr;
+  dbbc::BatchPivot* medium = nullptr;
+  dbbc::BatchHubItem* hub = nullptr;
+  int64_t n_light = 0, n_medium = 0, n_hub_items = 0, max_lower = 1;
+  unsigned long long* out = nullptr;  // [n_graphs][2]
+  int64_t* cursors = nullptr;
+  int* counters = nullptr;  // [0] light chunks, [1] hub items
+  unsigned* status = nullptr;
+  int hub_grid = 0, light_grid = 0, medium_grid = 0;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels_per_replay = 0;
+  std::vector<void*> allocations;
+};
+
+namespace dbbc {
+
+static void* batch_alloc(dbbc_batch* b, size_t bytes) {
+  void* p = dev_alloc(bytes ? bytes : 16, b->stream);
+  if (!p) throw Error{DBBC_ENOMEM, "batch_alloc"};
+  b->allocations.push_back(p);
+  return p;
+}
+
+static void batch_release(dbbc_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  for (void* p : b->allocations) dev_free(p, b->stream);
+  b->allocations.clear();
+  if (b->capture) cudaStreamDestroy(b->capture);
+  b->capture = nullptr;
+}
+
+static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
+  const int32_t n = b->n_graphs;
+  cudaStream_t s = b->stream;
+  std::vector<GraphDesc> desc((size_t)n);
+  std::vector<GatherJob> jobs((size_t)n);
+  struct HubRef {
+    BatchHubItem item;
+    uint64_t est;
+  };
+  std::vector<HubRef> hubs;
+  for (int32_t i = 0; i < n; i++) {
+    const dbbc_graph* g = gs[i];
+    desc[(size_t)i] = GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u, 0};
+    jobs[(size_t)i] = GatherJob{g->order, g->n_hub, g->n_medium, g->n_light, b->n_medium, b->n_light};
+    b->n_medium += g->n_medium;
+    b->n_light += g->n_light;
+    for (size_t k = 0; k < g->sweep_items_host.size(); k++)
+      hubs.push_back(HubRef{BatchHubItem{i, 0, g->sweep_items_host[k]}, g->sweep_est_host[k]});
+    if (g->n_hub > 0) b->max_lower = std::max<int64_t>(b->max_lower, g->sweep_max_lower);
+  }
+  std::stable_sort(hubs.begin(), hubs.end(), [](const HubRef& a, const HubRef& c) { return a.est > c.est; });
+  std::vector<BatchHubItem> items(hubs.size());
+  for (size_t k = 0; k < hubs.size(); k++) items[k] = hubs[k].item;
+  b->n_hub_items = (int64_t)items.size();
+
+  b->desc = static_cast<GraphDesc*>(batch_alloc(b, desc.size() * sizeof(GraphDesc)));
+  b->light = static_cast<BatchPivot*>(batch_alloc(b, (size_t)b->n_light * sizeof(BatchPivot)));
+  b->medium = static_cast<BatchPivot*>(batch_alloc(b, (size_t)b->n_medium * sizeof(BatchPivot)));
+  b->hub = static_cast<BatchHubItem*>(batch_alloc(b, items.size() * sizeof(BatchHubItem)));
+  b->out = static_cast<unsigned long long*>(batch_alloc(b, (size_t)n * 2 * sizeof(unsigned long long)));
+  b->counters = static_cast<int*>(batch_alloc(b, 2 * sizeof(int)));
+  b->status = static_cast<unsigned*>(batch_alloc(b, sizeof(unsigned)));
+  const size_t smem = (size_t)kSweepWindow16 * 4;
+  DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  b->hub_grid = num_sms() * blocks_per_sm((const void*)hub_sweep_batch_kernel, kSweepThreads, smem);
+  if (b->n_hub_items > 0)
+    b->cursors = static_cast<int64_t*>(batch_alloc(b, (size_t)b->hub_grid * (size_t)b->max_lower * 16));
+  {
+    const int sms = num_sms();
+    const int64_t want = ceil_div<int64_t>(ceil_div<int64_t>(b->n_light, 32), kLightWarps);
+    const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_light_batch_kernel, kLightWarps * 32,
+                                                     (size_t)kLightWarps * kLightSlots * 12);
+    b->light_grid = (int)std::max<int64_t>(1, std::min(want, cap));
+    const int64_t mcap = (int64_t)sms * blocks_per_sm((const void*)count_medium_batch_kernel, kMediumThreads,
+                                                      (size_t)kMediumSlots * 12);
+    b->medium_grid = (int)std::max<int64_t>(1, std::min<int64_t>(b->n_medium, mcap));
+  }
+  GatherJob* d_jobs = static_cast<GatherJob*>(batch_alloc(b, jobs.size() * sizeof(GatherJob)));
+  DBBC_CUDA(cudaMemcpyAsync(b->desc, desc.data(), desc.size() * sizeof(GraphDesc), cudaMemcpyHostToDevice, s));
+  DBBC_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(GatherJob), cudaMemcpyHostToDevice, s));
+  if (!items.empty())
+    DBBC_CUDA(cudaMemcpyAsync(b->hub, items.data(), items.size() * sizeof(BatchHubItem), cudaMemcpyHostToDevice, s));
+  if (n > 0) {
+    gather_pivots_kernel<<<(unsigned)n, 256, 0, s>>>(d_jobs, b->medium, b->light);
+    DBBC_LAUNCH_CHECK();
+  }
+  DBBC_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
+}
+
+// The batch count: clear outputs and counters, then the three tiers.
+static void enqueue_batch(dbbc_batch* b, cudaStream_t s) {
+  DBBC_CUDA(cudaMemsetAsync(b->out, 0, (size_t)b->n_graphs * 2 * sizeof(unsigned long long), s));
+  DBBC_CUDA(cudaMemsetAsync(b->counters, 0, 2 * sizeof(int), s));
+  DBBC_CUDA(cudaMemsetAsync(b->status, 0, sizeof(unsigned), s));
+  if (b->n_light > 0) {
+    const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
+    count_light_batch_kernel<<<(unsigned)b->light_grid, kLightWarps * 32, smem, s>>>(b->desc, b->light, b->n_light,
+                                                                                     b->counters, b->out, b->status);
+    DBBC_LAUNCH_CHECK();
+  }
+  if (b->n_medium > 0) {
+    const size_t smem = (size_t)kMediumSlots * 12;
+    count_medium_batch_kernel<<<(unsigned)b->medium_grid, kMediumThreads, smem, s>>>(b->desc, b->medium,
+                                                                                     b->n_medium, b->out, b->status);
+    DBBC_LAUNCH_CHECK();
+  }
+  if (b->n_hub_items > 0) {
+    const size_t smem = (size_t)kSweepWindow16 * 4;
+    const int grid = (int)std::min<int64_t>(b->hub_grid, b->n_hub_items);
+    hub_sweep_batch_kernel<<<grid, kSweepThreads, smem, s>>>(b->desc, b->hub, b->n_hub_items, b->counters + 1,
+                                                             b->cursors, b->max_lower, b->out);
+    DBBC_LAUNCH_CHECK();
+  }
+}
+
+static void set_batch_attributes() {
+  DBBC_CUDA(cudaFuncSetAttribute(count_light_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)kLightWarps * kLightSlots * 12)));
+  DBBC_CUDA(cudaFuncSetAttribute(count_medium_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)kMediumSlots * 12)));
+  DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)kSweepWindow16 * 4)));
+}
+
+static void check_batch_status(const dbbc_batch* b, cudaStream_t s) {
+  unsigned h = 0;
+  DBBC_CUDA(cudaMemcpyAsync(&h, b->status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  DBBC_CUDA(cudaStreamSynchronize(s));
+  if (h) throw Error{DBBC_EINTERNAL, "device status"};
+}
+
+template <typename F>
+static dbbc_status batch_guard(F&& f) {
+  try {
+    f();
+    return DBBC_OK;
+  } catch (const Error& e) {
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    return DBBC_ENOMEM;
+  } catch (...) {
+    return DBBC_EINTERNAL;
+  }
+}
+
+}  // namespace dbbc
+
+using namespace dbbc;
+
+extern "C" {
+
+dbbc_status dbbc_batch_create(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream, dbbc_batch** out) {
+  if (!out || n_graphs < 0 || (n_graphs > 0 && !gs)) return DBBC_EINVAL;
+  for (int32_t i = 0; i < n_graphs; i++)
+    if (!gs[i]) return DBBC_EINVAL;
+  dbbc_batch* b = nullptr;
+  try {
+    b = new dbbc_batch();
+  } catch (...) {
+    return DBBC_ENOMEM;
+  }
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->n_graphs = n_graphs;
+  const dbbc_status st = batch_guard([&] {
+    DBBC_CUDA(cudaGetDevice(&b->device));
+    set_batch_attributes();
+    plan_batch(b, gs);
+  });
+  if (st != DBBC_OK) {
+    batch_release(b);
+    (void)cudaStreamSynchronize(b->stream);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return DBBC_OK;
+}
+
+dbbc_status dbbc_batch_count_async(dbbc_batch* b, void* cuda_stream, uint64_t* d_out) {
+  if (!b) return DBBC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  return batch_guard([&] {
+    if (!b->exec) {
+      // capture on a private stream (the caller's may be the legacy stream,
+      // which cannot be captured), replay on the caller's stream
+      if (!b->capture) DBBC_CUDA(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+      cudaGraph_t graph = nullptr;
+      DBBC_CUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+      const uint64_t before = launches_so_far();
+      try {
+        enqueue_batch(b, b->capture);
+      } catch (...) {
+        cudaStreamEndCapture(b->capture, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      b->kernels_per_replay = launches_so_far() - before;
+      note_launches((uint64_t)0 - b->kernels_per_replay);  // captured, not yet run
+      DBBC_CUDA(cudaStreamEndCapture(b->capture, &graph));
+      const cudaError_t e = cudaGraphInstantiate(&b->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      DBBC_CUDA(e);
+    }
+    DBBC_CUDA(cudaGraphLaunch(b->exec, s));
+    note_launches(b->kernels_per_replay);
+    if (d_out)
+      DBBC_CUDA(cudaMemcpyAsync(d_out, b->out, (size_t)b->n_graphs * 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                                s));
+  });
+}
+
+dbbc_status dbbc_batch_count(dbbc_batch* b, void* cuda_stream, uint64_t* balanced, uint64_t* unbalanced) {
+  if (!b || (b->n_graphs > 0 && (!balanced || !unbalanced))) return DBBC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<uint64_t> h((size_t)b->n_graphs * 2);
+  dbbc_status st = dbbc_batch_count_async(b, cuda_stream, nullptr);
+  if (st != DBBC_OK) return st;
+  st = batch_guard([&] {
+    DBBC_CUDA(cudaMemcpyAsync(h.data(), b->out, h.size() * 8, cudaMemcpyDeviceToHost, s));
+    check_batch_status(b, s);
+  });
+  if (st != DBBC_OK) return st;
+  for (int32_t i = 0; i < b->n_graphs; i++) {
+    balanced[i] = h[2 * (size_t)i];
+    unbalanced[i] = h[2 * (size_t)i + 1];
+  }
+  return DBBC_OK;
+}
+
+void dbbc_batch_free(dbbc_batch* b) {
+  if (!b) return;
+  batch_release(b);
+  delete b;
+}
+
+// One-shot forms over a temporary plan (no graph capture).
+dbbc_status dbbc_count_batch_async(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream,
+                                   uint64_t* d_out) {
+  if (n_graphs < 0 || (n_graphs > 0 && (!gs || !d_out))) return DBBC_EINVAL;
+  if (n_graphs == 0) return DBBC_OK;
+  dbbc_batch* b = nullptr;
+  dbbc_status st = dbbc_batch_create(gs, n_graphs, cuda_stream, &b);
+  if (st != DBBC_OK) return st;
+  st = batch_guard([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    enqueue_batch(b, s);
+    DBBC_CUDA(cudaMemcpyAsync(d_out, b->out, (size_t)n_graphs * 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  });
+  dbbc_batch_free(b);  // frees are stream-ordered after the copy
+  return st;
+}
+
+dbbc_status dbbc_count_batch(const dbbc_graph* const* gs, int32_t n_graphs, void* cuda_stream, uint64_t* balanced,
+                             uint64_t* unbalanced) {
+  if (n_graphs < 0 || (n_graphs > 0 && (!gs || !balanced || !unbalanced))) return DBBC_EINVAL;
+  for (int32_t i = 0; i < n_graphs; i++)
+    if (!gs[i]) return DBBC_EINVAL;
+  if (n_graphs == 0) return DBBC_OK;
+  dbbc_batch* b = nullptr;
+  dbbc_status st = dbbc_batch_create(gs, n_graphs, cuda_stream, &b);
+  if (st != DBBC_OK) return st;
+  std::vector<uint64_t> h((size_t)n_graphs * 2);
+  st = batch_guard([&] {
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    enqueue_batch(b, s);
+    DBBC_CUDA(cudaMemcpyAsync(h.data(), b->out, h.size() * 8, cudaMemcpyDeviceToHost, s));
+    check_batch_status(b, s);
+  });
+  dbbc_batch_free(b);
+  if (st != DBBC_OK) return st;
+  for (int32_t i = 0; i < n_graphs; i++) {
+    balanced[i] = h[2 * (size_t)i];
+    unbalanced[i] = h[2 * (size_t)i + 1];
+  }
+  return DBBC_OK;
+}
+
+}  // extern "C"

@@ -31,7 +31,9 @@ struct Error {
     }                                                             \
   } while (0)
 
-void note_launch();  // counts kernels launched by the library
+void note_launch();                // counts kernels launched by the library
+void note_launches(uint64_t k);    // k kernels launched at once (a CUDA graph replay)
+uint64_t launches_so_far();
 #define DBBC_LAUNCH_CHECK()          \
   do {                               \
     ::dbbc::note_launch();           \

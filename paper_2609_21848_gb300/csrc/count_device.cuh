@@ -1,0 +1,239 @@
+// Device building blocks shared by the single-graph kernels (count.cu) and
+// the batched kernels (batch.cu): packed wedge counters, the incremental
+// Lemma 1 contribution, shared-memory hashing, the warp walk over a pivot's
+// lower neighbours, and one window of the hub sweep.
+#pragma once
+
+#include "internal.h"
+#include "common.cuh"
+
+namespace dbbc {
+
+// One packed increment: symmetric wedge -> +1, asymmetric -> +2^32.
+__device__ __forceinline__ unsigned long long wedge_inc(uint32_t x, uint32_t s1) {
+  return ((x ^ s1) & 1u) ? (1ull << 32) : 1ull;
+}
+
+// Lemma 1 contribution of one wedge, from its endpoint counter just before the
+// increment (sym = p, asym = q): adding a symmetric wedge to (p, q) closes p
+// new balanced pairs (C(p+1,2) - C(p,2) = p) and q unbalanced ones ((p+1)q - pq);
+// an asymmetric wedge closes q balanced and p unbalanced ones. Summed over all
+// wedges this equals C(p,2) + C(q,2) and p*q per endpoint.
+__device__ __forceinline__ void wedge_contrib(unsigned long long old, unsigned long long inc, uint64_t& bal,
+                                              uint64_t& unb) {
+  const uint64_t p = old & 0xFFFFFFFFull, q = old >> 32;
+  const bool sym = inc == 1ull;
+  bal += sym ? p : q;
+  unb += sym ? q : p;
+}
+
+__device__ __forceinline__ uint32_t hash_slot(uint32_t w, int log_h) {
+  return (w * 2654435769u) >> (32 - log_h);
+}
+
+// Find or insert endpoint w in a shared table of 2^log_h slots and add inc;
+// returns the counter's previous value through *old. Returns false if the
+// probe sequence ran past the table (cannot happen when the table has more
+// slots than the pivot's accepted wedges).
+__device__ __forceinline__ bool smem_hash_add(uint32_t* keys, unsigned long long* vals, int log_h, uint32_t w,
+                                              unsigned long long inc, unsigned long long* old) {
+  const uint32_t mask = (1u << log_h) - 1u;
+  uint32_t h = hash_slot(w, log_h);
+  for (uint32_t probe = 0; probe <= mask; probe++) {
+    uint32_t cur = *reinterpret_cast<volatile uint32_t*>(&keys[h]);
+    if (cur == kEmptyKey) cur = atomicCAS(&keys[h], kEmptyKey, w);
+    if (cur == kEmptyKey || cur == w) {
+      *old = atomicAdd(&vals[h], inc);
+      return true;
+    }
+    h = (h + 1u) & mask;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int table_log(uint64_t work, int max_log) {
+  // smallest 2^k >= 2 * work, at least 32 slots
+  int k = 5;
+  while (k < max_log && (1ull << k) < 2 * work) k++;
+  return k;
+}
+
+struct PivotGeom {
+  int64_t rb;    // row start of the pivot
+  uint32_t L;    // lower neighbours
+  uint32_t lim;  // entries x < lim are accepted endpoints: (side_rank(p) << 1)
+  int64_t base;  // first row of the other side
+};
+
+__device__ __forceinline__ PivotGeom pivot_geom(const CsrView& g, int32_t p) {
+  PivotGeom q;
+  q.rb = g.row_ptr[p];
+  q.L = g.lower[p];
+  const bool is_u = p < g.n_u;
+  q.lim = (is_u ? (uint32_t)p : (uint32_t)(p - g.n_u)) << 1;
+  q.base = is_u ? (int64_t)g.n_u : 0;
+  return q;
+}
+
+// The warp walks lower-neighbour positions [a, b) of the pivot in groups of
+// 32 (`step` = distance between this warp's groups) and, for each lower
+// neighbour v, the accepted prefix of v's row in chunks of 32 * U entries.
+// visit(x[U], s1) is called by all lanes together; lane l holds entries
+// chunk + u*32 + l, with x = 0xFFFFFFFF where nothing is accepted.
+template <int U, typename Visit>
+__device__ __forceinline__ void warp_walk(const CsrView& g, const PivotGeom& q, uint32_t a, uint32_t b,
+                                          uint32_t step, Visit&& visit) {
+  const unsigned lane = lane_id();
+  for (uint32_t i0 = a; i0 < b; i0 += step) {
+    uint32_t e = 0;
+    int64_t vb = 0, ve = 0;
+    if (i0 + lane < b) {
+      e = g.col[q.rb + i0 + lane];
+      const int64_t vrow = q.base + (e >> 1);
+      vb = g.row_ptr[vrow];
+      ve = g.row_ptr[vrow + 1];
+    }
+    const uint32_t cnt = min(32u, b - i0);
+    for (uint32_t k = 0; k < cnt; k++) {
+      const uint32_t s1 = __shfl_sync(kFullMask, e, k) & 1u;
+      const int64_t jb0 = __shfl_sync(kFullMask, vb, k);
+      const int64_t je = __shfl_sync(kFullMask, ve, k);
+      for (int64_t jb = jb0; jb < je; jb += 32 * U) {
+        uint32_t x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int64_t j = jb + u * 32 + lane;
+          x[u] = j < je ? g.col[j] : 0xFFFFFFFFu;
+        }
+        bool stop = false;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          if (x[u] >= q.lim) {
+            x[u] = 0xFFFFFFFFu;
+            stop = true;
+          }
+        }
+        visit(x, s1);
+        if (__any_sync(kFullMask, stop)) break;  // rows ascend: nothing accepted beyond
+      }
+    }
+  }
+}
+
+constexpr int kLightWarps = 8;
+
+constexpr int kMediumThreads = 256;
+constexpr int kMediumWarps = kMediumThreads / 32;
+
+// ------------------------------------------------------------------ hub tier
+// Window sweep. A hub pivot's accepted endpoints [0, side_rank(p)) are cut
+// into windows of kSweepWindow16 (or kSweepWindow32) consecutive side ranks. A
+// work item is one hub and a span of its windows, owned by one CTA, so the
+// counts of every endpoint in a window are complete inside that CTA: they live
+// in shared memory, and the Lemma 1 contributions come from the value each
+// atomic returns. Each lower neighbour v keeps a cursor into its row; rows
+// ascend, so sweeping the windows in order moves every cursor forward only.
+// Counters pack (asym << 16) | sym when the hub has fewer than 2^16 lower
+// neighbours (no count can exceed that), else (asym << 32) | sym.
+constexpr int kSweepThreads = DBBC_SWEEP_THREADS;
+constexpr int kSweepUnroll = DBBC_SWEEP_UNROLL;
+
+__device__ __forceinline__ void sweep_contrib16(uint32_t old, bool sym, uint64_t& bal, uint64_t& unb) {
+  const uint64_t p = old & 0xFFFFu, q = old >> 16;
+  bal += sym ? p : q;
+  unb += sym ? q : p;
+}
+
+// One window of one item: every group of G lanes takes lower neighbours
+// gid, gid + groups, ... and walks the neighbour's row from its cursor, G
+// consecutive entries at a time, until an entry leaves the window.
+template <int G, bool PACK16>
+__device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& q, int64_t* cur, uint32_t lo,
+                                             uint32_t hl, uint32_t* c16, unsigned long long* c32, uint64_t& bal,
+                                             uint64_t& unb) {
+  const int tid = threadIdx.x;
+  const int gl = tid & (G - 1);
+  const uint32_t gid = (uint32_t)tid / G;
+  constexpr uint32_t groups = kSweepThreads / G;
+  const unsigned lane = lane_id();
+  const unsigned gmask = G == 32 ? kFullMask : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+  const uint32_t lo2 = lo << 1;
+  // the next neighbour's cursor and edge sign are loaded while this one is walked
+  int64_t c_nx = 0, en_nx = 0;
+  uint32_t s1_nx = 0;
+  if (gid < q.L) {
+    c_nx = cur[2 * gid];
+    en_nx = cur[2 * gid + 1];
+    s1_nx = g.col[q.rb + gid] & 1u;
+  }
+  for (uint32_t i = gid; i < q.L; i += groups) {
+    int64_t c = c_nx;
+    const int64_t en = en_nx;
+    const uint32_t s1 = s1_nx;
+    const uint32_t i_nx = i + groups;
+    if (i_nx < q.L) {
+      c_nx = cur[2 * i_nx];
+      en_nx = cur[2 * i_nx + 1];
+      s1_nx = g.col[q.rb + i_nx] & 1u;
+    }
+    for (;;) {
+      uint32_t x[kSweepUnroll];
+#pragma unroll
+      for (int u = 0; u < kSweepUnroll; u++) {
+        const int64_t pos = c + u * G + gl;
+        x[u] = pos < en ? g.col[pos] : 0xFFFFFFFFu;
+      }
+      int n_ok = 0;
+#pragma unroll
+      for (int u = 0; u < kSweepUnroll; u++) {
+        const bool ok = x[u] < hl;
+        if (ok) {
+          const bool sym = ((x[u] ^ s1) & 1u) == 0;
+          const uint32_t k = (x[u] - lo2) >> 1;
+          if (PACK16) {
+            sweep_contrib16(atomicAdd(&c16[k], sym ? 1u : 0x10000u), sym, bal, unb);
+          } else {
+            const unsigned long long inc = sym ? 1ull : (1ull << 32);
+            wedge_contrib(atomicAdd(&c32[k], inc), inc, bal, unb);
+          }
+        }
+        n_ok += __popc(__ballot_sync(gmask, ok));  // accepted entries are a prefix
+      }
+      c += n_ok;
+      if (n_ok < G * kSweepUnroll) break;
+    }
+    if (gl == 0) cur[2 * i] = c;
+  }
+}
+
+template <bool PACK16>
+__device__ __forceinline__ void sweep_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
+                                                      int64_t* cur, uint32_t lo, uint32_t hl, uint32_t* c16,
+                                                      unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
+  switch (group_log) {
+    case 0: sweep_window<1, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 2: sweep_window<4, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 3: sweep_window<8, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 4: sweep_window<16, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    default: sweep_window<32, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+  }
+}
+
+inline int blocks_per_sm(const void* fn, int threads, size_t smem) {
+  int b = 0;
+  DBBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem));
+  return b > 0 ? b : 1;
+}
+
+inline int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    DBBC_CUDA(cudaGetDevice(&dev));
+    DBBC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (sms <= 0) sms = kNumSMs;
+  }
+  return sms;
+}
+
+}  // namespace dbbc

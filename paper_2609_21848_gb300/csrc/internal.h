@@ -105,6 +105,8 @@ struct dbbc_graph {
   // hub plan: window-span items in descending estimated work
   dbbc::SweepItem* sweep_items = nullptr;
   int64_t n_sweep_items = 0;
+  std::vector<dbbc::SweepItem> sweep_items_host;  // same items on the host (batch planning)
+  std::vector<uint64_t> sweep_est_host;           // their estimated accepted wedges
   int64_t sweep_max_lower = 0;  // largest lower-neighbour count of a hub (cursor scratch per CTA)
   int64_t narrow_ranks_u = 0, narrow_ranks_v = 0;  // per side: vertices of degree < 2^16 (a rank prefix)
   size_t device_bytes = 0;

@@ -393,7 +393,12 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
   }
   std::stable_sort(plan.begin(), plan.end(), [](const Planned& a, const Planned& b) { return a.est > b.est; });
   std::vector<SweepItem> items(plan.size());
-  for (size_t i = 0; i < plan.size(); i++) items[i] = plan[i].it;
+  g->sweep_est_host.resize(plan.size());
+  for (size_t i = 0; i < plan.size(); i++) {
+    items[i] = plan[i].it;
+    g->sweep_est_host[i] = plan[i].est;
+  }
+  g->sweep_items_host = items;
   g->n_sweep_items = (int64_t)items.size();
   g->sweep_max_lower = max_lower;
   g->sweep_items = static_cast<SweepItem*>(graph_alloc(g, items.size() * sizeof(SweepItem)));

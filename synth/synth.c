@@ -159,10 +159,11 @@ typedef struct {
   uint64_t* first; /* smallest candidate index per key */
 } hset_t;
 
-/* Insert key seen at candidate k; returns 1 if the key is new. */
+/* Insert key seen at candidate k; returns 1 if the key is new, 0 if it was
+ * present, -1 if the table is full (callers keep it at most half full). */
 static inline int hset_insert(hset_t* h, uint64_t key, uint64_t k) {
   uint64_t i = sm64_mix(key) & h->mask;
-  for (;;) {
+  for (uint64_t probe = 0; probe <= h->mask; probe++) {
     uint64_t cur = __atomic_load_n(&h->keys[i], __ATOMIC_RELAXED);
     if (cur == EMPTY_KEY) {
       uint64_t exp = EMPTY_KEY;
@@ -181,6 +182,7 @@ static inline int hset_insert(hset_t* h, uint64_t key, uint64_t k) {
     }
     i = (i + 1) & h->mask;
   }
+  return -1;
 }
 
 typedef struct {
@@ -193,7 +195,14 @@ typedef struct {
 static void* ins_worker(void* p) {
   ins_job_t* j = (ins_job_t*)p;
   int64_t fresh = 0;
-  for (uint64_t k = j->k0; k < j->k1; k++) fresh += hset_insert(j->h, cand_key(j->c, k), k);
+  for (uint64_t k = j->k0; k < j->k1; k++) {
+    const int r = hset_insert(j->h, cand_key(j->c, k), k);
+    if (r < 0) {
+      j->fresh = -1;
+      return NULL;
+    }
+    fresh += r;
+  }
   j->fresh = fresh;
   return NULL;
 }
@@ -259,7 +268,8 @@ static void fisher_yates(int32_t* p, int32_t n, uint64_t key) {
 /*
  * Generate one graph. Returns 0 on success, negative on error:
  *   -1 bad arguments (including m > n_u*n_v), -2 out of memory,
- *   -3 the candidate stream did not reach m distinct edges.
+ *   -3 the candidate stream did not reach m distinct edges, -4 the
+ *   first-occurrence set filled up (an internal sizing error).
  * sign_model: 0 = iid (p_plus), 1 = camp (p_camp).
  */
 int synth_graph(uint64_t seed, int model, int32_t n_u, int32_t n_v, int64_t m, double gamma_u, double gamma_v,
@@ -309,6 +319,9 @@ int synth_graph(uint64_t seed, int model, int32_t n_u, int32_t n_v, int64_t m, d
   while (distinct < m) {
     uint64_t need = (uint64_t)(m - distinct);
     uint64_t win = need + need / 8 + 1024;
+    /* a window adds at most `win` keys: keep the set at most half full */
+    const uint64_t room = (h.mask + 1) / 2 - (uint64_t)distinct;
+    if (win > room) win = room;
     if (kdone + win > kmax) win = kmax - kdone;
     if (win == 0) { rc = -3; goto done; }
     ins_job_t jobs[256];
@@ -320,7 +333,10 @@ int synth_graph(uint64_t seed, int model, int32_t n_u, int32_t n_v, int64_t m, d
       jobs[t].fresh = 0;
     }
     run_jobs(ins_worker, jobs, sizeof(ins_job_t), threads);
-    for (int t = 0; t < threads; t++) distinct += jobs[t].fresh;
+    for (int t = 0; t < threads; t++) {
+      if (jobs[t].fresh < 0) { rc = -4; goto done; }
+      distinct += jobs[t].fresh;
+    }
     kdone += win;
   }
   /* flag[k] = 1 iff candidate k is the first occurrence of its pair */

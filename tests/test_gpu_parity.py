@@ -202,6 +202,33 @@ def test_batch_and_async_match_single_counts():
             h.free()
 
 
+def test_batch_plan_capture_and_replay_mixed_graphs():
+    """A batch plan over uneven graphs (empty, tiny, light-only and hub-heavy):
+    the first count captures the CUDA graph, the second replays it; both must
+    equal the oracle for every graph."""
+    import torch
+    graphs = [synth.batch_graph(i) for i in range(40)]
+    graphs.append(synth.Graph(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8), 5, 7))
+    graphs.append(synth.workload("chunglu-1m-200k-20m", scale=0.01))
+    graphs.append(synth.workload("uniform-2k-3k-20k"))
+    u, v, s = _kab(150, 90)
+    graphs.append(synth.Graph(u, v, s, 150, 90))
+    want = [oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[:2] for g in graphs]
+    handles = [dbbc.dbbc_graph_from_coo(g.u, g.v, g.s, g.n_u, g.n_v) for g in graphs]
+    try:
+        with dbbc.dbbc_batch_create(handles) as b:
+            for _ in range(2):
+                bal, unb = dbbc.dbbc_batch_count(b)
+                assert list(zip(bal.tolist(), unb.tolist())) == want
+            d_out = torch.full((len(handles), 2), -1, dtype=torch.int64, device="cuda")
+            dbbc.dbbc_batch_count_async(b, d_out)
+            got = [tuple(map(int, r)) for r in d_out.cpu().numpy().astype(np.uint64)]
+            assert got == want
+    finally:
+        for h in handles:
+            h.free()
+
+
 def test_torch_allocator_hook():
     g = synth.workload("chunglu-1m-200k-20m", scale=0.003)
     want = oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[:2]

@@ -75,3 +75,19 @@ def test_batch_sizes_in_range():
 def test_empty_graph():
     g = synth.generate(1, 10, 10, 0)
     assert g.m == 0
+
+
+@pytest.mark.timeout(60)
+def test_small_graph_with_large_sides_terminates():
+    # m far below the side sizes: the first insertion window must not
+    # overfill the first-occurrence set (it used to probe forever)
+    g = synth.batch_graph(144)
+    assert (g.n_u, g.n_v, g.m) == (16158, 394, 1001)
+    assert np.unique(g.u.astype(np.int64) * g.n_v + g.v).size == g.m
+    g = synth.generate(7, 20_000, 20_000, 10, model="chung-lu", gamma_u=2.2, gamma_v=2.2)
+    assert g.m == 10
+
+
+def test_whole_batch_generates():
+    gs = synth.batch(256)
+    assert len(gs) == 256 and all(g.m > 0 for g in gs)
