@@ -87,14 +87,25 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+KERNEL_SOURCES = ("count.cu", "count_device.cuh", "internal.h", "common.cuh")
+
+
+def kernel_source_sha() -> str:
+    """Hash of the sources the counting kernels are built from."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2609_21848_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
 def known_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (profiles/traffic.txt: kernel workload sha bytes)."""
+    the current kernel sources (profiles/traffic.txt: kernel workload sha bytes)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_2609_21848_gb300", "csrc", "count.cu")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+    sha = kernel_source_sha()
     for line in open(path):
         f = line.split("#", 1)[0].split()
         if len(f) == 4 and f[0] == kernel and f[1] == workload and f[2] == sha:
