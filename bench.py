@@ -53,8 +53,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dbbc", "reference"], default="dbbc")
-    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS) + ["batch-4096"])
+    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS) + ["batch-4096", "serve"])
     ap.add_argument("--n-graphs", type=int, default=4096, help="graphs in the batch-4096 workload")
+    ap.add_argument("--requests", type=int, default=4000, help="requests of the served workload")
+    ap.add_argument("--large-pool", type=int, default=4, help="distinct large graphs cycled by the served stream")
     ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the host-buffer end-to-end timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -162,8 +164,9 @@ def run_reference(a):
     if rank != 0:
         return
     nc = cores()
-    if a.workload == "batch-4096":
-        # graphs of the batch counted one after another by the oracle; each
+    if a.workload in ("batch-4096", "serve"):
+        # graphs of the batch (the served stream's small requests) counted one
+        # after another by the oracle; each
         # step a bounded sample of consecutive graphs (about 2 minutes overall)
         per_step = 120.0 / max(1, a.steps + a.warmup)
         graphs = [synth.batch_graph(i) for i in range(min(a.n_graphs, 512))]
@@ -184,7 +187,7 @@ def run_reference(a):
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": a.gpus,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_total / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-                "data": "synthetic", "config": {"workload": "batch-4096", "parallelism": "host threads"},
+                "data": "synthetic", "config": {"workload": a.workload, "parallelism": "host threads"},
                 "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": nc, "kind": "oracle",
                                  "sample": f"{done} batch graphs counted one after another, {nc} threads"},
                 "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -301,18 +304,28 @@ def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
     bit_exact_vs_plain = got == plain
     value = world * len(handles) * a.steps / (t_ms / 1e3)
     plain_gps = len(handles) / plain_s
-    # end to end: host COO (pinned) -> build every graph -> one batch count -> counts on the host
+    # end to end: host COO (pinned) -> one union build of all graphs ->
+    # per-component counts on the host
     hU, hV, hS = (torch.from_numpy(np.concatenate([getattr(g, k) for g in graphs])).pin_memory()
                   for k in ("u", "v", "s"))
+    nus, nvs = [g.n_u for g in graphs], [g.n_v for g in graphs]
+    torch.cuda.synchronize(dev)
+    e2e_times = []
+    for _ in range(2):  # the first run warms the allocator pools
+        t0 = time.perf_counter()
+        with dbbc.dbbc_graph_from_coo_multi(hU, hV, hS, offs, nus, nvs, stream=stream) as hu_:
+            bal, unb = dbbc.dbbc_count_components(hu_, stream)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = e2e_times[-1]
+    e2e_exact = list(zip(bal.tolist(), unb.tolist())) == plain
+    # the union path from device-resident COO (build + count), for comparison
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    hs = [dbbc.dbbc_graph_from_coo(hU[offs[i]:offs[i + 1]], hV[offs[i]:offs[i + 1]], hS[offs[i]:offs[i + 1]],
-                                   g.n_u, g.n_v, stream=stream) for i, g in enumerate(graphs)]
-    bal, unb = dbbc.dbbc_count_batch(hs, stream)
-    e2e_s = time.perf_counter() - t0
-    e2e_exact = list(zip(bal.tolist(), unb.tolist())) == plain
-    for h in hs:
-        h.free()
+    with dbbc.dbbc_graph_from_coo_multi(U, V, S, offs, nus, nvs, stream=stream) as hu_:
+        ub, uu = dbbc.dbbc_count_components(hu_, stream)
+    union_s = time.perf_counter() - t0
+    union_exact = list(zip(ub.tolist(), uu.tolist())) == plain
+
     # algorithmic bytes of one batch count (all tiers)
     nbytes = sum(B_WEDGE * i["wedges"] + B_LOWER * (i["lower_light"] + i["lower_medium"])
                  + B_CUR_INIT * i["hub_cursor_inits"] + B_CUR_STEP * i["hub_cursor_steps"] for i in infos)
@@ -329,6 +342,7 @@ def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
             "plain_graphs_per_s": plain_gps, "batched_over_plain": value / world / plain_gps,
             "batched_gwedges_per_s": wedges * a.steps / (t_ms / 1e3) / 1e9,
             "build_ms_all_graphs": build_ms, "generate_s": gen_s,
+            "union_build_and_count_graphs_per_s": len(handles) / union_s, "union_bit_exact": union_exact,
             "bit_exact_vs_plain": bit_exact_vs_plain,
             "e2e": {"value": world * len(handles) / e2e_s, "unit": "graphs/s",
                     "h2d_bytes_per_step": 9 * int(offs[-1]), "d2h_bytes_per_step": 16 * len(handles),
@@ -360,6 +374,102 @@ def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(a, torch, dbbc, world, rank, local, dist, barrier):
+    """The served form: a Poisson stream at 2,000 requests/s, 99% graphs of the
+    batch distribution and 1% large polarized graphs (5M-20M edges), served
+    with continuous batching (paper_2609_21848_gb300.serve). Reports latency
+    percentiles at that rate, the saturated throughput (every request arrives
+    at once), and the plain path (one request at a time: build, count, free)."""
+    from paper_2609_21848_gb300.serve import DbbcBackend, Request, Server, poisson_arrivals
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    rate = synth.SERVE["rate"]
+    n = a.requests
+    t0 = time.perf_counter()
+    small = synth.batch(min(n, 4096))
+    is_large = [synth.serve_is_large(i) for i in range(n)]
+    n_large = sum(is_large)
+    large = [synth.serve_large_graph(i) for i in range(min(a.large_pool, max(1, n_large)))] if n_large else []
+    gen_s = time.perf_counter() - t0
+    pinned = {}
+
+    def pin(key, g):
+        if key not in pinned:
+            pinned[key] = tuple(torch.from_numpy(x).pin_memory() for x in (g.u, g.v, g.s)) + (g.n_u, g.n_v)
+        return pinned[key]
+
+    picks = []
+    kl = 0
+    for i in range(n):
+        if is_large[i]:
+            picks.append(("L", kl % len(large)))
+            kl += 1
+        else:
+            picks.append(("S", i % len(small)))
+    graph_of = {("S", j): small[j] for j in range(len(small))}
+    graph_of.update({("L", j): large[j] for j in range(len(large))})
+    # each distinct graph counted alone (reference answers for the served results)
+    alone = {}
+    for key in set(picks):
+        g = graph_of[key]
+        pu, pv, ps, nu, nv = pin(key, g)
+        with dbbc.dbbc_graph_from_coo(pu, pv, ps, nu, nv, stream=stream) as h:
+            alone[key] = dbbc.dbbc_count(h, stream)
+
+    def requests(arrivals):
+        out = []
+        for i, key in enumerate(picks):
+            pu, pv, ps, nu, nv = pin(key, graph_of[key])
+            out.append(Request(i, pu, pv, ps, nu, nv, float(arrivals[i])))
+        return out
+
+    backend = DbbcBackend(local)
+    torch.cuda.synchronize(dev)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = dbbc.dbbc_kernel_launches()
+    st = Server(backend).run(requests(poisson_arrivals(n, rate, seed=synth.SEED_BASE + 4)))
+    torch.cuda.synchronize(dev)
+    launches = dbbc.dbbc_kernel_launches() - launches0
+    clocks = sampler.stop()
+    nominal = st.summary()
+    exact = all((r.balanced, r.unbalanced) == alone[picks[r.rid]] for r in st.results)
+    # saturated: the whole stream at once
+    st2 = Server(backend).run(requests(np.zeros(n)))
+    torch.cuda.synchronize(dev)
+    sat = st2.summary()
+    exact = exact and all((r.balanced, r.unbalanced) == alone[picks[r.rid]] for r in st2.results)
+    # plain: one request at a time
+    n_plain = min(n, 1000)
+    t0 = time.perf_counter()
+    for i in range(n_plain):
+        pu, pv, ps, nu, nv = pin(picks[i], graph_of[picks[i]])
+        with dbbc.dbbc_graph_from_coo(pu, pv, ps, nu, nv, stream=stream) as h:
+            dbbc.dbbc_count(h, stream)
+    torch.cuda.synchronize(dev)
+    plain_gps = n_plain / (time.perf_counter() - t0)
+    value = world * sat["graphs_per_s"]
+    edges = sum(graph_of[k].m for k in picks)
+    line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * sat["wall_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "serve", "requests": n, "rate_per_s": rate, "large_requests": n_large,
+                       "distinct_large_graphs": len(large), "edges_total": edges,
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "timing": "wall clock around the whole stream (host COO in pinned memory)"},
+            "served_at_rate": {k: nominal[k] for k in ("graphs_per_s", "p50_ms", "p99_ms", "max_ms", "batches",
+                                                     "wall_s")},
+            "saturated": {k: sat[k] for k in ("graphs_per_s", "p50_ms", "p99_ms", "batches", "wall_s")},
+            "plain_graphs_per_s": plain_gps, "served_over_plain": sat["graphs_per_s"] / plain_gps,
+            "bit_exact_vs_alone": exact, "generate_s": gen_s,
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 9 * edges,
+                    "d2h_bytes_per_step": 16 * n, "steps": 1, "bit_exact": exact},
+            "roofline": None, "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -381,8 +491,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    if a.workload == "batch-4096":
-        run_batch(a, torch, dbbc, world, rank, local, dist, barrier)
+    if a.workload in ("batch-4096", "serve"):
+        (run_batch if a.workload == "batch-4096" else run_serve)(a, torch, dbbc, world, rank, local, dist, barrier)
         if dist is not None:
             dist.destroy_process_group()
         return

@@ -80,6 +80,27 @@ enum {
 DBBC_API dbbc_status dbbc_graph_from_coo(const int32_t* u, const int32_t* v, const int8_t* sign, int64_t m, int32_t n_u,
                                 int32_t n_v, uint32_t flags, void* cuda_stream, dbbc_graph** out);
 
+/* Build the disjoint union of n_graphs graphs as one handle. Graph i's edges
+ * are u, v, sign [edge_offsets[i], edge_offsets[i+1]) with ids local to graph
+ * i (0 <= u < n_u[i], 0 <= v < n_v[i]); edge_offsets (n_graphs + 1 entries,
+ * starting at 0), n_u and n_v are HOST arrays; u, v, sign are host or device
+ * per `flags` as in dbbc_graph_from_coo. Butterflies never span two
+ * components, and shifting each component's ids by a constant per side keeps
+ * its Def. 3 order, so dbbc_count_components returns exactly what counting
+ * every graph alone would (Theorem 1); dbbc_count returns their sum. One build
+ * pipeline serves all graphs. Errors as dbbc_graph_from_coo; the union must
+ * have < 2^31 edges and < 2^31 vertices. */
+DBBC_API dbbc_status dbbc_graph_from_coo_multi(const int32_t* u, const int32_t* v, const int8_t* sign,
+                                               const int64_t* edge_offsets, const int32_t* n_u, const int32_t* n_v,
+                                               int32_t n_graphs, uint32_t flags, void* cuda_stream,
+                                               dbbc_graph** out);
+
+/* Per-component counts of a handle: balanced[i] and unbalanced[i] (host
+ * arrays of n_components entries, see dbbc_graph_info) for component i of a
+ * dbbc_graph_from_coo_multi handle; one entry for a plain handle. Synchronous. */
+DBBC_API dbbc_status dbbc_count_components(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced,
+                                           uint64_t* unbalanced);
+
 /* Count balanced and unbalanced butterflies of one graph (Algorithm 1,
  * Phase 5, with the Lemma 1 unbalanced count). Host out-parameters; the call
  * returns after the counts are on the host. Either pointer may be NULL. */
@@ -166,6 +187,7 @@ typedef struct {
   int64_t hub_cursor_inits;  /* sum over hub items of the hub's lower neighbours */
   int64_t hub_cursor_steps;  /* sum over hub items of lower neighbours x windows */
   size_t device_bytes; /* device memory held by the handle */
+  int32_t n_components; /* graphs in a dbbc_graph_from_coo_multi handle, else 1 */
 } dbbc_graph_info;
 
 /* Sizes and the per-tier wedge split of a built graph. */

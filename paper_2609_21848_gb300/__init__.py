@@ -31,7 +31,7 @@ EXPORTED = (
     "dbbc_graph_get_info", "dbbc_graph_device_bytes", "dbbc_estimate_bytes", "dbbc_graph_free",
     "dbbc_graph_export", "dbbc_set_allocator", "dbbc_status_string", "dbbc_version", "dbbc_count_profiled",
     "dbbc_kernel_launches", "dbbc_count_noalloc", "dbbc_batch_create", "dbbc_batch_count_async",
-    "dbbc_batch_count", "dbbc_batch_free",
+    "dbbc_batch_count", "dbbc_batch_free", "dbbc_graph_from_coo_multi", "dbbc_count_components",
 )
 
 
@@ -48,7 +48,8 @@ class GraphInfo(ctypes.Structure):
                 ("wedges_light", ctypes.c_uint64), ("wedges_medium", ctypes.c_uint64),
                 ("wedges_hub", ctypes.c_uint64), ("lower_light", ctypes.c_int64), ("lower_medium", ctypes.c_int64),
                 ("lower_hub", ctypes.c_int64), ("hub_items", ctypes.c_int64), ("hub_cursor_inits", ctypes.c_int64),
-                ("hub_cursor_steps", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+                ("hub_cursor_steps", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
+                ("n_components", ctypes.c_int32)]
 
 
 class CountProfile(ctypes.Structure):
@@ -89,6 +90,10 @@ def lib() -> ctypes.CDLL:
         L.dbbc_count_profiled.restype = st
         L.dbbc_kernel_launches.argtypes = []
         L.dbbc_kernel_launches.restype = ctypes.c_uint64
+        L.dbbc_graph_from_coo_multi.argtypes = [P, P, P, P, P, P, I32, U32, P, ctypes.POINTER(P)]
+        L.dbbc_graph_from_coo_multi.restype = st
+        L.dbbc_count_components.argtypes = [P, P, P, P]
+        L.dbbc_count_components.restype = st
         L.dbbc_batch_create.argtypes = [P, I32, P, ctypes.POINTER(P)]
         L.dbbc_batch_create.restype = st
         L.dbbc_batch_count_async.argtypes = [P, P, P]
@@ -203,6 +208,40 @@ def dbbc_graph_from_coo(u, v, sign, n_u: int, n_v: int, *, reject_duplicates: bo
            "dbbc_graph_from_coo")
     del ku, kv, ks
     return Graph(h.value)
+
+
+def dbbc_graph_from_coo_multi(u, v, sign, edge_offsets, n_u, n_v, *, reject_duplicates: bool = False,
+                              stream=None) -> Graph:
+    """Build the disjoint union of several graphs (edges of graph i at
+    [edge_offsets[i], edge_offsets[i+1]), ids local to graph i) as one handle;
+    see :func:`dbbc_count_components`."""
+    pu, mu, du, ku = _array_ptr(u, np.int32)
+    pv, mv, dv, kv = _array_ptr(v, np.int32)
+    ps, ms, ds, ks = _array_ptr(sign, np.int8)
+    off = np.ascontiguousarray(edge_offsets, dtype=np.int64)
+    nu = np.ascontiguousarray(n_u, dtype=np.int32)
+    nv = np.ascontiguousarray(n_v, dtype=np.int32)
+    k = nu.shape[0]
+    if not (mu == mv == ms) or nv.shape[0] != k or off.shape[0] != k + 1 or (k and off[-1] != mu):
+        raise ValueError("inconsistent arrays")
+    if not (du == dv == ds):
+        raise ValueError("u, v and sign must all be on the host or all on the device")
+    flags = (DBBC_INPUT_DEVICE if du else DBBC_INPUT_HOST) | (DBBC_DUP_REJECT if reject_duplicates else 0)
+    h = ctypes.c_void_p()
+    _check(lib().dbbc_graph_from_coo_multi(pu, pv, ps, off.ctypes.data, nu.ctypes.data, nv.ctypes.data, k, flags,
+                                           _stream_ptr(stream), ctypes.byref(h)), "dbbc_graph_from_coo_multi")
+    del ku, kv, ks
+    return Graph(h.value)
+
+
+def dbbc_count_components(g: Graph, stream=None) -> tuple[np.ndarray, np.ndarray]:
+    """Per-component (balanced, unbalanced) of a union handle."""
+    n = dbbc_graph_get_info(g)["n_components"]
+    bal = np.zeros(max(n, 1), np.uint64)
+    unb = np.zeros(max(n, 1), np.uint64)
+    _check(lib().dbbc_count_components(g.handle, _stream_ptr(stream), bal.ctypes.data, unb.ctypes.data),
+           "dbbc_count_components")
+    return bal[:n], unb[:n]
 
 
 def dbbc_count(g: Graph, stream=None) -> tuple[int, int]:

@@ -124,6 +124,35 @@ dbbc_status dbbc_graph_from_coo(const int32_t* u, const int32_t* v, const int8_t
   return DBBC_OK;
 }
 
+dbbc_status dbbc_graph_from_coo_multi(const int32_t* u, const int32_t* v, const int8_t* sign,
+                                      const int64_t* edge_offsets, const int32_t* n_u, const int32_t* n_v,
+                                      int32_t n_graphs, uint32_t flags, void* cuda_stream, dbbc_graph** out) {
+  if (!out || n_graphs < 0 || (flags & ~3u) != 0) return DBBC_EINVAL;
+  if (n_graphs > 0 && (!edge_offsets || !n_u || !n_v)) return DBBC_EINVAL;
+  if (n_graphs > 0 && edge_offsets[n_graphs] > 0 && (!u || !v || !sign)) return DBBC_EINVAL;
+  dbbc_graph* g = nullptr;
+  try {
+    g = new dbbc_graph();
+  } catch (...) {
+    return DBBC_ENOMEM;
+  }
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  const int64_t zero = 0;
+  const dbbc_status st = guarded([&] {
+    DBBC_CUDA(cudaGetDevice(&g->device));
+    build_graph_multi(g, u, v, sign, n_graphs > 0 ? edge_offsets : &zero, n_u, n_v, n_graphs,
+                      (flags & DBBC_INPUT_DEVICE) != 0, (flags & DBBC_DUP_REJECT) != 0, g->stream);
+  });
+  if (st != DBBC_OK) {
+    free_graph_memory(g);
+    (void)cudaStreamSynchronize(g->stream);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return DBBC_OK;
+}
+
 void dbbc_graph_free(dbbc_graph* g) {
   if (!g) return;
   free_graph_memory(g);
@@ -165,6 +194,7 @@ dbbc_status dbbc_graph_get_info(const dbbc_graph* g, dbbc_graph_info* info) {
   r.hub_cursor_inits = g->hub_cursor_inits;
   r.hub_cursor_steps = g->hub_cursor_steps;
   r.device_bytes = g->device_bytes;
+  r.n_components = g->n_components;
   *info = r;
   return DBBC_OK;
 }

@@ -52,6 +52,25 @@ __global__ void gather_pivots_kernel(const GatherJob* __restrict__ jobs, BatchPi
     light[j.light_off + i] = BatchPivot{gi, j.order[j.n_hub + j.n_medium + i]};
 }
 
+// Pivots of a disjoint union, tagged with their component.
+__global__ void gather_component_pivots_kernel(const int32_t* __restrict__ order, int64_t n_hub, int64_t n_medium,
+                                               int64_t n_light, const int32_t* __restrict__ comp,
+                                               BatchPivot* __restrict__ med, BatchPivot* __restrict__ light) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_medium + n_light; i += stride) {
+    const int32_t row = order[n_hub + i];
+    const BatchPivot bp{comp[row], row};
+    if (i < n_medium) med[i] = bp;
+    else light[i - n_medium] = bp;
+  }
+}
+
+__global__ void gather_rows_kernel(const int32_t* __restrict__ comp, const int32_t* __restrict__ rows, int64_t n,
+                                   int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = comp[rows[i]];
+}
+
 __device__ __forceinline__ void warp_flush(int graph, uint64_t& bal, uint64_t& unb, unsigned long long* out) {
   const uint64_t b = warp_sum_u64(bal), u = warp_sum_u64(unb);
   if (lane_id() == 0 && graph >= 0) {
@@ -265,6 +284,44 @@ static void batch_release(dbbc_batch* b) {
   b->capture = nullptr;
 }
 
+static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector<BatchHubItem>& items);
+
+// Plan for the components of one union handle: every component shares the
+// union's CSR; pivots and hub items are tagged with their component.
+static void plan_components(dbbc_batch* b, const dbbc_graph* g) {
+  cudaStream_t s = b->stream;
+  std::vector<GraphDesc> desc((size_t)b->n_graphs, GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u, 0});
+  b->n_medium = g->n_medium;
+  b->n_light = g->n_light;
+  b->max_lower = std::max<int64_t>(1, g->sweep_max_lower);
+  // components of the hub items' rows
+  const size_t nh = g->sweep_items_host.size();
+  std::vector<int32_t> rows(nh), comps(nh);
+  for (size_t k = 0; k < nh; k++) rows[k] = g->sweep_items_host[k].row;
+  std::vector<BatchHubItem> items(nh);
+  if (nh > 0) {
+    Scratch sc(s);
+    int32_t* d_rows = sc.get<int32_t>(nh);
+    int32_t* d_comp = sc.get<int32_t>(nh);
+    DBBC_CUDA(cudaMemcpyAsync(d_rows, rows.data(), nh * 4, cudaMemcpyHostToDevice, s));
+    gather_rows_kernel<<<(unsigned)std::min<size_t>((nh + 255) / 256, 4096), 256, 0, s>>>(g->component, d_rows,
+                                                                                        (int64_t)nh, d_comp);
+    DBBC_LAUNCH_CHECK();
+    DBBC_CUDA(cudaMemcpyAsync(comps.data(), d_comp, nh * 4, cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaStreamSynchronize(s));
+  }
+  // the union's items are already in descending estimated work
+  for (size_t k = 0; k < nh; k++) items[k] = BatchHubItem{comps[k], 0, g->sweep_items_host[k]};
+  finish_plan(b, desc, items);
+  if (b->n_medium + b->n_light > 0) {
+    const int64_t total = b->n_medium + b->n_light;
+    gather_component_pivots_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, s>>>(
+        g->order, g->n_hub, g->n_medium, g->n_light, g->component, b->medium, b->light);
+    DBBC_LAUNCH_CHECK();
+  }
+  DBBC_CUDA(cudaStreamSynchronize(s));
+}
+
 static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
   const int32_t n = b->n_graphs;
   cudaStream_t s = b->stream;
@@ -288,8 +345,21 @@ static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
   std::stable_sort(hubs.begin(), hubs.end(), [](const HubRef& a, const HubRef& c) { return a.est > c.est; });
   std::vector<BatchHubItem> items(hubs.size());
   for (size_t k = 0; k < hubs.size(); k++) items[k] = hubs[k].item;
-  b->n_hub_items = (int64_t)items.size();
+  finish_plan(b, desc, items);
+  GatherJob* d_jobs = static_cast<GatherJob*>(batch_alloc(b, jobs.size() * sizeof(GatherJob)));
+  DBBC_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(GatherJob), cudaMemcpyHostToDevice, s));
+  if (n > 0) {
+    gather_pivots_kernel<<<(unsigned)n, 256, 0, s>>>(d_jobs, b->medium, b->light);
+    DBBC_LAUNCH_CHECK();
+  }
+  DBBC_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
+}
 
+// Allocations, launch shapes and uploads shared by both kinds of plan.
+static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector<BatchHubItem>& items) {
+  cudaStream_t s = b->stream;
+  const int32_t n = b->n_graphs;
+  b->n_hub_items = (int64_t)items.size();
   b->desc = static_cast<GraphDesc*>(batch_alloc(b, desc.size() * sizeof(GraphDesc)));
   b->light = static_cast<BatchPivot*>(batch_alloc(b, (size_t)b->n_light * sizeof(BatchPivot)));
   b->medium = static_cast<BatchPivot*>(batch_alloc(b, (size_t)b->n_medium * sizeof(BatchPivot)));
@@ -298,7 +368,6 @@ static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
   b->counters = static_cast<int*>(batch_alloc(b, 2 * sizeof(int)));
   b->status = static_cast<unsigned*>(batch_alloc(b, sizeof(unsigned)));
   const size_t smem = (size_t)kSweepWindow16 * 4;
-  DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   b->hub_grid = num_sms() * blocks_per_sm((const void*)hub_sweep_batch_kernel, kSweepThreads, smem);
   if (b->n_hub_items > 0)
     b->cursors = static_cast<int64_t*>(batch_alloc(b, (size_t)b->hub_grid * (size_t)b->max_lower * 16));
@@ -312,16 +381,10 @@ static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
                                                       (size_t)kMediumSlots * 12);
     b->medium_grid = (int)std::max<int64_t>(1, std::min<int64_t>(b->n_medium, mcap));
   }
-  GatherJob* d_jobs = static_cast<GatherJob*>(batch_alloc(b, jobs.size() * sizeof(GatherJob)));
   DBBC_CUDA(cudaMemcpyAsync(b->desc, desc.data(), desc.size() * sizeof(GraphDesc), cudaMemcpyHostToDevice, s));
-  DBBC_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(GatherJob), cudaMemcpyHostToDevice, s));
   if (!items.empty())
     DBBC_CUDA(cudaMemcpyAsync(b->hub, items.data(), items.size() * sizeof(BatchHubItem), cudaMemcpyHostToDevice, s));
-  if (n > 0) {
-    gather_pivots_kernel<<<(unsigned)n, 256, 0, s>>>(d_jobs, b->medium, b->light);
-    DBBC_LAUNCH_CHECK();
-  }
-  DBBC_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
+  DBBC_CUDA(cudaStreamSynchronize(s));  // host vectors must outlive the copies
 }
 
 // The batch count: clear outputs and counters, then the three tiers.
@@ -458,6 +521,38 @@ dbbc_status dbbc_batch_count(dbbc_batch* b, void* cuda_stream, uint64_t* balance
   });
   if (st != DBBC_OK) return st;
   for (int32_t i = 0; i < b->n_graphs; i++) {
+    balanced[i] = h[2 * (size_t)i];
+    unbalanced[i] = h[2 * (size_t)i + 1];
+  }
+  return DBBC_OK;
+}
+
+dbbc_status dbbc_count_components(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced,
+                                  uint64_t* unbalanced) {
+  if (!g || !balanced || !unbalanced) return DBBC_EINVAL;
+  if (!g->component) return dbbc_count(g, cuda_stream, balanced, unbalanced);
+  const int32_t n = g->n_components;
+  if (n == 0) return DBBC_OK;
+  dbbc_batch* b = nullptr;
+  try {
+    b = new dbbc_batch();
+  } catch (...) {
+    return DBBC_ENOMEM;
+  }
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->n_graphs = n;
+  std::vector<uint64_t> h((size_t)n * 2);
+  const dbbc_status st = batch_guard([&] {
+    DBBC_CUDA(cudaGetDevice(&b->device));
+    set_batch_attributes();
+    plan_components(b, g);
+    enqueue_batch(b, b->stream);
+    DBBC_CUDA(cudaMemcpyAsync(h.data(), b->out, h.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+    check_batch_status(b, b->stream);
+  });
+  dbbc_batch_free(b);
+  if (st != DBBC_OK) return st;
+  for (int32_t i = 0; i < n; i++) {
     balanced[i] = h[2 * (size_t)i];
     unbalanced[i] = h[2 * (size_t)i + 1];
   }

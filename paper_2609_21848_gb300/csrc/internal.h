@@ -109,6 +109,10 @@ struct dbbc_graph {
   std::vector<uint64_t> sweep_est_host;           // their estimated accepted wedges
   int64_t sweep_max_lower = 0;  // largest lower-neighbour count of a hub (cursor scratch per CTA)
   int64_t narrow_ranks_u = 0, narrow_ranks_v = 0;  // per side: vertices of degree < 2^16 (a rank prefix)
+  // disjoint union of several graphs (dbbc_graph_from_coo_multi): component
+  // of every row, 0 for a plain handle (n_components == 1)
+  int32_t n_components = 1;
+  int32_t* component = nullptr;  // [n] or nullptr for a plain handle
   size_t device_bytes = 0;
   std::vector<void*> allocations;
 };
@@ -116,8 +120,20 @@ struct dbbc_graph {
 namespace dbbc {
 
 // prep.cu
+// Components of a union being built: host and device copies of the per-side
+// id offsets (n_graphs + 1 entries each) and the largest side of any component.
+struct UnionSpec {
+  int32_t n_graphs = 1;
+  std::vector<int64_t> uoff, voff;
+  const int64_t* d_uoff = nullptr;
+  const int64_t* d_voff = nullptr;
+  int64_t max_side = 0;
+};
 void build_graph(dbbc_graph* g, const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, bool on_device,
-                 bool reject_duplicates, cudaStream_t stream);
+                 bool reject_duplicates, cudaStream_t stream, const UnionSpec* un = nullptr);
+void build_graph_multi(dbbc_graph* g, const int32_t* u, const int32_t* v, const int8_t* s,
+                       const int64_t* edge_offsets, const int32_t* n_u, const int32_t* n_v, int32_t n_graphs,
+                       bool on_device, bool reject_duplicates, cudaStream_t stream);
 void free_graph_memory(dbbc_graph* g);
 void* graph_alloc(dbbc_graph* g, size_t bytes);
 

@@ -9,7 +9,44 @@
 
 namespace dbbc {
 
+// Components of a disjoint union as seen by the kernels: component c owns the
+// side ids (and, after ranking, the side ranks) [uoff[c], uoff[c+1]) of U and
+// [voff[c], voff[c+1]) of V. A plain graph is one component.
+struct UnionView {
+  const int64_t* uoff;
+  const int64_t* voff;
+  int32_t n_graphs;
+};
+
+__device__ __forceinline__ int32_t component_of(const int64_t* off, int32_t n_graphs, int64_t side_id) {
+  int64_t lo = 0, hi = (int64_t)n_graphs + 1;  // upper_bound over off[0 .. n_graphs]
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= side_id) lo = mid + 1; else hi = mid;
+  }
+  return (int32_t)(lo - 1);
+}
+
 // ------------------------------------------------------------------ kernels
+template <typename T>
+__device__ __forceinline__ int64_t lower_bound_dev(const T* a, int64_t n, T x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+template <typename T>
+__device__ __forceinline__ int64_t upper_bound_dev(const T* a, int64_t n, T x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 __global__ void validate_kernel(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
                                 const int8_t* __restrict__ s, int64_t m, int32_t n_u, int32_t n_v, unsigned* err) {
   unsigned e = 0;
@@ -78,26 +115,34 @@ __global__ void degree_kernel(const int32_t* __restrict__ eu, const int32_t* __r
   }
 }
 
-// Sort key per vertex: (side, degree, side-local id). Ascending order is the
-// Def. 3 priority within each side; V ids follow U ids in the unified space.
-__global__ void vertex_keys_kernel(const int32_t* __restrict__ deg, int64_t n, int32_t n_u, int bits_deg,
-                                   int bits_id, uint64_t* __restrict__ key) {
+// Sort key per vertex: (side, component, degree, id within the component).
+// Ascending order is the Def. 3 priority within each side of each component
+// (V ids follow U ids in the unified space); components occupy contiguous
+// rank ranges, which keeps a component's accepted endpoints together.
+__global__ void vertex_keys_kernel(const int32_t* __restrict__ deg, int64_t n, int32_t n_u, int bits_comp,
+                                   int bits_deg, int bits_id, UnionView un, uint64_t* __restrict__ key) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t side = x >= n_u ? 1 : 0;
-    const uint64_t local = side ? (uint64_t)(x - n_u) : (uint64_t)x;
-    key[x] = (side << (bits_deg + bits_id)) | ((uint64_t)deg[x] << bits_id) | local;
+    const int64_t sid = side ? x - n_u : x;
+    const int64_t* off = side ? un.voff : un.uoff;
+    const int32_t c = component_of(off, un.n_graphs, sid);
+    const uint64_t local = (uint64_t)(sid - off[c]);
+    key[x] = (side << (bits_comp + bits_deg + bits_id)) | ((uint64_t)c << (bits_deg + bits_id)) |
+             ((uint64_t)deg[x] << bits_id) | local;
   }
 }
 
-__global__ void ranks_kernel(const uint64_t* __restrict__ skey, int64_t n, int32_t n_u, int bits_deg, int bits_id,
-                             int32_t* __restrict__ vertex, int32_t* __restrict__ side_rank,
+__global__ void ranks_kernel(const uint64_t* __restrict__ skey, int64_t n, int32_t n_u, int bits_comp, int bits_deg,
+                             int bits_id, UnionView un, int32_t* __restrict__ vertex, int32_t* __restrict__ side_rank,
                              int32_t* __restrict__ rowdeg) {
   const uint64_t id_mask = (1ull << bits_id) - 1, deg_mask = (1ull << bits_deg) - 1;
+  const uint64_t comp_mask = (1ull << bits_comp) - 1;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = skey[r];
-    const bool side = (k >> (bits_deg + bits_id)) & 1;
-    const int32_t local = (int32_t)(k & id_mask);
-    const int32_t x = side ? n_u + local : local;
+    const bool side = (k >> (bits_comp + bits_deg + bits_id)) & 1;
+    const int32_t c = bits_comp ? (int32_t)((k >> (bits_deg + bits_id)) & comp_mask) : 0;
+    const int64_t local = (int64_t)(k & id_mask);
+    const int32_t x = side ? (int32_t)(n_u + un.voff[c] + local) : (int32_t)(un.uoff[c] + local);
     vertex[r] = x;
     side_rank[x] = side ? (int32_t)(r - n_u) : (int32_t)r;
     rowdeg[r] = (int32_t)((k >> bits_id) & deg_mask);
@@ -133,38 +178,27 @@ __global__ void csr_cols_kernel(const uint64_t* __restrict__ key, int64_t nnz, i
     col[i] = (uint32_t)(key[i] & mask);
 }
 
-template <typename T>
-__device__ __forceinline__ int64_t lower_bound_dev(const T* a, int64_t n, T x) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-template <typename T>
-__device__ __forceinline__ int64_t upper_bound_dev(const T* a, int64_t n, T x) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (a[mid] <= x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
 // lower[r] = neighbours of row r with lower Def. 3 priority. A U vertex of
 // degree d is above a V vertex iff deg(v) < d (equal degree: the V id is
 // larger); a V vertex of degree d is above a U vertex iff deg(u) <= d.
-// Rows list neighbours by ascending side rank, so the lower ones are a prefix.
+// Neighbours lie in the row's own component, whose other-side ranks ascend by
+// degree, and rows list neighbours by ascending side rank, so the lower ones
+// are a prefix.
 __global__ void lower_kernel(const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
-                             const int32_t* __restrict__ rowdeg, int64_t n, int32_t n_u,
+                             const int32_t* __restrict__ rowdeg, int64_t n, int32_t n_u, UnionView un,
                              uint32_t* __restrict__ lower) {
-  const int32_t n_v = (int32_t)(n - n_u);
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
     const int32_t d = rowdeg[r];
     int64_t t;  // side rank threshold in the other side
-    if (r < n_u) t = lower_bound_dev<int32_t>(rowdeg + n_u, n_v, d);
-    else t = upper_bound_dev<int32_t>(rowdeg, n_u, d);
+    if (r < n_u) {
+      const int32_t c = component_of(un.uoff, un.n_graphs, r);
+      const int64_t b = un.voff[c], e = un.voff[c + 1];
+      t = b + lower_bound_dev<int32_t>(rowdeg + n_u + b, e - b, d);
+    } else {
+      const int32_t c = component_of(un.voff, un.n_graphs, r - n_u);
+      const int64_t b = un.uoff[c], e = un.uoff[c + 1];
+      t = b + upper_bound_dev<int32_t>(rowdeg + b, e - b, d);
+    }
     const int64_t b = row_ptr[r];
     lower[r] = (uint32_t)lower_bound_dev<uint32_t>(col + b, row_ptr[r + 1] - b, (uint32_t)(t << 1));
   }
@@ -281,6 +315,48 @@ __global__ void narrow_ranks_kernel(const int32_t* __restrict__ rowdeg, int64_t 
   if (threadIdx.x == 1) out[1] = lower_bound_dev<int32_t>(rowdeg + n_u, n - n_u, limit);
 }
 
+// Union of several graphs: graph i's local ids are validated against its own
+// sides and shifted by the sizes of the graphs before it.
+__global__ void union_ids_kernel(const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                 const int8_t* __restrict__ s, const int64_t* __restrict__ eoff,
+                                 const int32_t* __restrict__ nu, const int32_t* __restrict__ nv,
+                                 const int64_t* __restrict__ uoff, const int64_t* __restrict__ voff, int32_t n_graphs,
+                                 int32_t* __restrict__ ou, int32_t* __restrict__ ov, int8_t* __restrict__ os,
+                                 unsigned* err) {
+  unsigned e = 0;
+  for (int32_t gi = blockIdx.x; gi < n_graphs; gi += gridDim.x) {
+    const int64_t e0 = eoff[gi], e1 = eoff[gi + 1];
+    const int32_t a = nu[gi], b = nv[gi];
+    const int32_t du = (int32_t)uoff[gi], dv = (int32_t)voff[gi];
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+      const int32_t x = u[i], y = v[i];
+      const int8_t c = s[i];
+      if (x < 0 || x >= a) e |= 1u;
+      if (y < 0 || y >= b) e |= 2u;
+      if (c != 1 && c != -1) e |= 4u;
+      ou[i] = x + du;
+      ov[i] = y + dv;
+      os[i] = c;
+    }
+  }
+  e = __reduce_or_sync(kFullMask, e);
+  if (lane_id() == 0 && e) atomicOr(err, e);
+}
+
+// Component of every row of a union: the graph whose id range holds the
+// row's vertex.
+__global__ void component_kernel(const int32_t* __restrict__ vertex, int64_t n, int32_t n_u_total,
+                                 const int64_t* __restrict__ uoff, const int64_t* __restrict__ voff, int32_t n_graphs,
+                                 int32_t* __restrict__ comp) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = vertex[r];
+    const bool is_u = x < n_u_total;
+    const int64_t key = is_u ? x : (int64_t)x - n_u_total;
+    const int64_t* off = is_u ? uoff : voff;
+    comp[r] = (int32_t)upper_bound_dev<int64_t>(off, (int64_t)n_graphs + 1, key) - 1;
+  }
+}
+
 __global__ void gather_u32_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx, int64_t n,
                                   uint32_t* __restrict__ dst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -321,7 +397,7 @@ static T read_back(const T* d, cudaStream_t s) {
   return h;
 }
 
-static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
+static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
   if (g->n_hub == 0) return;
   std::vector<uint32_t> rows((size_t)g->n_hub), lows((size_t)g->n_hub);
   std::vector<uint64_t> works((size_t)g->n_hub);
@@ -357,10 +433,18 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
     const uint64_t W = works[h];
     const bool is_u = row < g->n_u;
     const uint64_t sp = is_u ? (uint64_t)row : (uint64_t)(row - g->n_u);
+    // the hub's accepted endpoints are the ranks of its own component below it
+    const std::vector<int64_t>& off = is_u ? un.uoff : un.voff;
+    const uint64_t start =
+        (uint64_t)off[(size_t)(std::upper_bound(off.begin(), off.end(), (int64_t)sp) - off.begin() - 1)];
+    // narrow counters below the side's first endpoint of degree >= 2^16 (for
+    // a union, whose ranks are component-major, only when every count fits)
     const uint64_t narrow_end =
-        L < (uint32_t)kNarrowCountLimit ? sp : std::min<uint64_t>(sp, (uint64_t)(is_u ? g->narrow_ranks_u
-                                                                                        : g->narrow_ranks_v));
-    const uint64_t Rn = (narrow_end + kSweepWindow16 - 1) / kSweepWindow16;
+        L < (uint32_t)kNarrowCountLimit ? sp
+        : un.n_graphs > 1               ? start
+                                        : std::max<uint64_t>(start, std::min<uint64_t>(
+                                              sp, (uint64_t)(is_u ? g->narrow_ranks_u : g->narrow_ranks_v)));
+    const uint64_t Rn = (narrow_end - start + kSweepWindow16 - 1) / kSweepWindow16;
     const uint64_t Rw = (sp - narrow_end + kSweepWindow32 - 1) / kSweepWindow32;
     const uint64_t target = std::max<uint64_t>(kSweepItemWork, 64ull * L);
     max_lower = std::max<int64_t>(max_lower, L);
@@ -386,8 +470,9 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
     const uint64_t spans = std::max<uint64_t>(1, std::min<uint64_t>(Rn, W / target));
     for (uint64_t k = 0; k < spans && Rn > 0; k++) {
       const uint64_t w0 = Rn * k / spans, w1 = Rn * (k + 1) / spans;
-      if (w1 > w0) add(w0 * kSweepWindow16, std::min<uint64_t>(narrow_end, w1 * kSweepWindow16), kSweepWindow16, 0,
-                       W / spans);
+      if (w1 > w0)
+        add(start + w0 * kSweepWindow16, std::min<uint64_t>(narrow_end, start + w1 * kSweepWindow16),
+            kSweepWindow16, 0, W / spans);
     }
     if (sp > narrow_end) add(narrow_end, sp, kSweepWindow32, 1, W / (spans + 1));
   }
@@ -407,13 +492,104 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s) {
   DBBC_CUDA(cudaStreamSynchronize(s));
 }
 
+void build_graph_multi(dbbc_graph* g, const int32_t* u, const int32_t* v, const int8_t* sgn,
+                       const int64_t* edge_offsets, const int32_t* n_u, const int32_t* n_v, int32_t n_graphs,
+                       bool on_device, bool reject_duplicates, cudaStream_t s) {
+  // host metadata: edge ranges and the id shift of every graph
+  std::vector<int64_t> uoff((size_t)n_graphs + 1, 0), voff((size_t)n_graphs + 1, 0);
+  for (int32_t i = 0; i < n_graphs; i++) {
+    if (n_u[i] < 0 || n_v[i] < 0 || edge_offsets[i + 1] < edge_offsets[i])
+      throw Error{DBBC_EINVAL, "bad component sizes or edge offsets"};
+    uoff[(size_t)i + 1] = uoff[(size_t)i] + n_u[i];
+    voff[(size_t)i + 1] = voff[(size_t)i] + n_v[i];
+  }
+  const int64_t m = edge_offsets[n_graphs] - edge_offsets[0];
+  if (edge_offsets[0] != 0 || m >= (int64_t{1} << 31) || uoff.back() + voff.back() >= (int64_t{1} << 31))
+    throw Error{DBBC_EINVAL, "union too large"};
+  g->n_u = (int32_t)uoff.back();
+  g->n_v = (int32_t)voff.back();
+  Scratch sc(s);
+  const int32_t* du = u;
+  const int32_t* dv = v;
+  const int8_t* ds = sgn;
+  if (!on_device && m > 0) {
+    int32_t* tu = sc.get<int32_t>((size_t)m);
+    int32_t* tv = sc.get<int32_t>((size_t)m);
+    int8_t* ts = sc.get<int8_t>((size_t)m);
+    DBBC_CUDA(cudaMemcpyAsync(tu, u, (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    DBBC_CUDA(cudaMemcpyAsync(tv, v, (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    DBBC_CUDA(cudaMemcpyAsync(ts, sgn, (size_t)m, cudaMemcpyHostToDevice, s));
+    du = tu;
+    dv = tv;
+    ds = ts;
+  }
+  int64_t* d_meta = sc.get<int64_t>((size_t)3 * (n_graphs + 1));
+  int32_t* d_n = sc.get<int32_t>((size_t)2 * n_graphs + 2);
+  std::vector<int32_t> nn((size_t)2 * n_graphs + 2, 0);
+  std::copy(n_u, n_u + n_graphs, nn.begin());
+  std::copy(n_v, n_v + n_graphs, nn.begin() + n_graphs);
+  DBBC_CUDA(cudaMemcpyAsync(d_meta, edge_offsets, (size_t)(n_graphs + 1) * 8, cudaMemcpyHostToDevice, s));
+  DBBC_CUDA(cudaMemcpyAsync(d_meta + n_graphs + 1, uoff.data(), uoff.size() * 8, cudaMemcpyHostToDevice, s));
+  DBBC_CUDA(cudaMemcpyAsync(d_meta + 2 * (n_graphs + 1), voff.data(), voff.size() * 8, cudaMemcpyHostToDevice, s));
+  DBBC_CUDA(cudaMemcpyAsync(d_n, nn.data(), nn.size() * 4, cudaMemcpyHostToDevice, s));
+  int32_t* ou = sc.get<int32_t>((size_t)std::max<int64_t>(m, 1));
+  int32_t* ov = sc.get<int32_t>((size_t)std::max<int64_t>(m, 1));
+  int8_t* os = sc.get<int8_t>((size_t)std::max<int64_t>(m, 1));
+  unsigned* d_err = sc.get<unsigned>(1);
+  DBBC_CUDA(cudaMemsetAsync(d_err, 0, sizeof(unsigned), s));
+  if (n_graphs > 0 && m > 0) {
+    union_ids_kernel<<<(unsigned)std::min<int32_t>(n_graphs, 65535), 256, 0, s>>>(
+        du, dv, ds, d_meta, d_n, d_n + n_graphs, d_meta + n_graphs + 1, d_meta + 2 * (n_graphs + 1), n_graphs, ou, ov,
+        os, d_err);
+    DBBC_LAUNCH_CHECK();
+    if (read_back(d_err, s) != 0) throw Error{DBBC_EINVAL, "invalid edge id or sign"};
+  }
+  UnionSpec un;
+  un.n_graphs = std::max<int32_t>(n_graphs, 1);
+  un.uoff = n_graphs > 0 ? uoff : std::vector<int64_t>{0, 0};
+  un.voff = n_graphs > 0 ? voff : std::vector<int64_t>{0, 0};
+  un.d_uoff = n_graphs > 0 ? d_meta + n_graphs + 1 : nullptr;
+  un.d_voff = n_graphs > 0 ? d_meta + 2 * (n_graphs + 1) : nullptr;
+  for (int32_t i = 0; i < n_graphs; i++) un.max_side = std::max<int64_t>(un.max_side, std::max(n_u[i], n_v[i]));
+  if (n_graphs == 0) {
+    int64_t* d = sc.get<int64_t>(4);
+    DBBC_CUDA(cudaMemsetAsync(d, 0, 32, s));
+    un.d_uoff = d;
+    un.d_voff = d + 2;
+  }
+  build_graph(g, ou, ov, os, m, true, reject_duplicates, s, &un);
+  g->n_components = n_graphs;
+  g->component = static_cast<int32_t*>(graph_alloc(g, (size_t)std::max<int64_t>(g->n, 1) * 4));
+  if (g->n > 0) {
+    component_kernel<<<grid_for(g->n), 256, 0, s>>>(g->vertex, g->n, g->n_u, d_meta + n_graphs + 1,
+                                                    d_meta + 2 * (n_graphs + 1), n_graphs, g->component);
+    DBBC_LAUNCH_CHECK();
+  }
+  DBBC_CUDA(cudaStreamSynchronize(s));
+}
+
 void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const int8_t* s_in, int64_t m,
-                 bool on_device, bool reject_duplicates, cudaStream_t s) {
+                 bool on_device, bool reject_duplicates, cudaStream_t s, const UnionSpec* union_spec) {
   const int32_t n_u = g->n_u, n_v = g->n_v;
   const int64_t n = (int64_t)n_u + n_v;
   g->n = n;
   g->m_input = m;
   Scratch sc(s);
+  // a plain graph is a union of one component
+  UnionSpec plain;
+  const UnionSpec* un = union_spec;
+  if (!un) {
+    plain.uoff = {0, (int64_t)n_u};
+    plain.voff = {0, (int64_t)n_v};
+    plain.max_side = std::max<int64_t>(n_u, n_v);
+    int64_t* d = sc.get<int64_t>(4);
+    DBBC_CUDA(cudaMemcpyAsync(d, plain.uoff.data(), 16, cudaMemcpyHostToDevice, s));
+    DBBC_CUDA(cudaMemcpyAsync(d + 2, plain.voff.data(), 16, cudaMemcpyHostToDevice, s));
+    plain.d_uoff = d;
+    plain.d_voff = d + 2;
+    un = &plain;
+  }
+  const UnionView uv{un->d_uoff, un->d_voff, un->n_graphs};
 
   // ---- inputs on the device
   const int32_t* du = u_in;
@@ -442,9 +618,13 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
 
   const int bits_u = bits_for(n_u > 0 ? (uint64_t)(n_u - 1) : 0);
   const int bits_v = bits_for(n_v > 0 ? (uint64_t)(n_v - 1) : 0);
+  // rank keys: (side, component, degree, id within the component)
   const int64_t max_side = std::max<int64_t>(n_u, n_v);
+  const int bits_comp = un->n_graphs > 1 ? bits_for((uint64_t)(un->n_graphs - 1)) : 0;
+  const int bits_lid = std::max(1, bits_for(un->max_side > 0 ? (uint64_t)(un->max_side - 1) : 0));
+  const int bits_deg = std::max(1, bits_for((uint64_t)un->max_side));
+  if (1 + bits_comp + bits_deg + bits_lid > 64) throw Error{DBBC_EINVAL, "union too large for 64-bit rank keys"};
   const int bits_id = std::max(1, bits_for(max_side > 0 ? (uint64_t)(max_side - 1) : 0));
-  const int bits_deg = std::max(1, bits_for((uint64_t)max_side));
   const int bits_col = bits_id;
   const int bits_row = std::max(1, bits_for(n > 0 ? (uint64_t)(n - 1) : 0));
   if (bits_row + bits_col + 1 > 64) throw Error{DBBC_EINVAL, "graph too large for 64-bit CSR keys"};
@@ -469,12 +649,12 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
       DBBC_LAUNCH_CHECK();
     }
     if (n > 0) {
-      vertex_keys_kernel<<<grid_for(n), 256, 0, s>>>(deg, n, n_u, bits_deg, bits_id, vk0);
+      vertex_keys_kernel<<<grid_for(n), 256, 0, s>>>(deg, n, n_u, bits_comp, bits_deg, bits_lid, uv, vk0);
       DBBC_LAUNCH_CHECK();
       const bool alt = radix_sort<uint64_t, uint32_t, false>(vk0, vk1, nullptr, nullptr, n, 0,
-                                                             1 + bits_deg + bits_id, s, sc);
-      ranks_kernel<<<grid_for(n), 256, 0, s>>>(alt ? vk1 : vk0, n, n_u, bits_deg, bits_id, g->vertex, side_rank,
-                                               rowdeg);
+                                                             1 + bits_comp + bits_deg + bits_lid, s, sc);
+      ranks_kernel<<<grid_for(n), 256, 0, s>>>(alt ? vk1 : vk0, n, n_u, bits_comp, bits_deg, bits_lid, uv,
+                                               g->vertex, side_rank, rowdeg);
       DBBC_LAUNCH_CHECK();
     }
     *dup = false;
@@ -535,7 +715,7 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
     DBBC_LAUNCH_CHECK();
   }
   if (n > 0) {
-    lower_kernel<<<grid_for(n), 256, 0, s>>>(g->row_ptr, g->col, rowdeg, n, n_u, g->lower);
+    lower_kernel<<<grid_for(n), 256, 0, s>>>(g->row_ptr, g->col, rowdeg, n, n_u, uv, g->lower);
     DBBC_LAUNCH_CHECK();
   }
 
@@ -590,7 +770,7 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
     g->narrow_ranks_u = ht[0];
     g->narrow_ranks_v = ht[1];
   }
-  plan_hubs(g, s);
+  plan_hubs(g, s, *un);
   DBBC_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -178,6 +178,29 @@ def batch_graph(g: int, seed: int = SEED_BASE + 3, threads: int = 1) -> Graph:
                     cap_u=nv, cap_v=nu, signs="iid", p_plus=b["p_plus"], threads=threads, name=f"batch[{g}]")
 
 
+SERVE = dict(index=4, rate=2000.0, n_requests=100_000, large_fraction=0.01, large_lo=5_000_000,
+             large_hi=20_000_000, avg_degree=13.6)
+
+
+def serve_large_graph(i: int, seed: int = SEED_BASE + 4, threads: int | None = None) -> Graph:
+    """Large request i of the served stream: a polarized Chung-Lu graph like the
+    300M-edge one (gamma 2.0 / 1.8, camp signs), m log-uniform in [5M, 20M],
+    |U| + |V| = m / 13.6 (that graph's average degree), |U| = |V| / 4."""
+    key = splitmix_at(seed, 0x2000 + i, 0)
+    lo, hi = np.log(SERVE["large_lo"]), np.log(SERVE["large_hi"])
+    m = int(round(np.exp(lo + (hi - lo) * ((key >> 11) / 2.0**53))))
+    n = int(m / SERVE["avg_degree"])
+    n_u, n_v = n // 5, n - n // 5
+    return generate(seed * 131 + i, n_u, n_v, m, model="chung-lu", gamma_u=2.0, gamma_v=1.8,
+                    cap_u=min(1_000_000, n_v), cap_v=min(1_000_000, n_u), signs="camp", p_camp=0.9,
+                    threads=threads, name=f"serve-large[{i}]")
+
+
+def serve_is_large(i: int, seed: int = SEED_BASE + 4) -> bool:
+    """Whether request i of the served stream is a large one (1% of requests)."""
+    return (splitmix_at(seed, 0x3000, i) >> 11) / 2.0**53 < SERVE["large_fraction"]
+
+
 def batch(n_graphs: int = 4096, seed: int = SEED_BASE + 3, threads: int | None = None) -> list[Graph]:
     from concurrent.futures import ThreadPoolExecutor
     nt = threads or default_threads()

@@ -229,6 +229,49 @@ def test_batch_plan_capture_and_replay_mixed_graphs():
             h.free()
 
 
+def _union_inputs(graphs):
+    u = np.concatenate([g.u for g in graphs]).astype(np.int32)
+    v = np.concatenate([g.v for g in graphs]).astype(np.int32)
+    s = np.concatenate([g.s for g in graphs]).astype(np.int8)
+    off = np.concatenate([[0], np.cumsum([g.m for g in graphs])]).astype(np.int64)
+    return u, v, s, off, [g.n_u for g in graphs], [g.n_v for g in graphs]
+
+
+@pytest.mark.parametrize("device_input", [False, True])
+def test_union_build_counts_each_component_exactly(device_input):
+    """dbbc_graph_from_coo_multi: per-component counts equal each graph counted
+    alone (oracle), the plain count of the union is their sum, and duplicates
+    stay within their own component."""
+    import torch
+    rng = np.random.default_rng(21)
+    graphs = [synth.batch_graph(i) for i in range(30)]
+    graphs.insert(3, synth.Graph(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8), 4, 9))
+    graphs.insert(10, synth.workload("chunglu-1m-200k-20m", scale=0.01))
+    gd = synth.batch_graph(77)  # a graph with conflicting duplicates
+    pick = rng.choice(gd.m, 50, replace=False)
+    graphs.append(synth.Graph(np.concatenate([gd.u, gd.u[pick]]), np.concatenate([gd.v, gd.v[pick]]),
+                              np.concatenate([gd.s, -gd.s[pick]]).astype(np.int8), gd.n_u, gd.n_v))
+    u, v, s, off, nu, nv = _union_inputs(graphs)
+    want = [oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[:2] for g in graphs]
+    if device_input:
+        u, v, s = (torch.from_numpy(x).cuda() for x in (u, v, s))
+    with dbbc.dbbc_graph_from_coo_multi(u, v, s, off, nu, nv) as h:
+        assert h.info["n_components"] == len(graphs)
+        bal, unb = dbbc.dbbc_count_components(h)
+        assert list(zip(bal.tolist(), unb.tolist())) == want
+        assert dbbc.dbbc_count(h) == (sum(w[0] for w in want), sum(w[1] for w in want))
+        assert h.info["wedges"] == sum(oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[2] for g in graphs)
+
+
+def test_union_build_validates_each_component():
+    graphs = [synth.batch_graph(i) for i in range(4)]
+    u, v, s, off, nu, nv = _union_inputs(graphs)
+    u[off[2]] = nu[2]  # out of range for graph 2 (in range for the union)
+    with pytest.raises(dbbc.DbbcError) as ei:
+        dbbc.dbbc_graph_from_coo_multi(u, v, s, off, nu, nv)
+    assert ei.value.status == dbbc.DBBC_EINVAL
+
+
 def test_torch_allocator_hook():
     g = synth.workload("chunglu-1m-200k-20m", scale=0.003)
     want = oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[:2]
