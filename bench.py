@@ -336,6 +336,7 @@ def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
             "warmup": a.warmup, "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": "batch-4096", "n_graphs": len(handles), "edges_total": int(offs[-1]),
+                       "tuning": dbbc.dbbc_get_tuning(),
                        "wedges_per_step": wedges, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (all graphs' CSR %.0f MB > 129 MB)" % (
                            sum(8 * i["m"] + 24 * (i["n_u"] + i["n_v"]) for i in infos) / 1e6)},
@@ -455,6 +456,7 @@ def run_serve(a, torch, dbbc, world, rank, local, dist, barrier):
             "ms_per_step": 1e3 * sat["wall_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": "serve", "requests": n, "rate_per_s": rate, "large_requests": n_large,
+                       "tuning": dbbc.dbbc_get_tuning(),
                        "distinct_large_graphs": len(large), "edges_total": edges,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "timing": "wall clock around the whole stream (host COO in pinned memory)"},
@@ -482,6 +484,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    # the autotuner's record for this workload on this GPU, if there is one
+    from paper_2609_21848_gb300 import autotune
+    dbbc.lib()
+    tuned = autotune.apply_saved("batch-4096" if a.workload == "serve" else a.workload)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -588,6 +594,7 @@ def main():
             "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": a.workload, "n_u": g.n_u, "n_v": g.n_v, "edges": g.m,
+                       "tuning": dbbc.dbbc_get_tuning(),
                        "wedges_per_step": wedges, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (COO %.0f MB, CSR %.0f MB > 129 MB)" % (
                            g.m * 9 / 1e6, (2 * g.m * 4 + (g.n_u + g.n_v) * 8) / 1e6)},

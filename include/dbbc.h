@@ -221,6 +221,30 @@ DBBC_API dbbc_status dbbc_graph_export(const dbbc_graph* g, void* cuda_stream, i
 DBBC_API void dbbc_set_allocator(void* (*alloc_fn)(size_t bytes, void* cuda_stream, void* ctx),
                         void (*free_fn)(void* ptr, void* cuda_stream, void* ctx), void* ctx);
 
+/* Tuning of the counting tiers, applied to graphs built after the call (a
+ * handle keeps the values it was built with). Chosen per GPU by the
+ * project's autotuner (paper_2609_21848_gb300/autotune.py); every setting only
+ * changes speed, never a count.
+ *   light_max_work  : pivots with at most this many accepted wedges use one
+ *                     warp each (1..512);
+ *   medium_max_work : ... and up to this many one CTA each (light..4096);
+ *                     more go to the hub window sweep;
+ *   hub_item_work   : target accepted wedges per hub work item (>= 1024);
+ *   group_density   : mean (lower neighbour, window) segment lengths at which
+ *                     32, 16, 8 and 4 lanes walk a segment (descending);
+ *   hash_mult_log   : shared hash tables get at least 2^hash_mult_log slots
+ *                     per accepted wedge of the pivot (1..3; capped by the
+ *                     tier's table size, never below 2 per wedge). */
+typedef struct {
+  uint64_t light_max_work;
+  uint64_t medium_max_work;
+  uint64_t hub_item_work;
+  double group_density[4];
+  int32_t hash_mult_log;
+} dbbc_tuning;
+DBBC_API dbbc_status dbbc_set_tuning(const dbbc_tuning* t); /* NULL restores the defaults; DBBC_EINVAL if out of range */
+DBBC_API void dbbc_get_tuning(dbbc_tuning* t);
+
 /* Static description of a status code. */
 DBBC_API const char* dbbc_status_string(dbbc_status s);
 

@@ -32,6 +32,7 @@ EXPORTED = (
     "dbbc_graph_export", "dbbc_set_allocator", "dbbc_status_string", "dbbc_version", "dbbc_count_profiled",
     "dbbc_kernel_launches", "dbbc_count_noalloc", "dbbc_batch_create", "dbbc_batch_count_async",
     "dbbc_batch_count", "dbbc_batch_free", "dbbc_graph_from_coo_multi", "dbbc_count_components",
+    "dbbc_set_tuning", "dbbc_get_tuning",
 )
 
 
@@ -58,6 +59,12 @@ class CountProfile(ctypes.Structure):
                 ("launches_light", ctypes.c_int64), ("launches_medium", ctypes.c_int64),
                 ("launches_hub_aggregate", ctypes.c_int64), ("launches_hub_finalize", ctypes.c_int64),
                 ("hub_touched", ctypes.c_uint64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("light_max_work", ctypes.c_uint64), ("medium_max_work", ctypes.c_uint64),
+                ("hub_item_work", ctypes.c_uint64), ("group_density", ctypes.c_double * 4),
+                ("hash_mult_log", ctypes.c_int32)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -90,6 +97,10 @@ def lib() -> ctypes.CDLL:
         L.dbbc_count_profiled.restype = st
         L.dbbc_kernel_launches.argtypes = []
         L.dbbc_kernel_launches.restype = ctypes.c_uint64
+        L.dbbc_set_tuning.argtypes = [ctypes.POINTER(Tuning)]
+        L.dbbc_set_tuning.restype = st
+        L.dbbc_get_tuning.argtypes = [ctypes.POINTER(Tuning)]
+        L.dbbc_get_tuning.restype = None
         L.dbbc_graph_from_coo_multi.argtypes = [P, P, P, P, P, P, I32, U32, P, ctypes.POINTER(P)]
         L.dbbc_graph_from_coo_multi.restype = st
         L.dbbc_count_components.argtypes = [P, P, P, P]
@@ -127,6 +138,9 @@ def lib() -> ctypes.CDLL:
         L.dbbc_version.argtypes = []
         L.dbbc_version.restype = ctypes.c_char_p
         _lib = L
+        if not os.environ.get("DBBC_NO_TUNING"):
+            from . import autotune
+            autotune.apply_saved()
     return _lib
 
 
@@ -411,6 +425,26 @@ def dbbc_set_allocator(use_torch: bool = True) -> None:
     refs = (_ALLOC_FN(_alloc), _FREE_FN(_free))
     lib().dbbc_set_allocator(ctypes.cast(refs[0], ctypes.c_void_p), ctypes.cast(refs[1], ctypes.c_void_p), None)
     _allocator_refs = refs
+
+
+def dbbc_set_tuning(tuning: dict | None) -> None:
+    """Set the tier tuning for graphs built afterwards (None: defaults). Keys:
+    light_max_work, medium_max_work, hub_item_work, group_density (4 values),
+    hash_mult_log."""
+    if tuning is None:
+        _check(lib().dbbc_set_tuning(None), "dbbc_set_tuning")
+        return
+    t = Tuning(int(tuning["light_max_work"]), int(tuning["medium_max_work"]), int(tuning["hub_item_work"]),
+               (ctypes.c_double * 4)(*[float(x) for x in tuning["group_density"]]), int(tuning["hash_mult_log"]))
+    _check(lib().dbbc_set_tuning(ctypes.byref(t)), "dbbc_set_tuning")
+
+
+def dbbc_get_tuning() -> dict:
+    t = Tuning()
+    lib().dbbc_get_tuning(ctypes.byref(t))
+    return {"light_max_work": t.light_max_work, "medium_max_work": t.medium_max_work,
+            "hub_item_work": t.hub_item_work, "group_density": list(t.group_density),
+            "hash_mult_log": t.hash_mult_log}
 
 
 def dbbc_status_string(status: int) -> str:

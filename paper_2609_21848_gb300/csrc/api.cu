@@ -17,6 +17,9 @@ void (*g_free_fn)(void*, void*, void*) = nullptr;
 void* g_alloc_ctx = nullptr;
 }  // namespace
 
+Tuning g_tuning;
+const Tuning& current_tuning() { return g_tuning; }
+
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
@@ -81,6 +84,36 @@ const char* dbbc_status_string(dbbc_status s) {
     case DBBC_EINTERNAL: return "internal consistency check failed";
   }
   return "unknown status";
+}
+
+dbbc_status dbbc_set_tuning(const dbbc_tuning* t) {
+  if (!t) {
+    g_tuning = Tuning();
+    return DBBC_OK;
+  }
+  if (t->light_max_work < 1 || t->light_max_work > kLightMaxWork || t->medium_max_work < t->light_max_work ||
+      t->medium_max_work > kMediumMaxWork || t->hub_item_work < 1024 || t->hash_mult_log < 1 ||
+      t->hash_mult_log > 3)
+    return DBBC_EINVAL;
+  for (int i = 0; i < 4; i++)
+    if (!(t->group_density[i] >= 0) || (i > 0 && t->group_density[i] > t->group_density[i - 1])) return DBBC_EINVAL;
+  Tuning n;
+  n.light_max_work = t->light_max_work;
+  n.medium_max_work = t->medium_max_work;
+  n.hub_item_work = t->hub_item_work;
+  for (int i = 0; i < 4; i++) n.group_density[i] = t->group_density[i];
+  n.hash_mult_log = t->hash_mult_log;
+  g_tuning = n;
+  return DBBC_OK;
+}
+
+void dbbc_get_tuning(dbbc_tuning* t) {
+  if (!t) return;
+  t->light_max_work = g_tuning.light_max_work;
+  t->medium_max_work = g_tuning.medium_max_work;
+  t->hub_item_work = g_tuning.hub_item_work;
+  for (int i = 0; i < 4; i++) t->group_density[i] = g_tuning.group_density[i];
+  t->hash_mult_log = g_tuning.hash_mult_log;
 }
 
 void dbbc_set_allocator(void* (*alloc_fn)(size_t, void*, void*), void (*free_fn)(void*, void*, void*), void* ctx) {

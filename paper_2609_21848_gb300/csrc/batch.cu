@@ -19,7 +19,7 @@ struct GraphDesc {
   const uint64_t* work;
   int64_t n;
   int32_t n_u;
-  int32_t pad;
+  int32_t hash_mult_log;
 };
 
 struct BatchPivot {
@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(kLightWarps * 32) count_light_batch_kernel(
   int cur_graph = -1;
   CsrView g{};
   const uint64_t* work = nullptr;
+  int mult_log = 1;
   for (;;) {
     int chunk = 0;
     if (lane == 0) chunk = atomicAdd(next_chunk, 1);
@@ -119,8 +120,9 @@ __global__ void __launch_bounds__(kLightWarps * 32) count_light_batch_kernel(
         const GraphDesc d = desc[bp.graph];
         g = view_of(d);
         work = d.work;
+        mult_log = d.hash_mult_log;
       }
-      const int log_h = table_log(work[bp.row], max_log);
+      const int log_h = table_log(work[bp.row], max_log, mult_log);
       const PivotGeom q = pivot_geom(g, bp.row);
       warp_walk<1>(g, q, 0, q.L, 32, [&](const uint32_t (&x)[1], uint32_t s1) {
         if (x[0] != 0xFFFFFFFFu) {
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_batch_kernel(cons
     const BatchPivot bp = piv[t];
     const GraphDesc d = desc[bp.graph];
     const CsrView g = view_of(d);
-    const int log_h = table_log(d.work[bp.row], max_log);
+    const int log_h = table_log(d.work[bp.row], max_log, d.hash_mult_log);
     const PivotGeom q = pivot_geom(g, bp.row);
     uint64_t bal = 0, unb = 0;
     warp_walk<2>(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u, [&](const uint32_t (&x)[2], uint32_t s1) {
@@ -290,7 +292,7 @@ static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector
 // union's CSR; pivots and hub items are tagged with their component.
 static void plan_components(dbbc_batch* b, const dbbc_graph* g) {
   cudaStream_t s = b->stream;
-  std::vector<GraphDesc> desc((size_t)b->n_graphs, GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u, 0});
+  std::vector<GraphDesc> desc((size_t)b->n_graphs, GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u, g->tune.hash_mult_log});
   b->n_medium = g->n_medium;
   b->n_light = g->n_light;
   b->max_lower = std::max<int64_t>(1, g->sweep_max_lower);
@@ -334,7 +336,7 @@ static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
   std::vector<HubRef> hubs;
   for (int32_t i = 0; i < n; i++) {
     const dbbc_graph* g = gs[i];
-    desc[(size_t)i] = GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u, 0};
+    desc[(size_t)i] = GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u, g->tune.hash_mult_log};
     jobs[(size_t)i] = GatherJob{g->order, g->n_hub, g->n_medium, g->n_light, b->n_medium, b->n_light};
     b->n_medium += g->n_medium;
     b->n_light += g->n_light;

@@ -19,7 +19,8 @@ namespace dbbc {
 // ------------------------------------------------------------------ light tier
 __global__ void __launch_bounds__(kLightWarps * 32) count_light_kernel(CsrView g, const int32_t* __restrict__ piv,
                                                                        const uint64_t* __restrict__ work, int64_t n_piv,
-                                                                       unsigned long long* out, unsigned* status) {
+                                                                       int hash_mult_log, unsigned long long* out,
+                                                                       unsigned* status) {
   extern __shared__ __align__(16) unsigned char light_smem[];
   unsigned long long* vals_all = reinterpret_cast<unsigned long long*>(light_smem);
   uint32_t* keys_all = reinterpret_cast<uint32_t*>(vals_all + kLightWarps * kLightSlots);
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(kLightWarps * 32) count_light_kernel(CsrView g
   const int64_t nw = (int64_t)gridDim.x * kLightWarps;
   for (int64_t t = (int64_t)blockIdx.x * kLightWarps + w; t < n_piv; t += nw) {
     const int32_t p = piv[t];
-    const int log_h = table_log(work[p], max_log);
+    const int log_h = table_log(work[p], max_log, hash_mult_log);
     const PivotGeom q = pivot_geom(g, p);
     warp_walk<1>(g, q, 0, q.L, 32, [&](const uint32_t (&x)[1], uint32_t s1) {
       if (x[0] != 0xFFFFFFFFu) {
@@ -62,8 +63,8 @@ __global__ void __launch_bounds__(kLightWarps * 32) count_light_kernel(CsrView g
 // ------------------------------------------------------------------ medium tier
 __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g, const int32_t* __restrict__ piv,
                                                                       const uint64_t* __restrict__ work,
-                                                                      int64_t n_piv, unsigned long long* out,
-                                                                      unsigned* status) {
+                                                                      int64_t n_piv, int hash_mult_log,
+                                                                      unsigned long long* out, unsigned* status) {
   extern __shared__ __align__(16) unsigned char med_smem[];
   unsigned long long* vals = reinterpret_cast<unsigned long long*>(med_smem);
   uint32_t* keys = reinterpret_cast<uint32_t*>(vals + kMediumSlots);
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
   bool full = false;
   for (int64_t t = blockIdx.x; t < n_piv; t += gridDim.x) {
     const int32_t p = piv[t];
-    const int log_h = table_log(work[p], max_log);
+    const int log_h = table_log(work[p], max_log, hash_mult_log);
     const PivotGeom q = pivot_geom(g, p);
     warp_walk<2>(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u, [&](const uint32_t (&x)[2], uint32_t s1) {
 #pragma unroll
@@ -215,7 +216,7 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
     const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
     const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_light_kernel, kLightWarps * 32, smem);
     count_light_kernel<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
-        view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, d_out, d_status);
+        view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, d_out, d_status);
     DBBC_LAUNCH_CHECK();
     if (prof) {
       prof->end(CountProfiler::LIGHT, t0, s);
@@ -228,7 +229,7 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
     DBBC_CUDA(cudaFuncSetAttribute(count_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_medium_kernel, kMediumThreads, smem);
     count_medium_kernel<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
-        view, g->order + g->n_hub, g->work, g->n_medium, d_out, d_status);
+        view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, d_out, d_status);
     DBBC_LAUNCH_CHECK();
     if (prof) {
       prof->end(CountProfiler::MEDIUM, t0, s);
@@ -282,7 +283,7 @@ void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t s, unsigned long l
     const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
     const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_light_kernel, kLightWarps * 32, smem);
     count_light_kernel<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
-        view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, d_out, d_status);
+        view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, d_out, d_status);
     DBBC_LAUNCH_CHECK();
   }
   if (g->n_medium > 0) {
@@ -290,7 +291,7 @@ void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t s, unsigned long l
     DBBC_CUDA(cudaFuncSetAttribute(count_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_medium_kernel, kMediumThreads, smem);
     count_medium_kernel<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
-        view, g->order + g->n_hub, g->work, g->n_medium, d_out, d_status);
+        view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, d_out, d_status);
     DBBC_LAUNCH_CHECK();
   }
   if (g->n_hub > 0) {

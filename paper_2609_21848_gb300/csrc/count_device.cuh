@@ -51,10 +51,12 @@ __device__ __forceinline__ bool smem_hash_add(uint32_t* keys, unsigned long long
   return false;
 }
 
-__device__ __forceinline__ int table_log(uint64_t work, int max_log) {
-  // smallest 2^k >= 2 * work, at least 32 slots
+// Smallest 2^k >= (work << mult_log) slots (at least 32, at most 2^max_log).
+// The tiers keep work <= 2^(max_log - 1), so a table always has more slots
+// than the pivot has accepted wedges (and hence distinct endpoints).
+__device__ __forceinline__ int table_log(uint64_t work, int max_log, int mult_log) {
   int k = 5;
-  while (k < max_log && (1ull << k) < 2 * work) k++;
+  while (k < max_log && (1ull << k) < (work << mult_log)) k++;
   return k;
 }
 

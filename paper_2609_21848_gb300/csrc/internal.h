@@ -13,7 +13,7 @@
 
 namespace dbbc {
 
-// Counting tiers by accepted wedges W(p) of a pivot.
+// Counting tiers by accepted wedges W(p) of a pivot (defaults; see Tuning).
 constexpr uint64_t kLightMaxWork = 512;    // warp per pivot, per-warp shared hash (<= 1024 slots)
 constexpr uint64_t kMediumMaxWork = 4096;  // CTA per pivot, shared hash (<= 8192 slots)
 constexpr int kLightSlots = 1024;
@@ -46,6 +46,16 @@ constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per wor
 #define DBBC_GROUP_T4 2
 #endif
 constexpr double kGroupThreshold[4] = {DBBC_GROUP_T32, DBBC_GROUP_T16, DBBC_GROUP_T8, DBBC_GROUP_T4};
+
+// Runtime tuning (dbbc_set_tuning), snapshotted into every graph at build.
+struct Tuning {
+  uint64_t light_max_work = kLightMaxWork;
+  uint64_t medium_max_work = kMediumMaxWork;
+  uint64_t hub_item_work = kSweepItemWork;
+  double group_density[4] = {DBBC_GROUP_T32, DBBC_GROUP_T16, DBBC_GROUP_T8, DBBC_GROUP_T4};
+  int32_t hash_mult_log = 1;
+};
+const Tuning& current_tuning();
 
 // Counts below this fit the 16-bit halves of a narrow counter.
 constexpr int32_t kNarrowCountLimit = 65536;
@@ -112,6 +122,7 @@ struct dbbc_graph {
   // disjoint union of several graphs (dbbc_graph_from_coo_multi): component
   // of every row, 0 for a plain handle (n_components == 1)
   int32_t n_components = 1;
+  dbbc::Tuning tune;  // tuning the handle was built with
   int32_t* component = nullptr;  // [n] or nullptr for a plain handle
   size_t device_bytes = 0;
   std::vector<void*> allocations;

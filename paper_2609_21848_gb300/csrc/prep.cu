@@ -249,7 +249,8 @@ struct PrepStats {
 // least one accepted wedge. (A pivot with a single lower neighbour v reaches
 // every endpoint w at most once, so all its buckets stay below 2.)
 __global__ void pivot_flags_kernel(const uint64_t* __restrict__ work, const uint32_t* __restrict__ lower, int64_t n,
-                                   uint32_t* __restrict__ flag, PrepStats* st) {
+                                   uint64_t light_max, uint64_t medium_max, uint32_t* __restrict__ flag,
+                                   PrepStats* st) {
   uint64_t w_all = 0, w_hub = 0, w_med = 0, w_light = 0, mx = 0, np = 0, nh = 0, nm = 0;
   uint64_t l_hub = 0, l_med = 0, l_light = 0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
@@ -261,8 +262,8 @@ __global__ void pivot_flags_kernel(const uint64_t* __restrict__ work, const uint
       np++;
       mx = w > mx ? w : mx;
       const uint64_t L = lower[r];
-      if (w > kMediumMaxWork) { nh++; w_hub += w; l_hub += L; }
-      else if (w > kLightMaxWork) { nm++; w_med += w; l_med += L; }
+      if (w > medium_max) { nh++; w_hub += w; l_hub += L; }
+      else if (w > light_max) { nm++; w_med += w; l_med += L; }
       else { w_light += w; l_light += L; }
     }
   }
@@ -446,15 +447,12 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
                                               sp, (uint64_t)(is_u ? g->narrow_ranks_u : g->narrow_ranks_v)));
     const uint64_t Rn = (narrow_end - start + kSweepWindow16 - 1) / kSweepWindow16;
     const uint64_t Rw = (sp - narrow_end + kSweepWindow32 - 1) / kSweepWindow32;
-    const uint64_t target = std::max<uint64_t>(kSweepItemWork, 64ull * L);
+    const uint64_t target = std::max<uint64_t>(g->tune.hub_item_work, 64ull * L);
     max_lower = std::max<int64_t>(max_lower, L);
     // lanes per (neighbour, window) segment from the hub's mean segment length
     const double density = (double)W / ((double)L * (double)std::max<uint64_t>(1, Rn + Rw));
-    const int16_t group_log = density >= kGroupThreshold[0]   ? 5
-                              : density >= kGroupThreshold[1] ? 4
-                              : density >= kGroupThreshold[2] ? 3
-                              : density >= kGroupThreshold[3] ? 2
-                                                              : 0;
+    const double* gd = g->tune.group_density;
+    const int16_t group_log = density >= gd[0] ? 5 : density >= gd[1] ? 4 : density >= gd[2] ? 3 : density >= gd[3] ? 2 : 0;
     auto add = [&](uint64_t lo, uint64_t hi, uint64_t H, int16_t wide, uint64_t est) {
       Planned p;
       p.it.row = row;
@@ -574,6 +572,7 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
   const int64_t n = (int64_t)n_u + n_v;
   g->n = n;
   g->m_input = m;
+  g->tune = current_tuning();
   Scratch sc(s);
   // a plain graph is a union of one component
   UnionSpec plain;
@@ -729,7 +728,8 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
   DBBC_CUDA(cudaMemsetAsync(d_st, 0, sizeof(PrepStats), s));
   uint32_t* pflag = sc.get<uint32_t>((size_t)std::max<int64_t>(n, 1));
   if (n > 0) {
-    pivot_flags_kernel<<<grid_for(n), 256, 0, s>>>(g->work, g->lower, n, pflag, d_st);
+    pivot_flags_kernel<<<grid_for(n), 256, 0, s>>>(g->work, g->lower, n, g->tune.light_max_work,
+                                                   g->tune.medium_max_work, pflag, d_st);
     DBBC_LAUNCH_CHECK();
   }
   const PrepStats st = read_back(d_st, s);

@@ -272,6 +272,35 @@ def test_union_build_validates_each_component():
     assert ei.value.status == dbbc.DBBC_EINVAL
 
 
+@pytest.mark.parametrize("tuning", [
+    dict(light_max_work=1, medium_max_work=1, hub_item_work=1024, group_density=[40.0, 16.0, 6.0, 2.0],
+         hash_mult_log=1),   # every pivot in the hub sweep, many small items
+    dict(light_max_work=512, medium_max_work=4096, hub_item_work=1 << 22, group_density=[0.0, 0.0, 0.0, 0.0],
+         hash_mult_log=3),   # 32-lane groups everywhere, sparse hash tables
+    dict(light_max_work=16, medium_max_work=64, hub_item_work=4096, group_density=[1e9, 1e9, 1e9, 1e9],
+         hash_mult_log=2),   # one lane per segment
+])
+def test_counts_do_not_depend_on_tuning(tuning):
+    base = dbbc.dbbc_get_tuning()
+    g = synth.workload("chunglu-1m-200k-20m", scale=0.01)
+    want = oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)
+    graphs = [synth.batch_graph(i) for i in range(8)]
+    want_b = [oracle.count(x.u, x.v, x.s, x.n_u, x.n_v)[:2] for x in graphs]
+    try:
+        dbbc.dbbc_set_tuning(tuning)
+        bal, unb, info = gpu_count(g.u, g.v, g.s, g.n_u, g.n_v)
+        assert (bal, unb, info["wedges"]) == want
+        handles = [dbbc.dbbc_graph_from_coo(x.u, x.v, x.s, x.n_u, x.n_v) for x in graphs]
+        try:
+            b, u = dbbc.dbbc_count_batch(handles)
+            assert list(zip(b.tolist(), u.tolist())) == want_b
+        finally:
+            for h in handles:
+                h.free()
+    finally:
+        dbbc.dbbc_set_tuning(base)
+
+
 def test_torch_allocator_hook():
     g = synth.workload("chunglu-1m-200k-20m", scale=0.003)
     want = oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[:2]
