@@ -53,13 +53,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dbbc", "reference"], default="dbbc")
-    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS) + ["batch-4096", "serve"])
+    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS) + ["batch-4096", "serve", "sign-sweep"])
     ap.add_argument("--n-graphs", type=int, default=4096, help="graphs in the batch-4096 workload")
     ap.add_argument("--requests", type=int, default=4000, help="requests of the served workload")
     ap.add_argument("--large-pool", type=int, default=4, help="distinct large graphs cycled by the served stream")
     ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the host-buffer end-to-end timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--partition", action="store_true",
+                    help="with N > 1 GPUs: every rank counts its LPT share of the pivots of one graph (strong "
+                         "scaling) instead of counting its own replica (weak scaling)")
     return ap.parse_args()
 
 
@@ -337,7 +340,9 @@ def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": "batch-4096", "n_graphs": len(handles), "edges_total": int(offs[-1]),
                        "tuning": dbbc.dbbc_get_tuning(),
-                       "wedges_per_step": wedges, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "wedges_per_step": wedges,
+                       "parallelism": (f"LPT pivot partition x{world}" if partition else f"replicas x{world}")
+                       if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (all graphs' CSR %.0f MB > 129 MB)" % (
                            sum(8 * i["m"] + 24 * (i["n_u"] + i["n_v"]) for i in infos) / 1e6)},
             "plain_graphs_per_s": plain_gps, "batched_over_plain": value / world / plain_gps,
@@ -472,6 +477,48 @@ def run_serve(a, torch, dbbc, world, rank, local, dist, barrier):
         print(json.dumps(line), flush=True)
 
 
+def run_sign_sweep(a, torch, dbbc, world, rank, local, dist, barrier):
+    """The sign-ratio study (paper Section VI, "Sign Distribution"): the
+    Chung-Lu 1M x 200k x 20M topology with P(+) from 0.1 to 0.9. The count
+    time should not move (one packed counter per endpoint, no branch on the
+    sign); the balanced / unbalanced split does, while their sum (the unsigned
+    butterfly count) stays put."""
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p = dict(synth.WORKLOADS["chunglu-1m-200k-20m"])
+    p.pop("index")
+    rows = []
+    for pp in (0.1, 0.3, 0.5, 0.7, 0.9):
+        p["p_plus"] = pp
+        g = synth.generate(synth.SEED_BASE + 1, name=f"p+={pp}", **p)
+        du, dv, ds = (torch.from_numpy(x).to(dev) for x in (g.u, g.v, g.s))
+        times, counts = [], None
+        for k in range(a.warmup + a.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with dbbc.dbbc_graph_from_coo(du, dv, ds, g.n_u, g.n_v, stream=stream) as h:
+                counts = dbbc.dbbc_count(h, stream)
+                wedges = h.info["wedges"]
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if k >= a.warmup:
+                times.append(e0.elapsed_time(e1))
+        times.sort()
+        rows.append({"p_plus": pp, "ms_per_step": times[len(times) // 2], "balanced": counts[0],
+                     "unbalanced": counts[1], "balanced_fraction": counts[0] / max(1, counts[0] + counts[1]),
+                     "wedges": wedges})
+    ms = [r["ms_per_step"] for r in rows]
+    total = {r["balanced"] + r["unbalanced"] for r in rows}
+    line = {"metric": METRIC, "value": world * rows[2]["wedges"] / (rows[2]["ms_per_step"] / 1e3) / 1e9,
+            "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": rows[2]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "sign-sweep", "topology": "chunglu-1m-200k-20m", "tuning": dbbc.dbbc_get_tuning()},
+            "sweep": rows, "time_spread": (max(ms) - min(ms)) / min(ms),
+            "unsigned_count_constant": len(total) == 1, "e2e": None, "roofline": None, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -487,7 +534,8 @@ def main():
     # the autotuner's record for this workload on this GPU, if there is one
     from paper_2609_21848_gb300 import autotune
     dbbc.lib()
-    tuned = autotune.apply_saved("batch-4096" if a.workload == "serve" else a.workload)
+    tuned = autotune.apply_saved({"serve": "batch-4096", "sign-sweep": "chunglu-1m-200k-20m"}.get(a.workload,
+                                                                                                  a.workload))
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -497,8 +545,9 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    if a.workload in ("batch-4096", "serve"):
-        (run_batch if a.workload == "batch-4096" else run_serve)(a, torch, dbbc, world, rank, local, dist, barrier)
+    if a.workload in ("batch-4096", "serve", "sign-sweep"):
+        fn = {"batch-4096": run_batch, "serve": run_serve, "sign-sweep": run_sign_sweep}[a.workload]
+        fn(a, torch, dbbc, world, rank, local, dist, barrier)
         if dist is not None:
             dist.destroy_process_group()
         return
@@ -511,11 +560,17 @@ def main():
 
     eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
+    partition = a.partition and world > 1
+
     def step(prof_acc=None):
         eb0.record(stream)
         h = dbbc.dbbc_graph_from_coo(du, dv, ds, g.n_u, g.n_v, stream=stream)
         eb1.record(stream)
-        bal, unb, prof = dbbc.dbbc_count_profiled(h, stream=stream)
+        if partition:
+            bal, unb = dbbc.dbbc_count_partition(h, rank, world, stream=stream)
+            prof = {}
+        else:
+            bal, unb, prof = dbbc.dbbc_count_profiled(h, stream=stream)
         info = h.info
         h.free()
         if prof_acc is not None:
@@ -526,6 +581,10 @@ def main():
 
     for _ in range(a.warmup):
         bal, unb, info = step()
+    if partition:  # the parts' 16-byte results add up to the graph's counts
+        t = torch.tensor([bal, unb], dtype=torch.int64, device=dev)
+        dist.all_reduce(t)
+        bal, unb = (int(x) for x in t.tolist())
     want = expected_counts(a.workload)
     verified = None if want is None else ((bal, unb, info["wedges"]) == want)
 
@@ -550,7 +609,7 @@ def main():
         dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
     t_ms = float(t_ms.item())
     wedges = info["wedges"]
-    value = world * wedges * a.steps / (t_ms / 1e3) / 1e9
+    value = (1 if partition else world) * wedges * a.steps / (t_ms / 1e3) / 1e9
 
     # end to end through the public API with host buffers (pinned), H2D + D2H inside
     e2e_steps = a.steps if a.e2e_steps is None else a.e2e_steps
@@ -561,12 +620,20 @@ def main():
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            r = dbbc.count_coo(hu, hv, hs, g.n_u, g.n_v, stream=stream)
+            if partition:
+                with dbbc.dbbc_graph_from_coo(hu, hv, hs, g.n_u, g.n_v, stream=stream) as he:
+                    r = dbbc.dbbc_count_partition(he, rank, world, stream=stream)
+            else:
+                r = dbbc.count_coo(hu, hv, hs, g.n_u, g.n_v, stream=stream)
         torch.cuda.synchronize(dev)
         t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
         if dist is not None:
             dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * wedges * e2e_steps / float(t_e2e.item()) / 1e9, "unit": UNIT,
+        if partition:
+            t = torch.tensor(list(r), dtype=torch.int64, device=dev)
+            dist.all_reduce(t)
+            r = tuple(int(x) for x in t.tolist())
+        e2e = {"value": (1 if partition else world) * wedges * e2e_steps / float(t_e2e.item()) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 9 * g.m, "d2h_bytes_per_step": 16, "steps": e2e_steps,
                "bit_exact": r == (bal, unb)}
 
@@ -591,11 +658,14 @@ def main():
                                                          "ms_total")}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": t_ms / a.steps, "higher_is_better": True,
+            "scaling": "strong" if partition else "weak", "vs_baseline": None,
             "dtype": "int64", "data": "synthetic",
             "config": {"workload": a.workload, "n_u": g.n_u, "n_v": g.n_v, "edges": g.m,
                        "tuning": dbbc.dbbc_get_tuning(),
-                       "wedges_per_step": wedges, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "wedges_per_step": wedges,
+                       "parallelism": (f"LPT pivot partition x{world}" if partition else f"replicas x{world}")
+                       if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (COO %.0f MB, CSR %.0f MB > 129 MB)" % (
                            g.m * 9 / 1e6, (2 * g.m * 4 + (g.n_u + g.n_v) * 8) / 1e6)},
             "verified": verified, "counts": {"balanced": bal, "unbalanced": unb},

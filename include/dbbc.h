@@ -221,6 +221,21 @@ DBBC_API dbbc_status dbbc_graph_export(const dbbc_graph* g, void* cuda_stream, i
 DBBC_API void dbbc_set_allocator(void* (*alloc_fn)(size_t bytes, void* cuda_stream, void* ctx),
                         void (*free_fn)(void* ptr, void* cuda_stream, void* ctx), void* ctx);
 
+/* Greedy bin packing of Phase 3 (Section IV-A, Example 2): items in
+ * descending `work` order, each to the part with the smallest load so far
+ * (lowest part index on ties). Host arrays: work[n_items] in, part_of[n_items]
+ * and loads[n_parts] out. Pure host code (no GPU). */
+DBBC_API dbbc_status dbbc_lpt_partition(const uint64_t* work, int64_t n_items, int32_t n_parts, int32_t* part_of,
+                                        uint64_t* loads);
+
+/* Counts of the pivots that dbbc_lpt_partition assigns to `part` of
+ * `n_parts` by their accepted wedges (a hub's work items stay with it): with
+ * the graph replicated on n_parts GPUs, GPU k counts part k and the 16-byte
+ * results add up to dbbc_count's (Theorem 1). Host out-parameters;
+ * synchronous. */
+DBBC_API dbbc_status dbbc_count_partition(const dbbc_graph* g, void* cuda_stream, int32_t part, int32_t n_parts,
+                                          uint64_t* balanced, uint64_t* unbalanced);
+
 /* Tuning of the counting tiers, applied to graphs built after the call (a
  * handle keeps the values it was built with). Chosen per GPU by the
  * project's autotuner (paper_2609_21848_gb300/autotune.py); every setting only

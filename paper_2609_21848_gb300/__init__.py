@@ -32,7 +32,7 @@ EXPORTED = (
     "dbbc_graph_export", "dbbc_set_allocator", "dbbc_status_string", "dbbc_version", "dbbc_count_profiled",
     "dbbc_kernel_launches", "dbbc_count_noalloc", "dbbc_batch_create", "dbbc_batch_count_async",
     "dbbc_batch_count", "dbbc_batch_free", "dbbc_graph_from_coo_multi", "dbbc_count_components",
-    "dbbc_set_tuning", "dbbc_get_tuning",
+    "dbbc_set_tuning", "dbbc_get_tuning", "dbbc_lpt_partition", "dbbc_count_partition",
 )
 
 
@@ -97,6 +97,10 @@ def lib() -> ctypes.CDLL:
         L.dbbc_count_profiled.restype = st
         L.dbbc_kernel_launches.argtypes = []
         L.dbbc_kernel_launches.restype = ctypes.c_uint64
+        L.dbbc_lpt_partition.argtypes = [P, I64, I32, P, P]
+        L.dbbc_lpt_partition.restype = st
+        L.dbbc_count_partition.argtypes = [P, P, I32, I32, P, P]
+        L.dbbc_count_partition.restype = st
         L.dbbc_set_tuning.argtypes = [ctypes.POINTER(Tuning)]
         L.dbbc_set_tuning.restype = st
         L.dbbc_get_tuning.argtypes = [ctypes.POINTER(Tuning)]
@@ -425,6 +429,25 @@ def dbbc_set_allocator(use_torch: bool = True) -> None:
     refs = (_ALLOC_FN(_alloc), _FREE_FN(_free))
     lib().dbbc_set_allocator(ctypes.cast(refs[0], ctypes.c_void_p), ctypes.cast(refs[1], ctypes.c_void_p), None)
     _allocator_refs = refs
+
+
+def dbbc_lpt_partition(work, n_parts: int) -> tuple[np.ndarray, np.ndarray]:
+    """Greedy bin packing (Phase 3): (part of every item, load of every part)."""
+    w = np.ascontiguousarray(work, dtype=np.uint64)
+    part = np.zeros(w.shape[0], np.int32)
+    loads = np.zeros(n_parts, np.uint64)
+    _check(lib().dbbc_lpt_partition(w.ctypes.data, w.shape[0], n_parts, part.ctypes.data, loads.ctypes.data),
+           "dbbc_lpt_partition")
+    return part, loads
+
+
+def dbbc_count_partition(g: Graph, part: int, n_parts: int, stream=None) -> tuple[int, int]:
+    """(balanced, unbalanced) of the pivots LPT assigns to `part` of `n_parts`."""
+    out = (ctypes.c_uint64 * 2)()
+    base = ctypes.addressof(out)
+    _check(lib().dbbc_count_partition(g.handle, _stream_ptr(stream), part, n_parts, base, base + 8),
+           "dbbc_count_partition")
+    return int(out[0]), int(out[1])
 
 
 def dbbc_set_tuning(tuning: dict | None) -> None:

@@ -445,6 +445,47 @@ static dbbc_status batch_guard(F&& f) {
   }
 }
 
+// Counts of one graph restricted to some of its pivots: a one-graph plan
+// over the given medium and light pivot rows and hub items.
+void count_subset(const dbbc_graph* g, cudaStream_t s, const std::vector<int32_t>& medium_rows,
+                  const std::vector<int32_t>& light_rows, const std::vector<SweepItem>& hub_items, uint64_t* balanced,
+                  uint64_t* unbalanced) {
+  dbbc_batch plan;
+  dbbc_batch* b = &plan;
+  b->stream = s;
+  b->n_graphs = 1;
+  uint64_t h[2] = {0, 0};
+  try {
+    DBBC_CUDA(cudaGetDevice(&b->device));
+    set_batch_attributes();
+    std::vector<GraphDesc> desc(1, GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u,
+                                              g->tune.hash_mult_log});
+    b->n_medium = (int64_t)medium_rows.size();
+    b->n_light = (int64_t)light_rows.size();
+    b->max_lower = std::max<int64_t>(1, g->sweep_max_lower);
+    std::vector<BatchHubItem> items(hub_items.size());
+    for (size_t k = 0; k < hub_items.size(); k++) items[k] = BatchHubItem{0, 0, hub_items[k]};
+    finish_plan(b, desc, items);
+    std::vector<BatchPivot> med(medium_rows.size()), light(light_rows.size());
+    for (size_t k = 0; k < medium_rows.size(); k++) med[k] = BatchPivot{0, medium_rows[k]};
+    for (size_t k = 0; k < light_rows.size(); k++) light[k] = BatchPivot{0, light_rows[k]};
+    if (!med.empty())
+      DBBC_CUDA(cudaMemcpyAsync(b->medium, med.data(), med.size() * sizeof(BatchPivot), cudaMemcpyHostToDevice, s));
+    if (!light.empty())
+      DBBC_CUDA(cudaMemcpyAsync(b->light, light.data(), light.size() * sizeof(BatchPivot), cudaMemcpyHostToDevice,
+                                s));
+    enqueue_batch(b, s);
+    DBBC_CUDA(cudaMemcpyAsync(h, b->out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    check_batch_status(b, s);  // synchronizes (the host vectors outlive the copies)
+  } catch (...) {
+    batch_release(b);
+    throw;
+  }
+  batch_release(b);
+  if (balanced) *balanced = h[0];
+  if (unbalanced) *unbalanced = h[1];
+}
+
 }  // namespace dbbc
 
 using namespace dbbc;

@@ -301,6 +301,42 @@ def test_counts_do_not_depend_on_tuning(tuning):
         dbbc.dbbc_set_tuning(base)
 
 
+def test_sign_ratio_changes_the_split_not_the_total():
+    """Section VI sign-ratio study on a scaled Chung-Lu topology: the same
+    edges with P(+) from 0.1 to 0.9 give the same accepted wedges and the same
+    balanced + unbalanced total (the unsigned count), while the split moves;
+    every point matches the oracle."""
+    p = dict(synth.WORKLOADS["chunglu-1m-200k-20m"])
+    p.pop("index")
+    for k in ("n_u", "n_v", "m"):
+        p[k] = p[k] // 200
+    p["cap_u"] = p["cap_v"] = 100
+    totals, fracs, wedges = set(), [], set()
+    for pp in (0.1, 0.5, 0.9):
+        p["p_plus"] = pp
+        g = synth.generate(synth.SEED_BASE + 1, **p)
+        bal, unb, info = gpu_count(g.u, g.v, g.s, g.n_u, g.n_v)
+        assert (bal, unb, info["wedges"]) == oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)
+        totals.add(bal + unb)
+        wedges.add(info["wedges"])
+        fracs.append(bal / (bal + unb))
+    assert len(totals) == 1 and len(wedges) == 1
+    assert fracs[1] < fracs[0] and fracs[1] < fracs[2]  # P(+) = 1/2 balances least
+
+
+@pytest.mark.parametrize("parts", [1, 2, 3, 8])
+def test_partitions_add_up_to_the_count(parts):
+    """dbbc_count_partition: the LPT parts of one graph (as on `parts` GPUs)
+    add up to its count, on a graph with hubs, medium and light pivots."""
+    g = synth.workload("chunglu-1m-200k-20m", scale=0.02)
+    with dbbc.dbbc_graph_from_coo(g.u, g.v, g.s, g.n_u, g.n_v) as h:
+        total = dbbc.dbbc_count(h)
+        sums = [dbbc.dbbc_count_partition(h, p, parts) for p in range(parts)]
+    assert (sum(x[0] for x in sums), sum(x[1] for x in sums)) == total
+    if parts > 1:
+        assert all(x != (0, 0) for x in sums)
+
+
 def test_torch_allocator_hook():
     g = synth.workload("chunglu-1m-200k-20m", scale=0.003)
     want = oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[:2]
