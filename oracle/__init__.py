@@ -21,6 +21,10 @@ Counting in Signed Bipartite Graphs"):
   biadjacency (+1/-1/0) and A = |S|, for i < j, (AA^T)_ij = p + q and
   (SS^T)_ij = p - q, so balanced + unbalanced = sum C((AA^T)_ij, 2) and
   balanced - unbalanced = sum ((SS^T)_ij^2 - (AA^T)_ij) / 2.
+* :func:`count_per_vertex` -- butterflies containing each vertex (the "tip"
+  input of the paper's applications), Algorithm 1 plus a second walk of each
+  pivot's wedges for the middle vertices; :func:`brute_force_per_vertex`
+  enumerates Def. 1-2 for the same numbers.
 * :func:`workload_eq1` -- Eq. (1) of Phase 3; :func:`lpt` -- the Phase 3 greedy
   bin packing of Example 2.
 
@@ -66,6 +70,10 @@ def _load():
         lib.oracle_brute_force.argtypes = graph_args + [P, P]
         lib.oracle_workload_eq1.argtypes = graph_args + [P]
         lib.oracle_lpt.argtypes = [P, ctypes.c_int64, ctypes.c_int32, P, P]
+        lib.oracle_count_per_vertex.argtypes = graph_args + [P, P]
+        lib.oracle_count_per_vertex.restype = ctypes.c_int
+        lib.oracle_brute_force_per_vertex.argtypes = graph_args + [P, P]
+        lib.oracle_brute_force_per_vertex.restype = ctypes.c_int
         lib.oracle_graph_new.argtypes = graph_args + [ctypes.POINTER(ctypes.c_int)]
         lib.oracle_graph_new.restype = P
         lib.oracle_graph_count_sample.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, P, P, P]
@@ -119,6 +127,28 @@ def count_per_pivot(u, v, s, n_u: int, n_v: int, threads: int = 1):
                                         threads, b.ctypes.data, ub.ctypes.data, w.ctypes.data)
     _check(rc)
     return b, ub, w
+
+
+def count_per_vertex(u, v, s, n_u: int, n_v: int):
+    """Balanced and unbalanced butterflies containing each vertex (arrays over
+    unified ids u -> u, v -> n_u + v), following Algorithm 1 with a second
+    walk of each pivot's wedges for the middle vertices."""
+    u, v, s = _coo(u, v, s)
+    b = np.zeros(n_u + n_v, np.uint64)
+    ub = np.zeros(n_u + n_v, np.uint64)
+    _check(_load().oracle_count_per_vertex(u.ctypes.data, v.ctypes.data, s.ctypes.data, u.shape[0], n_u, n_v,
+                                           b.ctypes.data, ub.ctypes.data))
+    return b, ub
+
+
+def brute_force_per_vertex(u, v, s, n_u: int, n_v: int):
+    """Per-vertex counts by enumerating Def. 1-2 directly (tiny graphs)."""
+    u, v, s = _coo(u, v, s)
+    b = np.zeros(n_u + n_v, np.uint64)
+    ub = np.zeros(n_u + n_v, np.uint64)
+    _check(_load().oracle_brute_force_per_vertex(u.ctypes.data, v.ctypes.data, s.ctypes.data, u.shape[0], n_u,
+                                                 n_v, b.ctypes.data, ub.ctypes.data))
+    return b, ub
 
 
 class BuiltGraph:

@@ -224,6 +224,96 @@ int oracle_graph_count_sample(const void* h, int64_t first, int64_t step, int th
 
 void oracle_graph_free(void* h) { delete static_cast<SignedGraph*>(h); }
 
+// Butterflies containing each vertex (unified ids), following Algorithm 1:
+// after a pivot's buckets are complete, every touched endpoint w and the
+// pivot itself are in C(B1[w],2) + C(B2[w],2) balanced and B1[w]*B2[w]
+// unbalanced butterflies of that pivot; a middle vertex v of a symmetric
+// wedge u-v-w pairs with the B1[w] - 1 other symmetric wedges (balanced) and
+// the B2[w] asymmetric ones (unbalanced), and an asymmetric middle the other
+// way round (Lemma 1). The middles are found by walking the pivot's wedges a
+// second time.
+int oracle_count_per_vertex(const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, int32_t n_u,
+                            int32_t n_v, uint64_t* bal_v, uint64_t* unb_v) {
+  SignedGraph g;
+  int rc = build_graph(u, v, s, m, n_u, n_v, g);
+  if (rc != OK) return rc;
+  std::vector<uint32_t> B1(static_cast<size_t>(g.n), 0), B2(static_cast<size_t>(g.n), 0);
+  std::vector<uint8_t> seen(static_cast<size_t>(g.n), 0);
+  std::vector<int32_t> touched;
+  std::vector<u128> bal(static_cast<size_t>(g.n), 0), unb(static_cast<size_t>(g.n), 0);
+  for (int64_t p = 0; p < g.n; p++) {
+    for (const auto& pv : g.adj[p]) {
+      if (!lower_priority(g, pv.first, p)) continue;
+      for (const auto& vw : g.adj[pv.first]) {
+        if (!lower_priority(g, vw.first, p)) continue;
+        if (pv.second == vw.second) B1[vw.first]++; else B2[vw.first]++;
+        if (!seen[vw.first]) { seen[vw.first] = 1; touched.push_back(vw.first); }
+      }
+    }
+    for (int32_t w : touched) {
+      const u128 c = choose2(B1[w]) + choose2(B2[w]), d = static_cast<u128>(B1[w]) * B2[w];
+      bal[p] += c;
+      unb[p] += d;
+      bal[w] += c;
+      unb[w] += d;
+    }
+    for (const auto& pv : g.adj[p]) {  // second walk: the middle vertices
+      if (!lower_priority(g, pv.first, p)) continue;
+      for (const auto& vw : g.adj[pv.first]) {
+        if (!lower_priority(g, vw.first, p)) continue;
+        const uint32_t same = pv.second == vw.second ? B1[vw.first] : B2[vw.first];
+        const uint32_t other = pv.second == vw.second ? B2[vw.first] : B1[vw.first];
+        bal[pv.first] += same - 1;
+        unb[pv.first] += other;
+      }
+    }
+    for (int32_t w : touched) {
+      B1[w] = 0;
+      B2[w] = 0;
+      seen[w] = 0;
+    }
+    touched.clear();
+  }
+  const u128 lim = static_cast<u128>(UINT64_MAX);
+  for (int64_t x = 0; x < g.n; x++) {
+    if (bal[x] > lim || unb[x] > lim) return OVERFLOW_64;
+    bal_v[x] = static_cast<uint64_t>(bal[x]);
+    unb_v[x] = static_cast<uint64_t>(unb[x]);
+  }
+  return OK;
+}
+
+// Butterflies containing each vertex by direct enumeration of Def. 1-2 on a
+// dense sign matrix (tiny graphs only; shares nothing with the code above).
+int oracle_brute_force_per_vertex(const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, int32_t n_u,
+                                  int32_t n_v, uint64_t* bal_v, uint64_t* unb_v) {
+  if (m < 0 || n_u < 0 || n_v < 0) return BAD_INPUT;
+  if (static_cast<int64_t>(n_u) * n_v > (int64_t{1} << 24)) return BAD_INPUT;
+  std::vector<int8_t> S(static_cast<size_t>(n_u) * n_v, 0);
+  for (int64_t i = 0; i < m; i++) {
+    if (u[i] < 0 || u[i] >= n_u || v[i] < 0 || v[i] >= n_v) return BAD_INPUT;
+    if (s[i] != 1 && s[i] != -1) return BAD_INPUT;
+    S[static_cast<size_t>(u[i]) * n_v + v[i]] = s[i];
+  }
+  const int64_t n = static_cast<int64_t>(n_u) + n_v;
+  for (int64_t x = 0; x < n; x++) bal_v[x] = unb_v[x] = 0;
+  for (int32_t a = 0; a < n_u; a++)
+    for (int32_t b = a + 1; b < n_u; b++)
+      for (int32_t c = 0; c < n_v; c++)
+        for (int32_t d = c + 1; d < n_v; d++) {
+          const int8_t e[4] = {S[(size_t)a * n_v + c], S[(size_t)a * n_v + d], S[(size_t)b * n_v + c],
+                               S[(size_t)b * n_v + d]};
+          if (!e[0] || !e[1] || !e[2] || !e[3]) continue;
+          const int negatives = (e[0] < 0) + (e[1] < 0) + (e[2] < 0) + (e[3] < 0);
+          uint64_t* out = negatives % 2 == 0 ? bal_v : unb_v;
+          out[a]++;
+          out[b]++;
+          out[n_u + c]++;
+          out[n_u + d]++;
+        }
+  return OK;
+}
+
 // Def. 1-2 enumerated directly: a dense |U| x |V| sign matrix (later edges
 // overwrite earlier ones), every pair u1 < u2 and every pair v1 < v2, parity of
 // the negative edges among the four. Only for tiny graphs.

@@ -259,3 +259,39 @@ def test_lpt_example2():
     naive = [sum(work[i * 2:(i + 1) * 2]) for i in range(P)]
     assert naive == g["example2_naive_loads"][0]
     assert max(loads) / min(loads) == pytest.approx(19 / 16)
+
+
+# --------------------------------------------------------------- per-vertex counts
+@pytest.mark.parametrize("seed", range(6))
+def test_per_vertex_matches_brute_force(seed):
+    rng = np.random.default_rng(600 + seed)
+    n_u, n_v = int(rng.integers(2, 12)), int(rng.integers(2, 12))
+    u, v, s = _rand_graph(rng, n_u, n_v, int(rng.integers(1, n_u * n_v + 1)), float(rng.random()))
+    b, ub = oracle.count_per_vertex(u, v, s, n_u, n_v)
+    bb, bub = oracle.brute_force_per_vertex(u, v, s, n_u, n_v)
+    assert np.array_equal(b, bb) and np.array_equal(ub, bub)
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 5), (6, 4)])
+def test_per_vertex_complete_bipartite(a, b):
+    u, v, s = _kab(a, b)
+    bal, unb = oracle.count_per_vertex(u, v, s, a, b)
+    # a U vertex shares a butterfly with each other U vertex over each pair of V
+    assert bal[:a].tolist() == [(a - 1) * math.comb(b, 2)] * a
+    assert bal[a:].tolist() == [(b - 1) * math.comb(a, 2)] * b
+    assert unb.sum() == 0
+
+
+def test_per_vertex_sums_to_four_times_the_totals():
+    g = synth.workload("uniform-2k-3k-20k")
+    bal, unb, _ = oracle.count(g.u, g.v, g.s, g.n_u, g.n_v)
+    b, ub = oracle.count_per_vertex(g.u, g.v, g.s, g.n_u, g.n_v)
+    assert int(b.sum()) == 4 * bal and int(ub.sum()) == 4 * unb
+
+
+def test_per_vertex_worked_example():
+    g = read_golden("worked_example_k22.txt")
+    e = np.array(g["edge"])
+    b, ub = oracle.count_per_vertex(e[:, 0], e[:, 1], e[:, 2], 8, 9)
+    # the single balanced butterfly {2,7} x {5,8} contains exactly those four vertices
+    assert sorted(np.nonzero(b)[0].tolist()) == [2, 7, 8 + 5, 8 + 8] and b.sum() == 4 and ub.sum() == 0

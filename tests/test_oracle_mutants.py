@@ -90,9 +90,40 @@ def _pins_hold(lib) -> bool:
     return True
 
 
+VERTEX_MUTANTS = {
+    "middle counts itself": ("bal[pv.first] += same - 1;", "bal[pv.first] += same;"),
+    "middle unbalanced uses the same class": ("unb[pv.first] += other;", "unb[pv.first] += same;"),
+    "endpoint not credited": ("      bal[w] += c;\n", ""),
+    "pivot not credited": ("      unb[p] += d;\n", ""),
+}
+
+
+def _vertex_pins_hold(lib) -> bool:
+    P = ctypes.c_void_p
+    lib.oracle_count_per_vertex.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P]
+    lib.oracle_count_per_vertex.restype = ctypes.c_int
+    rng = np.random.default_rng(3)
+    for _ in range(6):
+        n_u, n_v = int(rng.integers(3, 9)), int(rng.integers(3, 9))
+        pairs = rng.choice(n_u * n_v, size=int(rng.integers(6, n_u * n_v + 1)), replace=False)
+        u = (pairs // n_v).astype(np.int32)
+        v = (pairs % n_v).astype(np.int32)
+        s = rng.choice([-1, 1], size=u.shape[0]).astype(np.int8)
+        b = np.zeros(n_u + n_v, np.uint64)
+        ub = np.zeros(n_u + n_v, np.uint64)
+        if lib.oracle_count_per_vertex(u.ctypes.data, v.ctypes.data, s.ctypes.data, u.shape[0], n_u, n_v,
+                                       b.ctypes.data, ub.ctypes.data):
+            return False
+        bb, bub = oracle.brute_force_per_vertex(u, v, s, n_u, n_v)
+        if not (np.array_equal(b, bb) and np.array_equal(ub, bub)):
+            return False
+    return True
+
+
 def test_unplanted_copy_passes(tmp_path):
     lib = _build_mutant(tmp_path, "none", "// CPU oracle", "// CPU oracle")
     assert _pins_hold(lib)
+    assert _vertex_pins_hold(lib)
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -100,3 +131,10 @@ def test_planted_mistake_is_caught(tmp_path, name):
     old, new = MUTANTS[name]
     lib = _build_mutant(tmp_path, name, old, new)
     assert not _pins_hold(lib), f"pins did not catch: {name}"
+
+
+@pytest.mark.parametrize("name", sorted(VERTEX_MUTANTS))
+def test_planted_per_vertex_mistake_is_caught(tmp_path, name):
+    old, new = VERTEX_MUTANTS[name]
+    lib = _build_mutant(tmp_path, name, old, new)
+    assert not _vertex_pins_hold(lib), f"pins did not catch: {name}"
