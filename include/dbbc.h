@@ -101,6 +101,20 @@ DBBC_API dbbc_status dbbc_graph_from_coo_multi(const int32_t* u, const int32_t* 
 DBBC_API dbbc_status dbbc_count_components(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced,
                                            uint64_t* unbalanced);
 
+/* Butterflies containing each vertex: balanced_v[x] and unbalanced_v[x]
+ * (HOST arrays of n_u + n_v entries, indexed by unified id: U vertex u is u,
+ * V vertex v is n_u + v; for a dbbc_graph_from_coo_multi handle the ids are
+ * the union's, graph i's U vertex u at sum_{j<i} n_u[j] + u and its V vertex v
+ * at N_U + sum_{j<i} n_v[j] + v, N_U the union's U side). Each butterfly of
+ * Def. 4 counted by dbbc_count is credited to its four vertices, so each array
+ * sums to four times the matching total. Computed by Algorithm 1 with a second
+ * walk of every pivot's wedges once its endpoint counts (Lemma 1's B1, B2) are
+ * final. Synchronous. Errors: DBBC_EINVAL (NULL graph, NULL array with
+ * vertices), DBBC_ENOMEM, DBBC_ECUDA, DBBC_EINTERNAL (a device-side check
+ * failed). */
+DBBC_API dbbc_status dbbc_count_vertices(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced_v,
+                                         uint64_t* unbalanced_v);
+
 /* Count balanced and unbalanced butterflies of one graph (Algorithm 1,
  * Phase 5, with the Lemma 1 unbalanced count). Host out-parameters; the call
  * returns after the counts are on the host. Either pointer may be NULL. */

@@ -33,6 +33,7 @@ EXPORTED = (
     "dbbc_kernel_launches", "dbbc_count_noalloc", "dbbc_batch_create", "dbbc_batch_count_async",
     "dbbc_batch_count", "dbbc_batch_free", "dbbc_graph_from_coo_multi", "dbbc_count_components",
     "dbbc_set_tuning", "dbbc_get_tuning", "dbbc_lpt_partition", "dbbc_count_partition",
+    "dbbc_count_vertices",
 )
 
 
@@ -109,6 +110,8 @@ def lib() -> ctypes.CDLL:
         L.dbbc_graph_from_coo_multi.restype = st
         L.dbbc_count_components.argtypes = [P, P, P, P]
         L.dbbc_count_components.restype = st
+        L.dbbc_count_vertices.argtypes = [P, P, P, P]
+        L.dbbc_count_vertices.restype = st
         L.dbbc_batch_create.argtypes = [P, I32, P, ctypes.POINTER(P)]
         L.dbbc_batch_create.restype = st
         L.dbbc_batch_count_async.argtypes = [P, P, P]
@@ -259,6 +262,18 @@ def dbbc_count_components(g: Graph, stream=None) -> tuple[np.ndarray, np.ndarray
     unb = np.zeros(max(n, 1), np.uint64)
     _check(lib().dbbc_count_components(g.handle, _stream_ptr(stream), bal.ctypes.data, unb.ctypes.data),
            "dbbc_count_components")
+    return bal[:n], unb[:n]
+
+
+def dbbc_count_vertices(g: Graph, stream=None) -> tuple[np.ndarray, np.ndarray]:
+    """(balanced, unbalanced) butterflies containing each vertex, indexed by
+    unified id (U vertex u at u, V vertex v at n_u + v); synchronous."""
+    info = dbbc_graph_get_info(g)
+    n = int(info["n_u"]) + int(info["n_v"])
+    bal = np.zeros(max(n, 1), np.uint64)
+    unb = np.zeros(max(n, 1), np.uint64)
+    _check(lib().dbbc_count_vertices(g.handle, _stream_ptr(stream), bal.ctypes.data, unb.ctypes.data),
+           "dbbc_count_vertices")
     return bal[:n], unb[:n]
 
 

@@ -1,0 +1,401 @@
+// Butterflies containing each vertex (the "tip" input of the paper's
+// applications), computed with the same tiers as the totals. Once the buckets
+// of a pivot u are complete (a pivot's hash table, or one window of a hub):
+//   * every endpoint w and u itself are in C(p,2) + C(q,2) balanced and p*q
+//     unbalanced butterflies of u, where (p, q) are w's symmetric and
+//     asymmetric bucket counts (Algorithm 1, Lemma 1);
+//   * the middle vertex v of a symmetric wedge u-v-w pairs with the p - 1
+//     other symmetric wedges (balanced) and the q asymmetric ones
+//     (unbalanced); of an asymmetric wedge, with q - 1 and p.
+// The middles need a second walk of the same wedges after the counts are
+// final; each (middle, pivot or window) adds its sums with one atomic.
+// Results are accumulated per CSR row and mapped to unified ids at the end.
+#include "count_device.cuh"
+
+namespace dbbc {
+
+// Counter of endpoint w in a shared hash table (the key must be present).
+__device__ __forceinline__ unsigned long long hash_find(const uint32_t* keys, const unsigned long long* vals,
+                                                        int log_h, uint32_t w) {
+  const uint32_t mask = (1u << log_h) - 1u;
+  uint32_t h = hash_slot(w, log_h);
+  for (uint32_t probe = 0; probe <= mask; probe++) {
+    if (keys[h] == w) return vals[h];
+    if (keys[h] == kEmptyKey) break;
+    h = (h + 1u) & mask;
+  }
+  return 0ull;
+}
+
+// Contribution to a middle vertex from one wedge whose endpoint has buckets
+// (p, q) packed as (q << 32) | p.
+__device__ __forceinline__ void middle_contrib(unsigned long long packed, bool sym, uint64_t& bal, uint64_t& unb) {
+  const uint64_t p = packed & 0xFFFFFFFFull, q = packed >> 32;
+  bal += sym ? p - 1 : q - 1;
+  unb += sym ? q : p;
+}
+
+__device__ __forceinline__ void endpoint_contrib(unsigned long long packed, uint64_t& bal, uint64_t& unb) {
+  const uint64_t p = packed & 0xFFFFFFFFull, q = packed >> 32;
+  bal += (p * (p - (p > 0)) >> 1) + (q * (q - (q > 0)) >> 1);
+  unb += p * q;
+}
+
+__device__ __forceinline__ void add_pair(unsigned long long* vb, unsigned long long* vu, int64_t row, uint64_t b,
+                                         uint64_t u) {
+  if (b) atomicAdd(&vb[row], (unsigned long long)b);
+  if (u) atomicAdd(&vu[row], (unsigned long long)u);
+}
+
+// The second walk over a pivot's wedges (lower-neighbour positions [a, b),
+// `step` apart in groups of 32 per warp): for each lower neighbour v, the warp
+// sums v's contributions over v's accepted segment and one lane adds them.
+template <typename Lookup>
+__device__ __forceinline__ void warp_middles(const CsrView& g, const PivotGeom& q, uint32_t a, uint32_t b,
+                                             uint32_t step, Lookup&& lookup, unsigned long long* vb,
+                                             unsigned long long* vu) {
+  const unsigned lane = lane_id();
+  for (uint32_t i0 = a; i0 < b; i0 += step) {
+    uint32_t e = 0;
+    int64_t vb0 = 0, ve = 0;
+    if (i0 + lane < b) {
+      e = g.col[q.rb + i0 + lane];
+      const int64_t vrow = q.base + (e >> 1);
+      vb0 = g.row_ptr[vrow];
+      ve = g.row_ptr[vrow + 1];
+    }
+    const uint32_t cnt = min(32u, b - i0);
+    for (uint32_t k = 0; k < cnt; k++) {
+      const uint32_t ek = __shfl_sync(kFullMask, e, k);
+      const uint32_t s1 = ek & 1u;
+      const int64_t jb0 = __shfl_sync(kFullMask, vb0, k);
+      const int64_t je = __shfl_sync(kFullMask, ve, k);
+      uint64_t sb = 0, su = 0;
+      for (int64_t jb = jb0; jb < je; jb += 32) {
+        const int64_t j = jb + lane;
+        const uint32_t x = j < je ? g.col[j] : 0xFFFFFFFFu;
+        const bool ok = x < q.lim;
+        if (ok) middle_contrib(lookup(x >> 1), ((x ^ s1) & 1u) == 0, sb, su);
+        if (__ballot_sync(kFullMask, !ok)) break;
+      }
+      sb = warp_sum_u64(sb);
+      su = warp_sum_u64(su);
+      if (lane == 0) add_pair(vb, vu, q.base + (ek >> 1), sb, su);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ light / medium
+__global__ void __launch_bounds__(kLightWarps * 32) vertex_light_kernel(CsrView g, const int32_t* __restrict__ piv,
+                                                                        const uint64_t* __restrict__ work,
+                                                                        int64_t n_piv, int hash_mult_log,
+                                                                        unsigned long long* vb,
+                                                                        unsigned long long* vu, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char light_smem[];
+  unsigned long long* vals_all = reinterpret_cast<unsigned long long*>(light_smem);
+  uint32_t* keys_all = reinterpret_cast<uint32_t*>(vals_all + kLightWarps * kLightSlots);
+  const int w = threadIdx.x >> 5;
+  const unsigned lane = lane_id();
+  uint32_t* keys = keys_all + w * kLightSlots;
+  unsigned long long* vals = vals_all + w * kLightSlots;
+  for (int i = lane; i < kLightSlots; i += 32) {
+    keys[i] = kEmptyKey;
+    vals[i] = 0;
+  }
+  __syncwarp();
+  bool full = false;
+  const int64_t nw = (int64_t)gridDim.x * kLightWarps;
+  for (int64_t t = (int64_t)blockIdx.x * kLightWarps + w; t < n_piv; t += nw) {
+    const int32_t p = piv[t];
+    const int log_h = table_log(work[p], 10, hash_mult_log);
+    const PivotGeom q = pivot_geom(g, p);
+    warp_walk<1>(g, q, 0, q.L, 32, [&](const uint32_t (&x)[1], uint32_t s1) {
+      if (x[0] != 0xFFFFFFFFu) {
+        unsigned long long old;
+        full |= !smem_hash_add(keys, vals, log_h, x[0] >> 1, wedge_inc(x[0], s1), &old);
+      }
+    });
+    __syncwarp();
+    const int64_t end_base = p < g.n_u ? 0 : (int64_t)g.n_u;  // endpoints share the pivot's side
+    uint64_t pb = 0, pu = 0;
+    for (int i = lane; i < (1 << log_h); i += 32) {
+      if (keys[i] != kEmptyKey) {
+        uint64_t eb = 0, eu = 0;
+        endpoint_contrib(vals[i], eb, eu);
+        add_pair(vb, vu, end_base + keys[i], eb, eu);
+        pb += eb;
+        pu += eu;
+      }
+    }
+    pb = warp_sum_u64(pb);
+    pu = warp_sum_u64(pu);
+    if (lane == 0) add_pair(vb, vu, p, pb, pu);
+    warp_middles(g, q, 0, q.L, 32, [&](uint32_t x) { return hash_find(keys, vals, log_h, x); }, vb, vu);
+    __syncwarp();
+    for (int i = lane; i < (1 << log_h); i += 32) {
+      keys[i] = kEmptyKey;
+      vals[i] = 0;
+    }
+    __syncwarp();
+  }
+  if (full) atomicOr(status, DBBC_DEV_HASH_FULL);
+}
+
+__global__ void __launch_bounds__(kMediumThreads) vertex_medium_kernel(CsrView g, const int32_t* __restrict__ piv,
+                                                                       const uint64_t* __restrict__ work,
+                                                                       int64_t n_piv, int hash_mult_log,
+                                                                       unsigned long long* vb,
+                                                                       unsigned long long* vu, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char med_smem[];
+  unsigned long long* vals = reinterpret_cast<unsigned long long*>(med_smem);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(vals + kMediumSlots);
+  for (int i = threadIdx.x; i < kMediumSlots; i += kMediumThreads) {
+    keys[i] = kEmptyKey;
+    vals[i] = 0;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5;
+  bool full = false;
+  for (int64_t t = blockIdx.x; t < n_piv; t += gridDim.x) {
+    const int32_t p = piv[t];
+    const int log_h = table_log(work[p], 13, hash_mult_log);
+    const PivotGeom q = pivot_geom(g, p);
+    warp_walk<2>(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u, [&](const uint32_t (&x)[2], uint32_t s1) {
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        if (x[u] != 0xFFFFFFFFu) {
+          unsigned long long old;
+          full |= !smem_hash_add(keys, vals, log_h, x[u] >> 1, wedge_inc(x[u], s1), &old);
+        }
+      }
+    });
+    __syncthreads();
+    const int64_t end_base = p < g.n_u ? 0 : (int64_t)g.n_u;
+    uint64_t pb = 0, pu = 0;
+    for (int i = threadIdx.x; i < (1 << log_h); i += kMediumThreads) {
+      if (keys[i] != kEmptyKey) {
+        uint64_t eb = 0, eu = 0;
+        endpoint_contrib(vals[i], eb, eu);
+        add_pair(vb, vu, end_base + keys[i], eb, eu);
+        pb += eb;
+        pu += eu;
+      }
+    }
+    pb = warp_sum_u64(pb);
+    pu = warp_sum_u64(pu);
+    if (lane_id() == 0) add_pair(vb, vu, p, pb, pu);
+    warp_middles(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u,
+                 [&](uint32_t x) { return hash_find(keys, vals, log_h, x); }, vb, vu);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (1 << log_h); i += kMediumThreads) {
+      keys[i] = kEmptyKey;
+      vals[i] = 0;
+    }
+    __syncthreads();
+  }
+  if (full) atomicOr(status, DBBC_DEV_HASH_FULL);
+}
+
+// ------------------------------------------------------------------ hub windows
+// Per window of a hub item: count (cursors move to `next`), credit endpoints
+// and the pivot from the dense window, then walk [pos, next) of every lower
+// neighbour again for the middles and advance pos. One lane per neighbour
+// segment (cursor state: pos, end, next).
+template <bool PACK16>
+__device__ __forceinline__ unsigned long long window_value(const uint32_t* c16, const unsigned long long* c32,
+                                                           uint32_t k) {
+  if (PACK16) {
+    const uint32_t v = c16[k];
+    return ((unsigned long long)(v >> 16) << 32) | (v & 0xFFFFu);
+  }
+  return c32[k];
+}
+
+template <bool PACK16>
+__device__ void vertex_window(const CsrView& g, const PivotGeom& q, int64_t* cur, uint32_t lo, uint32_t hi,
+                              uint32_t* c16, unsigned long long* c32, unsigned long long* vb,
+                              unsigned long long* vu, uint64_t& pb, uint64_t& pu) {
+  const uint32_t hl = hi << 1, lo2 = lo << 1;
+  for (uint32_t i = threadIdx.x; i < q.L; i += kSweepThreads) {
+    int64_t c = cur[3 * i];
+    const int64_t en = cur[3 * i + 1];
+    const uint32_t s1 = g.col[q.rb + i] & 1u;
+    for (; c < en; c++) {
+      const uint32_t x = g.col[c];
+      if (x >= hl) break;
+      const bool sym = ((x ^ s1) & 1u) == 0;
+      const uint32_t k = (x - lo2) >> 1;
+      if (PACK16) atomicAdd(&c16[k], sym ? 1u : 0x10000u);
+      else atomicAdd(&c32[k], sym ? 1ull : (1ull << 32));
+    }
+    cur[3 * i + 2] = c;
+  }
+  __syncthreads();
+  const int64_t end_base = q.base == 0 ? (int64_t)g.n_u : 0;  // endpoints share the pivot's side
+  for (uint32_t k = threadIdx.x; k < hi - lo; k += kSweepThreads) {
+    const unsigned long long v = window_value<PACK16>(c16, c32, k);
+    if (v) {
+      uint64_t eb = 0, eu = 0;
+      endpoint_contrib(v, eb, eu);
+      add_pair(vb, vu, end_base + lo + k, eb, eu);
+      pb += eb;
+      pu += eu;
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < q.L; i += kSweepThreads) {
+    const int64_t c0 = cur[3 * i], c1 = cur[3 * i + 2];
+    const uint32_t e = g.col[q.rb + i];
+    const uint32_t s1 = e & 1u;
+    uint64_t sb = 0, su = 0;
+    for (int64_t c = c0; c < c1; c++) {
+      const uint32_t x = g.col[c];
+      middle_contrib(window_value<PACK16>(c16, c32, (x - lo2) >> 1), ((x ^ s1) & 1u) == 0, sb, su);
+    }
+    add_pair(vb, vu, q.base + (e >> 1), sb, su);
+    cur[3 * i] = c1;
+  }
+  __syncthreads();
+  const uint32_t words = PACK16 ? (hi - lo) : 2 * (hi - lo);
+  for (uint32_t j = threadIdx.x; j < words; j += kSweepThreads) c16[j] = 0u;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSweepThreads) vertex_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
+                                                                     int64_t n_items, int* next_item,
+                                                                     int64_t* __restrict__ cursors, int64_t cur_cap,
+                                                                     unsigned long long* vb,
+                                                                     unsigned long long* vu) {
+  extern __shared__ __align__(16) unsigned char sweep_smem[];
+  uint32_t* c16 = reinterpret_cast<uint32_t*>(sweep_smem);
+  unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
+  __shared__ int item_sh;
+  __shared__ unsigned long long red[2][kSweepThreads / 32];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < (int)kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
+  int64_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 3;
+  for (;;) {
+    if (tid == 0) item_sh = atomicAdd(next_item, 1);
+    __syncthreads();
+    const int64_t it = item_sh;
+    __syncthreads();
+    if (it >= n_items) break;
+    const SweepItem item = items[it];
+    const PivotGeom q = pivot_geom(g, item.row);
+    const bool wide = item.wide != 0;
+    const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
+    const uint32_t first = item.lo << 1;
+    for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
+      const uint32_t e = g.col[q.rb + i];
+      const int64_t vrow = q.base + (e >> 1);
+      int64_t b = g.row_ptr[vrow];
+      const int64_t en = g.row_ptr[vrow + 1];
+      if (first) {
+        int64_t lo = b, hi = en;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (g.col[mid] < first) lo = mid + 1; else hi = mid;
+        }
+        b = lo;
+      }
+      cur[3 * i] = b;
+      cur[3 * i + 1] = en;
+    }
+    __syncthreads();
+    uint64_t pb = 0, pu = 0;
+    for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
+      const uint32_t hi = min(lo + H, item.hi);
+      if (wide) vertex_window<false>(g, q, cur, lo, hi, c16, c32, vb, vu, pb, pu);
+      else vertex_window<true>(g, q, cur, lo, hi, c16, c32, vb, vu, pb, pu);
+    }
+    // the pivot's own share of this item
+    pb = warp_sum_u64(pb);
+    pu = warp_sum_u64(pu);
+    if (lane_id() == 0) {
+      red[0][tid >> 5] = pb;
+      red[1][tid >> 5] = pu;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      uint64_t x = tid < kSweepThreads / 32 ? red[0][tid] : 0, y = tid < kSweepThreads / 32 ? red[1][tid] : 0;
+      x = warp_sum_u64(x);
+      y = warp_sum_u64(y);
+      if (tid == 0) add_pair(vb, vu, item.row, x, y);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void rows_to_ids_kernel(const int32_t* __restrict__ vertex, int64_t n, const unsigned long long* rb,
+                                   const unsigned long long* ru, unsigned long long* ob, unsigned long long* ou) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    ob[vertex[r]] = rb[r];
+    ou[vertex[r]] = ru[r];
+  }
+}
+
+}  // namespace dbbc
+
+using namespace dbbc;
+
+extern "C" dbbc_status dbbc_count_vertices(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced_v,
+                                           uint64_t* unbalanced_v) {
+  if (!g || (g->n > 0 && (!balanced_v || !unbalanced_v))) return DBBC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  try {
+    if (g->n == 0) return DBBC_OK;
+    Scratch sc(s);
+    const int64_t n = g->n;
+    unsigned long long* rows = sc.get<unsigned long long>((size_t)(4 * n));  // row sums, then per-id output
+    unsigned* d_status = sc.get<unsigned>(1);
+    DBBC_CUDA(cudaMemsetAsync(rows, 0, (size_t)(2 * n) * 8, s));
+    DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
+    unsigned long long* vb = rows;
+    unsigned long long* vu = rows + n;
+    const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
+    const int sms = num_sms();
+    if (g->n_light > 0) {
+      const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
+      DBBC_CUDA(cudaFuncSetAttribute(vertex_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
+      const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)vertex_light_kernel, kLightWarps * 32, smem);
+      vertex_light_kernel<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
+          view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, vb, vu, d_status);
+      DBBC_LAUNCH_CHECK();
+    }
+    if (g->n_medium > 0) {
+      const size_t smem = (size_t)kMediumSlots * 12;
+      DBBC_CUDA(cudaFuncSetAttribute(vertex_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)vertex_medium_kernel, kMediumThreads, smem);
+      vertex_medium_kernel<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
+          view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, vb, vu, d_status);
+      DBBC_LAUNCH_CHECK();
+    }
+    if (g->n_hub > 0) {
+      const size_t smem = (size_t)kSweepWindow16 * 4;
+      DBBC_CUDA(cudaFuncSetAttribute(vertex_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const int grid = sms * blocks_per_sm((const void*)vertex_sweep_kernel, kSweepThreads, smem);
+      int64_t* cursors = sc.get<int64_t>((size_t)grid * (size_t)g->sweep_max_lower * 3);
+      int* next = sc.get<int>(1);
+      DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
+      vertex_sweep_kernel<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, next, cursors,
+                                                            g->sweep_max_lower, vb, vu);
+      DBBC_LAUNCH_CHECK();
+    }
+    unsigned long long* ob = rows + 2 * n;
+    unsigned long long* ou = rows + 3 * n;
+    rows_to_ids_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(g->vertex, n, vb, vu, ob,
+                                                                                          ou);
+    DBBC_LAUNCH_CHECK();
+    DBBC_CUDA(cudaMemcpyAsync(balanced_v, ob, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaMemcpyAsync(unbalanced_v, ou, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    unsigned h = 0;
+    DBBC_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaStreamSynchronize(s));
+    if (h) return DBBC_EINTERNAL;
+  } catch (const Error& e) {
+    return e.status;
+  } catch (...) {
+    return DBBC_EINTERNAL;
+  }
+  return DBBC_OK;
+}
