@@ -25,6 +25,9 @@ Counting in Signed Bipartite Graphs"):
   input of the paper's applications), Algorithm 1 plus a second walk of each
   pivot's wedges for the middle vertices; :func:`brute_force_per_vertex`
   enumerates Def. 1-2 for the same numbers.
+* :func:`count_per_edge` -- butterflies containing each queried edge (the
+  "wing" input), Algorithm 1 with the same second walk crediting both edges of
+  every wedge; :func:`brute_force_per_edge` enumerates Def. 1-2 for them.
 * :func:`workload_eq1` -- Eq. (1) of Phase 3; :func:`lpt` -- the Phase 3 greedy
   bin packing of Example 2.
 
@@ -74,6 +77,10 @@ def _load():
         lib.oracle_count_per_vertex.restype = ctypes.c_int
         lib.oracle_brute_force_per_vertex.argtypes = graph_args + [P, P]
         lib.oracle_brute_force_per_vertex.restype = ctypes.c_int
+        lib.oracle_count_per_edge.argtypes = graph_args + [P, P, ctypes.c_int64, P, P]
+        lib.oracle_count_per_edge.restype = ctypes.c_int
+        lib.oracle_brute_force_per_edge.argtypes = graph_args + [P, P, ctypes.c_int64, P, P]
+        lib.oracle_brute_force_per_edge.restype = ctypes.c_int
         lib.oracle_graph_new.argtypes = graph_args + [ctypes.POINTER(ctypes.c_int)]
         lib.oracle_graph_new.restype = P
         lib.oracle_graph_count_sample.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, P, P, P]
@@ -149,6 +156,34 @@ def brute_force_per_vertex(u, v, s, n_u: int, n_v: int):
     _check(_load().oracle_brute_force_per_vertex(u.ctypes.data, v.ctypes.data, s.ctypes.data, u.shape[0], n_u,
                                                  n_v, b.ctypes.data, ub.ctypes.data))
     return b, ub
+
+
+def _per_edge(fn, u, v, s, n_u, n_v, qu, qv):
+    u, v, s = _coo(u, v, s)
+    if qu is None:
+        qu, qv = u, v
+    qu = np.ascontiguousarray(qu, dtype=np.int32)
+    qv = np.ascontiguousarray(qv, dtype=np.int32)
+    if qu.shape != qv.shape:
+        raise ValueError("qu and qv differ in length")
+    b = np.zeros(max(qu.shape[0], 1), np.uint64)
+    ub = np.zeros(max(qu.shape[0], 1), np.uint64)
+    _check(fn(u.ctypes.data, v.ctypes.data, s.ctypes.data, u.shape[0], n_u, n_v, qu.ctypes.data, qv.ctypes.data,
+              qu.shape[0], b.ctypes.data, ub.ctypes.data))
+    return b[:qu.shape[0]], ub[:qu.shape[0]]
+
+
+def count_per_edge(u, v, s, n_u: int, n_v: int, qu=None, qv=None):
+    """Balanced and unbalanced butterflies containing each queried pair
+    (qu[i], qv[i]) (default: the input edges, a repeated pair answering for the
+    edge it became); a pair that is not an edge gets zeros. Algorithm 1 with a
+    second walk crediting both edges of every wedge."""
+    return _per_edge(_load().oracle_count_per_edge, u, v, s, n_u, n_v, qu, qv)
+
+
+def brute_force_per_edge(u, v, s, n_u: int, n_v: int, qu=None, qv=None):
+    """Per-edge counts by enumerating Def. 1-2 directly (tiny graphs)."""
+    return _per_edge(_load().oracle_brute_force_per_edge, u, v, s, n_u, n_v, qu, qv)
 
 
 class BuiltGraph:

@@ -283,6 +283,113 @@ int oracle_count_per_vertex(const int32_t* u, const int32_t* v, const int8_t* s,
   return OK;
 }
 
+// Butterflies containing each edge (the pairs (qu[i], qv[i]), local ids; a
+// pair that is not an edge is in none), following Algorithm 1: once a pivot's
+// buckets are complete, the wedge u-v-w pairs with the other wedges that end
+// at w, B1[w] - 1 + B2[w] of them, closing a butterfly through both of its
+// edges (u, v) and (v, w); the pairs with the wedges of the same sign class are
+// balanced and the others unbalanced (Lemma 1). Every butterfly is found at its
+// highest-priority vertex with its four edges on its two wedges, so each edge
+// is credited once per butterfly. The wedges are walked a second time.
+int oracle_count_per_edge(const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, int32_t n_u,
+                          int32_t n_v, const int32_t* qu, const int32_t* qv, int64_t k, uint64_t* bal_e,
+                          uint64_t* unb_e) {
+  SignedGraph g;
+  int rc = build_graph(u, v, s, m, n_u, n_v, g);
+  if (rc != OK) return rc;
+  if (k < 0) return BAD_INPUT;
+  for (int64_t i = 0; i < k; i++)
+    if (qu[i] < 0 || qu[i] >= n_u || qv[i] < 0 || qv[i] >= n_v) return BAD_INPUT;
+  // an edge is keyed by its U end and its V end (local V id)
+  auto key = [n_u](int64_t a, int64_t b) -> uint64_t {
+    if (a >= n_u) std::swap(a, b);
+    return (static_cast<uint64_t>(a) << 32) | static_cast<uint64_t>(b - n_u);
+  };
+  std::unordered_map<uint64_t, std::pair<u128, u128>> per_edge;
+  std::vector<uint32_t> B1(static_cast<size_t>(g.n), 0), B2(static_cast<size_t>(g.n), 0);
+  std::vector<uint8_t> seen(static_cast<size_t>(g.n), 0);
+  std::vector<int32_t> touched;
+  for (int64_t p = 0; p < g.n; p++) {
+    for (const auto& pv : g.adj[p]) {
+      if (!lower_priority(g, pv.first, p)) continue;
+      for (const auto& vw : g.adj[pv.first]) {
+        if (!lower_priority(g, vw.first, p)) continue;
+        if (pv.second == vw.second) B1[vw.first]++; else B2[vw.first]++;
+        if (!seen[vw.first]) { seen[vw.first] = 1; touched.push_back(vw.first); }
+      }
+    }
+    for (const auto& pv : g.adj[p]) {  // second walk over the same wedges
+      if (!lower_priority(g, pv.first, p)) continue;
+      for (const auto& vw : g.adj[pv.first]) {
+        if (!lower_priority(g, vw.first, p)) continue;
+        const bool sym = pv.second == vw.second;
+        const u128 same = (sym ? B1[vw.first] : B2[vw.first]) - 1;
+        const u128 other = sym ? B2[vw.first] : B1[vw.first];
+        for (uint64_t e : {key(p, pv.first), key(pv.first, vw.first)}) {
+          auto& c = per_edge[e];
+          c.first += same;
+          c.second += other;
+        }
+      }
+    }
+    for (int32_t w : touched) {
+      B1[w] = 0;
+      B2[w] = 0;
+      seen[w] = 0;
+    }
+    touched.clear();
+  }
+  const u128 lim = static_cast<u128>(UINT64_MAX);
+  for (int64_t i = 0; i < k; i++) {
+    const auto it = per_edge.find(key(qu[i], static_cast<int64_t>(n_u) + qv[i]));
+    u128 b = 0, ub = 0;
+    if (it != per_edge.end()) {
+      b = it->second.first;
+      ub = it->second.second;
+    }
+    if (b > lim || ub > lim) return OVERFLOW_64;
+    bal_e[i] = static_cast<uint64_t>(b);
+    unb_e[i] = static_cast<uint64_t>(ub);
+  }
+  return OK;
+}
+
+// Butterflies containing each queried pair by direct enumeration of Def. 1-2
+// on a dense sign matrix (tiny graphs only; shares nothing with the code
+// above): every butterfly adds one to each of its four edges.
+int oracle_brute_force_per_edge(const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, int32_t n_u,
+                                int32_t n_v, const int32_t* qu, const int32_t* qv, int64_t k, uint64_t* bal_e,
+                                uint64_t* unb_e) {
+  if (m < 0 || n_u < 0 || n_v < 0 || k < 0) return BAD_INPUT;
+  if (static_cast<int64_t>(n_u) * n_v > (int64_t{1} << 24)) return BAD_INPUT;
+  const size_t cells = static_cast<size_t>(n_u) * n_v;
+  std::vector<int8_t> S(cells, 0);
+  for (int64_t i = 0; i < m; i++) {
+    if (u[i] < 0 || u[i] >= n_u || v[i] < 0 || v[i] >= n_v) return BAD_INPUT;
+    if (s[i] != 1 && s[i] != -1) return BAD_INPUT;
+    S[static_cast<size_t>(u[i]) * n_v + v[i]] = s[i];
+  }
+  std::vector<uint64_t> B(cells, 0), UB(cells, 0);
+  for (int32_t a = 0; a < n_u; a++)
+    for (int32_t b = a + 1; b < n_u; b++)
+      for (int32_t c = 0; c < n_v; c++)
+        for (int32_t d = c + 1; d < n_v; d++) {
+          const size_t cell[4] = {(size_t)a * n_v + c, (size_t)a * n_v + d, (size_t)b * n_v + c,
+                                  (size_t)b * n_v + d};
+          if (!S[cell[0]] || !S[cell[1]] || !S[cell[2]] || !S[cell[3]]) continue;
+          const int negatives = (S[cell[0]] < 0) + (S[cell[1]] < 0) + (S[cell[2]] < 0) + (S[cell[3]] < 0);
+          std::vector<uint64_t>& out = negatives % 2 == 0 ? B : UB;
+          for (size_t x : cell) out[x]++;
+        }
+  for (int64_t i = 0; i < k; i++) {
+    if (qu[i] < 0 || qu[i] >= n_u || qv[i] < 0 || qv[i] >= n_v) return BAD_INPUT;
+    const size_t x = static_cast<size_t>(qu[i]) * n_v + qv[i];
+    bal_e[i] = B[x];
+    unb_e[i] = UB[x];
+  }
+  return OK;
+}
+
 // Butterflies containing each vertex by direct enumeration of Def. 1-2 on a
 // dense sign matrix (tiny graphs only; shares nothing with the code above).
 int oracle_brute_force_per_vertex(const int32_t* u, const int32_t* v, const int8_t* s, int64_t m, int32_t n_u,

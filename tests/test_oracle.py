@@ -295,3 +295,52 @@ def test_per_vertex_worked_example():
     b, ub = oracle.count_per_vertex(e[:, 0], e[:, 1], e[:, 2], 8, 9)
     # the single balanced butterfly {2,7} x {5,8} contains exactly those four vertices
     assert sorted(np.nonzero(b)[0].tolist()) == [2, 7, 8 + 5, 8 + 8] and b.sum() == 4 and ub.sum() == 0
+
+
+# --------------------------------------------------------------- per-edge counts
+@pytest.mark.parametrize("seed", range(6))
+def test_per_edge_matches_brute_force(seed):
+    rng = np.random.default_rng(700 + seed)
+    n_u, n_v = int(rng.integers(2, 12)), int(rng.integers(2, 12))
+    u, v, s = _rand_graph(rng, n_u, n_v, int(rng.integers(1, n_u * n_v + 1)), float(rng.random()))
+    # queries: every cell of the biadjacency, edges and non-edges alike
+    qu, qv = np.meshgrid(np.arange(n_u), np.arange(n_v), indexing="ij")
+    b, ub = oracle.count_per_edge(u, v, s, n_u, n_v, qu.ravel(), qv.ravel())
+    bb, bub = oracle.brute_force_per_edge(u, v, s, n_u, n_v, qu.ravel(), qv.ravel())
+    assert np.array_equal(b, bb) and np.array_equal(ub, bub)
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 5), (6, 4)])
+def test_per_edge_complete_bipartite(a, b):
+    # an edge (u, v) of K(a,b) closes a butterfly with every other u' and v'
+    u, v, s = _kab(a, b)
+    bal, unb = oracle.count_per_edge(u, v, s, a, b)
+    assert bal.tolist() == [(a - 1) * (b - 1)] * (a * b) and unb.sum() == 0
+
+
+def test_per_edge_sums_to_four_times_the_totals():
+    g = synth.workload("uniform-2k-3k-20k")
+    bal, unb, _ = oracle.count(g.u, g.v, g.s, g.n_u, g.n_v)
+    # one query per distinct pair
+    pairs = np.unique(g.u.astype(np.int64) * g.n_v + g.v)
+    b, ub = oracle.count_per_edge(g.u, g.v, g.s, g.n_u, g.n_v, pairs // g.n_v, pairs % g.n_v)
+    assert int(b.sum()) == 4 * bal and int(ub.sum()) == 4 * unb
+
+
+def test_per_edge_worked_example_and_non_edges():
+    g = read_golden("worked_example_k22.txt")
+    e = np.array(g["edge"])
+    b, ub = oracle.count_per_edge(e[:, 0], e[:, 1], e[:, 2], 8, 9)
+    # the butterfly {2,7} x {5,8}: each of its four edges is in it, no other edge is
+    in_bf = np.isin(e[:, 0], [2, 7]) & np.isin(e[:, 1], [5, 8])
+    assert b.tolist() == in_bf.astype(int).tolist() and ub.sum() == 0
+    b, ub = oracle.count_per_edge(e[:, 0], e[:, 1], e[:, 2], 8, 9, [0, 7], [0, 0])
+    assert b.tolist() == [0, 0] and ub.tolist() == [0, 0]
+
+
+def test_per_edge_repeated_pairs_answer_for_the_kept_edge():
+    # K(2,2) whose edge (0,0) is first negative and then positive: the latest
+    # sign wins, so the butterfly is balanced and both copies report it
+    u, v, s = [0, 0, 0, 1, 1], [0, 0, 1, 0, 1], [-1, 1, 1, 1, 1]
+    b, ub = oracle.count_per_edge(u, v, s, 2, 2)
+    assert b.tolist() == [1] * 5 and ub.tolist() == [0] * 5

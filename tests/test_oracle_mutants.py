@@ -120,10 +120,45 @@ def _vertex_pins_hold(lib) -> bool:
     return True
 
 
+EDGE_MUTANTS = {
+    "edge pairs with itself": ("const u128 same = (sym ? B1[vw.first] : B2[vw.first]) - 1;",
+                               "const u128 same = (sym ? B1[vw.first] : B2[vw.first]);"),
+    "far edge not credited": ("for (uint64_t e : {key(p, pv.first), key(pv.first, vw.first)})",
+                              "for (uint64_t e : {key(p, pv.first)})"),
+    "edge unbalanced from the same class": ("const u128 other = sym ? B2[vw.first] : B1[vw.first];",
+                                            "const u128 other = sym ? B1[vw.first] : B2[vw.first];"),
+    "edge key ignores the sides": ("    if (a >= n_u) std::swap(a, b);\n", ""),
+}
+
+
+def _edge_pins_hold(lib) -> bool:
+    P = ctypes.c_void_p
+    lib.oracle_count_per_edge.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P,
+                                          ctypes.c_int64, P, P]
+    lib.oracle_count_per_edge.restype = ctypes.c_int
+    rng = np.random.default_rng(4)
+    for _ in range(6):
+        n_u, n_v = int(rng.integers(3, 9)), int(rng.integers(3, 9))
+        pairs = rng.choice(n_u * n_v, size=int(rng.integers(6, n_u * n_v + 1)), replace=False)
+        u = (pairs // n_v).astype(np.int32)
+        v = (pairs % n_v).astype(np.int32)
+        s = rng.choice([-1, 1], size=u.shape[0]).astype(np.int8)
+        b = np.zeros(u.shape[0], np.uint64)
+        ub = np.zeros(u.shape[0], np.uint64)
+        if lib.oracle_count_per_edge(u.ctypes.data, v.ctypes.data, s.ctypes.data, u.shape[0], n_u, n_v,
+                                     u.ctypes.data, v.ctypes.data, u.shape[0], b.ctypes.data, ub.ctypes.data):
+            return False
+        bb, bub = oracle.brute_force_per_edge(u, v, s, n_u, n_v)
+        if not (np.array_equal(b, bb) and np.array_equal(ub, bub)):
+            return False
+    return True
+
+
 def test_unplanted_copy_passes(tmp_path):
     lib = _build_mutant(tmp_path, "none", "// CPU oracle", "// CPU oracle")
     assert _pins_hold(lib)
     assert _vertex_pins_hold(lib)
+    assert _edge_pins_hold(lib)
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -138,3 +173,10 @@ def test_planted_per_vertex_mistake_is_caught(tmp_path, name):
     old, new = VERTEX_MUTANTS[name]
     lib = _build_mutant(tmp_path, name, old, new)
     assert not _vertex_pins_hold(lib), f"pins did not catch: {name}"
+
+
+@pytest.mark.parametrize("name", sorted(EDGE_MUTANTS))
+def test_planted_per_edge_mistake_is_caught(tmp_path, name):
+    old, new = EDGE_MUTANTS[name]
+    lib = _build_mutant(tmp_path, name, old, new)
+    assert not _edge_pins_hold(lib), f"pins did not catch: {name}"
