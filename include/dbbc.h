@@ -115,6 +115,25 @@ DBBC_API dbbc_status dbbc_count_components(const dbbc_graph* g, void* cuda_strea
 DBBC_API dbbc_status dbbc_count_vertices(const dbbc_graph* g, void* cuda_stream, uint64_t* balanced_v,
                                          uint64_t* unbalanced_v);
 
+/* Butterflies containing each queried edge: balanced_e[i] and
+ * unbalanced_e[i] for the pair (qu[i], qv[i]) (U id, V id, as passed to the
+ * build; a union handle takes the union's ids as in dbbc_count_vertices). A
+ * pair that is not an edge of the graph is in no butterfly and gets zeros; a
+ * pair passed to the build several times answers for the edge it became
+ * (latest sign). Every butterfly counted by dbbc_count is credited to its four
+ * edges, so over all distinct edges each array sums to four times the
+ * matching total. Computed by Algorithm 1 with a second walk of every pivot's
+ * wedges once Lemma 1's B1, B2 are final: a wedge u-v-w pairs with the other
+ * wedges ending at w, which closes one butterfly through (u, v) and (v, w)
+ * per pair.
+ *   qu, qv, balanced_e, unbalanced_e : k entries each, all four HOST or all
+ *       four DEVICE memory per `flags` (DBBC_INPUT_HOST / DBBC_INPUT_DEVICE).
+ * Device scratch: 16 bytes per CSR entry (2m) plus 4 bytes per vertex.
+ * Synchronous. Errors: DBBC_EINVAL (NULL graph or array, k < 0, unknown
+ * flags, an id out of range), DBBC_ENOMEM, DBBC_ECUDA, DBBC_EINTERNAL. */
+DBBC_API dbbc_status dbbc_count_edges(const dbbc_graph* g, void* cuda_stream, const int32_t* qu, const int32_t* qv,
+                                      int64_t k, uint32_t flags, uint64_t* balanced_e, uint64_t* unbalanced_e);
+
 /* Count balanced and unbalanced butterflies of one graph (Algorithm 1,
  * Phase 5, with the Lemma 1 unbalanced count). Host out-parameters; the call
  * returns after the counts are on the host. Either pointer may be NULL. */

@@ -33,7 +33,7 @@ EXPORTED = (
     "dbbc_kernel_launches", "dbbc_count_noalloc", "dbbc_batch_create", "dbbc_batch_count_async",
     "dbbc_batch_count", "dbbc_batch_free", "dbbc_graph_from_coo_multi", "dbbc_count_components",
     "dbbc_set_tuning", "dbbc_get_tuning", "dbbc_lpt_partition", "dbbc_count_partition",
-    "dbbc_count_vertices",
+    "dbbc_count_vertices", "dbbc_count_edges",
 )
 
 
@@ -112,6 +112,8 @@ def lib() -> ctypes.CDLL:
         L.dbbc_count_components.restype = st
         L.dbbc_count_vertices.argtypes = [P, P, P, P]
         L.dbbc_count_vertices.restype = st
+        L.dbbc_count_edges.argtypes = [P, P, P, P, I64, U32, P, P]
+        L.dbbc_count_edges.restype = st
         L.dbbc_batch_create.argtypes = [P, I32, P, ctypes.POINTER(P)]
         L.dbbc_batch_create.restype = st
         L.dbbc_batch_count_async.argtypes = [P, P, P]
@@ -275,6 +277,33 @@ def dbbc_count_vertices(g: Graph, stream=None) -> tuple[np.ndarray, np.ndarray]:
     _check(lib().dbbc_count_vertices(g.handle, _stream_ptr(stream), bal.ctypes.data, unb.ctypes.data),
            "dbbc_count_vertices")
     return bal[:n], unb[:n]
+
+
+def dbbc_count_edges(g: Graph, qu, qv, stream=None):
+    """(balanced, unbalanced) butterflies containing each queried edge
+    (qu[i], qv[i]); zeros for a pair that is not an edge. Host arrays in give
+    numpy uint64 arrays out; CUDA tensors in give CUDA uint64 tensors out."""
+    pu, ku_n, du, ku = _array_ptr(qu, np.int32)
+    pv, kv_n, dv, kv = _array_ptr(qv, np.int32)
+    if ku_n != kv_n:
+        raise ValueError("qu and qv differ in length")
+    if du != dv:
+        raise ValueError("qu and qv must both be on the host or both on the device")
+    k = ku_n
+    if du:
+        import torch
+        dev = qu.device
+        bal = torch.zeros(max(k, 1), dtype=torch.uint64, device=dev)
+        unb = torch.zeros(max(k, 1), dtype=torch.uint64, device=dev)
+        pb, pub = bal.data_ptr(), unb.data_ptr()
+    else:
+        bal = np.zeros(max(k, 1), np.uint64)
+        unb = np.zeros(max(k, 1), np.uint64)
+        pb, pub = bal.ctypes.data, unb.ctypes.data
+    _check(lib().dbbc_count_edges(g.handle, _stream_ptr(stream), pu, pv, k,
+                                  DBBC_INPUT_DEVICE if du else DBBC_INPUT_HOST, pb, pub), "dbbc_count_edges")
+    del ku, kv
+    return bal[:k], unb[:k]
 
 
 def dbbc_count(g: Graph, stream=None) -> tuple[int, int]:

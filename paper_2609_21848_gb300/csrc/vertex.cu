@@ -1,18 +1,28 @@
 // Butterflies containing each vertex (the "tip" input of the paper's
-// applications), computed with the same tiers as the totals. Once the buckets
-// of a pivot u are complete (a pivot's hash table, or one window of a hub):
+// applications) and each edge (the "wing" input), computed with the same
+// tiers as the totals. Once the buckets of a pivot u are complete (a pivot's
+// hash table, or one window of a hub):
 //   * every endpoint w and u itself are in C(p,2) + C(q,2) balanced and p*q
 //     unbalanced butterflies of u, where (p, q) are w's symmetric and
 //     asymmetric bucket counts (Algorithm 1, Lemma 1);
-//   * the middle vertex v of a symmetric wedge u-v-w pairs with the p - 1
-//     other symmetric wedges (balanced) and the q asymmetric ones
-//     (unbalanced); of an asymmetric wedge, with q - 1 and p.
-// The middles need a second walk of the same wedges after the counts are
-// final; each (middle, pivot or window) adds its sums with one atomic.
-// Results are accumulated per CSR row and mapped to unified ids at the end.
+//   * a symmetric wedge u-v-w pairs with the p - 1 other symmetric wedges to w
+//     (balanced) and the q asymmetric ones (unbalanced); an asymmetric wedge
+//     with q - 1 and p. Each pairing is one butterfly through the middle v and
+//     through both edges (u, v) and (v, w) of the wedge.
+// The middles and edges need a second walk of the same wedges after the counts
+// are final. Vertex results are accumulated per CSR row and mapped to unified
+// ids at the end; edge results per CSR position (an edge has one position in
+// each of its two rows), summed over both positions when an edge is queried.
 #include "count_device.cuh"
 
 namespace dbbc {
+
+struct TipOut {
+  unsigned long long* vb = nullptr;  // [n] per row (vertex counts)
+  unsigned long long* vu = nullptr;
+  unsigned long long* eb = nullptr;  // [nnz] per CSR position (edge counts)
+  unsigned long long* eu = nullptr;
+};
 
 // Counter of endpoint w in a shared hash table (the key must be present).
 __device__ __forceinline__ unsigned long long hash_find(const uint32_t* keys, const unsigned long long* vals,
@@ -27,12 +37,13 @@ __device__ __forceinline__ unsigned long long hash_find(const uint32_t* keys, co
   return 0ull;
 }
 
-// Contribution to a middle vertex from one wedge whose endpoint has buckets
-// (p, q) packed as (q << 32) | p.
-__device__ __forceinline__ void middle_contrib(unsigned long long packed, bool sym, uint64_t& bal, uint64_t& unb) {
+// Butterflies one wedge is in, from its endpoint's buckets (p, q) packed as
+// (q << 32) | p: the other wedges of its own class close balanced ones, the
+// wedges of the other class unbalanced ones.
+__device__ __forceinline__ void wedge_pairs(unsigned long long packed, bool sym, uint64_t& bal, uint64_t& unb) {
   const uint64_t p = packed & 0xFFFFFFFFull, q = packed >> 32;
-  bal += sym ? p - 1 : q - 1;
-  unb += sym ? q : p;
+  bal = sym ? p - 1 : q - 1;
+  unb = sym ? q : p;
 }
 
 __device__ __forceinline__ void endpoint_contrib(unsigned long long packed, uint64_t& bal, uint64_t& unb) {
@@ -41,19 +52,19 @@ __device__ __forceinline__ void endpoint_contrib(unsigned long long packed, uint
   unb += p * q;
 }
 
-__device__ __forceinline__ void add_pair(unsigned long long* vb, unsigned long long* vu, int64_t row, uint64_t b,
-                                         uint64_t u) {
-  if (b) atomicAdd(&vb[row], (unsigned long long)b);
-  if (u) atomicAdd(&vu[row], (unsigned long long)u);
+__device__ __forceinline__ void add_pair(unsigned long long* b, unsigned long long* u, int64_t i, uint64_t x,
+                                         uint64_t y) {
+  if (x) atomicAdd(&b[i], (unsigned long long)x);
+  if (y) atomicAdd(&u[i], (unsigned long long)y);
 }
 
 // The second walk over a pivot's wedges (lower-neighbour positions [a, b),
-// `step` apart in groups of 32 per warp): for each lower neighbour v, the warp
-// sums v's contributions over v's accepted segment and one lane adds them.
-template <typename Lookup>
-__device__ __forceinline__ void warp_middles(const CsrView& g, const PivotGeom& q, uint32_t a, uint32_t b,
-                                             uint32_t step, Lookup&& lookup, unsigned long long* vb,
-                                             unsigned long long* vu) {
+// `step` apart in groups of 32 per warp): each lane credits the far edge
+// (v, w) of its wedge; the warp sums v's wedges and one lane credits the
+// middle v and the near edge (u, v).
+template <bool VERT, bool EDGE, typename Lookup>
+__device__ __forceinline__ void warp_second_walk(const CsrView& g, const PivotGeom& q, uint32_t a, uint32_t b,
+                                                 uint32_t step, Lookup&& lookup, const TipOut& o) {
   const unsigned lane = lane_id();
   for (uint32_t i0 = a; i0 < b; i0 += step) {
     uint32_t e = 0;
@@ -75,22 +86,31 @@ __device__ __forceinline__ void warp_middles(const CsrView& g, const PivotGeom& 
         const int64_t j = jb + lane;
         const uint32_t x = j < je ? g.col[j] : 0xFFFFFFFFu;
         const bool ok = x < q.lim;
-        if (ok) middle_contrib(lookup(x >> 1), ((x ^ s1) & 1u) == 0, sb, su);
-        if (__ballot_sync(kFullMask, !ok)) break;
+        if (ok) {
+          uint64_t cb, cu;
+          wedge_pairs(lookup(x >> 1), ((x ^ s1) & 1u) == 0, cb, cu);
+          if (EDGE) add_pair(o.eb, o.eu, j, cb, cu);
+          sb += cb;
+          su += cu;
+        }
+        if (__ballot_sync(kFullMask, !ok)) break;  // rows ascend: nothing accepted beyond
       }
       sb = warp_sum_u64(sb);
       su = warp_sum_u64(su);
-      if (lane == 0) add_pair(vb, vu, q.base + (ek >> 1), sb, su);
+      if (lane == 0) {
+        if (VERT) add_pair(o.vb, o.vu, q.base + (ek >> 1), sb, su);
+        if (EDGE) add_pair(o.eb, o.eu, q.rb + i0 + k, sb, su);
+      }
     }
   }
 }
 
 // ------------------------------------------------------------------ light / medium
-__global__ void __launch_bounds__(kLightWarps * 32) vertex_light_kernel(CsrView g, const int32_t* __restrict__ piv,
-                                                                        const uint64_t* __restrict__ work,
-                                                                        int64_t n_piv, int hash_mult_log,
-                                                                        unsigned long long* vb,
-                                                                        unsigned long long* vu, unsigned* status) {
+template <bool VERT, bool EDGE>
+__global__ void __launch_bounds__(kLightWarps * 32) tips_light_kernel(CsrView g, const int32_t* __restrict__ piv,
+                                                                      const uint64_t* __restrict__ work,
+                                                                      int64_t n_piv, int hash_mult_log, TipOut o,
+                                                                      unsigned* status) {
   extern __shared__ __align__(16) unsigned char light_smem[];
   unsigned long long* vals_all = reinterpret_cast<unsigned long long*>(light_smem);
   uint32_t* keys_all = reinterpret_cast<uint32_t*>(vals_all + kLightWarps * kLightSlots);
@@ -116,21 +136,23 @@ __global__ void __launch_bounds__(kLightWarps * 32) vertex_light_kernel(CsrView 
       }
     });
     __syncwarp();
-    const int64_t end_base = p < g.n_u ? 0 : (int64_t)g.n_u;  // endpoints share the pivot's side
-    uint64_t pb = 0, pu = 0;
-    for (int i = lane; i < (1 << log_h); i += 32) {
-      if (keys[i] != kEmptyKey) {
-        uint64_t eb = 0, eu = 0;
-        endpoint_contrib(vals[i], eb, eu);
-        add_pair(vb, vu, end_base + keys[i], eb, eu);
-        pb += eb;
-        pu += eu;
+    if (VERT) {
+      const int64_t end_base = p < g.n_u ? 0 : (int64_t)g.n_u;  // endpoints share the pivot's side
+      uint64_t pb = 0, pu = 0;
+      for (int i = lane; i < (1 << log_h); i += 32) {
+        if (keys[i] != kEmptyKey) {
+          uint64_t eb = 0, eu = 0;
+          endpoint_contrib(vals[i], eb, eu);
+          add_pair(o.vb, o.vu, end_base + keys[i], eb, eu);
+          pb += eb;
+          pu += eu;
+        }
       }
+      pb = warp_sum_u64(pb);
+      pu = warp_sum_u64(pu);
+      if (lane == 0) add_pair(o.vb, o.vu, p, pb, pu);
     }
-    pb = warp_sum_u64(pb);
-    pu = warp_sum_u64(pu);
-    if (lane == 0) add_pair(vb, vu, p, pb, pu);
-    warp_middles(g, q, 0, q.L, 32, [&](uint32_t x) { return hash_find(keys, vals, log_h, x); }, vb, vu);
+    warp_second_walk<VERT, EDGE>(g, q, 0, q.L, 32, [&](uint32_t x) { return hash_find(keys, vals, log_h, x); }, o);
     __syncwarp();
     for (int i = lane; i < (1 << log_h); i += 32) {
       keys[i] = kEmptyKey;
@@ -141,11 +163,11 @@ __global__ void __launch_bounds__(kLightWarps * 32) vertex_light_kernel(CsrView 
   if (full) atomicOr(status, DBBC_DEV_HASH_FULL);
 }
 
-__global__ void __launch_bounds__(kMediumThreads) vertex_medium_kernel(CsrView g, const int32_t* __restrict__ piv,
-                                                                       const uint64_t* __restrict__ work,
-                                                                       int64_t n_piv, int hash_mult_log,
-                                                                       unsigned long long* vb,
-                                                                       unsigned long long* vu, unsigned* status) {
+template <bool VERT, bool EDGE>
+__global__ void __launch_bounds__(kMediumThreads) tips_medium_kernel(CsrView g, const int32_t* __restrict__ piv,
+                                                                     const uint64_t* __restrict__ work,
+                                                                     int64_t n_piv, int hash_mult_log, TipOut o,
+                                                                     unsigned* status) {
   extern __shared__ __align__(16) unsigned char med_smem[];
   unsigned long long* vals = reinterpret_cast<unsigned long long*>(med_smem);
   uint32_t* keys = reinterpret_cast<uint32_t*>(vals + kMediumSlots);
@@ -170,22 +192,24 @@ __global__ void __launch_bounds__(kMediumThreads) vertex_medium_kernel(CsrView g
       }
     });
     __syncthreads();
-    const int64_t end_base = p < g.n_u ? 0 : (int64_t)g.n_u;
-    uint64_t pb = 0, pu = 0;
-    for (int i = threadIdx.x; i < (1 << log_h); i += kMediumThreads) {
-      if (keys[i] != kEmptyKey) {
-        uint64_t eb = 0, eu = 0;
-        endpoint_contrib(vals[i], eb, eu);
-        add_pair(vb, vu, end_base + keys[i], eb, eu);
-        pb += eb;
-        pu += eu;
+    if (VERT) {
+      const int64_t end_base = p < g.n_u ? 0 : (int64_t)g.n_u;
+      uint64_t pb = 0, pu = 0;
+      for (int i = threadIdx.x; i < (1 << log_h); i += kMediumThreads) {
+        if (keys[i] != kEmptyKey) {
+          uint64_t eb = 0, eu = 0;
+          endpoint_contrib(vals[i], eb, eu);
+          add_pair(o.vb, o.vu, end_base + keys[i], eb, eu);
+          pb += eb;
+          pu += eu;
+        }
       }
+      pb = warp_sum_u64(pb);
+      pu = warp_sum_u64(pu);
+      if (lane_id() == 0) add_pair(o.vb, o.vu, p, pb, pu);
     }
-    pb = warp_sum_u64(pb);
-    pu = warp_sum_u64(pu);
-    if (lane_id() == 0) add_pair(vb, vu, p, pb, pu);
-    warp_middles(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u,
-                 [&](uint32_t x) { return hash_find(keys, vals, log_h, x); }, vb, vu);
+    warp_second_walk<VERT, EDGE>(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u,
+                                 [&](uint32_t x) { return hash_find(keys, vals, log_h, x); }, o);
     __syncthreads();
     for (int i = threadIdx.x; i < (1 << log_h); i += kMediumThreads) {
       keys[i] = kEmptyKey;
@@ -197,10 +221,11 @@ __global__ void __launch_bounds__(kMediumThreads) vertex_medium_kernel(CsrView g
 }
 
 // ------------------------------------------------------------------ hub windows
-// Per window of a hub item: count (cursors move to `next`), credit endpoints
-// and the pivot from the dense window, then walk [pos, next) of every lower
-// neighbour again for the middles and advance pos. One lane per neighbour
-// segment (cursor state: pos, end, next).
+// Per window of a hub item: count (each lower neighbour's cursor stops at
+// `next`), credit the endpoints and the pivot from the dense window, then walk
+// [pos, next) of every lower neighbour again for the middles and edges and
+// move pos to next. One thread per neighbour segment; cursor state per
+// neighbour: pos, end, next.
 template <bool PACK16>
 __device__ __forceinline__ unsigned long long window_value(const uint32_t* c16, const unsigned long long* c32,
                                                            uint32_t k) {
@@ -211,10 +236,9 @@ __device__ __forceinline__ unsigned long long window_value(const uint32_t* c16, 
   return c32[k];
 }
 
-template <bool PACK16>
-__device__ void vertex_window(const CsrView& g, const PivotGeom& q, int64_t* cur, uint32_t lo, uint32_t hi,
-                              uint32_t* c16, unsigned long long* c32, unsigned long long* vb,
-                              unsigned long long* vu, uint64_t& pb, uint64_t& pu) {
+template <bool PACK16, bool VERT, bool EDGE>
+__device__ void tips_window(const CsrView& g, const PivotGeom& q, int64_t* cur, uint32_t lo, uint32_t hi,
+                            uint32_t* c16, unsigned long long* c32, const TipOut& o, uint64_t& pb, uint64_t& pu) {
   const uint32_t hl = hi << 1, lo2 = lo << 1;
   for (uint32_t i = threadIdx.x; i < q.L; i += kSweepThreads) {
     int64_t c = cur[3 * i];
@@ -231,15 +255,17 @@ __device__ void vertex_window(const CsrView& g, const PivotGeom& q, int64_t* cur
     cur[3 * i + 2] = c;
   }
   __syncthreads();
-  const int64_t end_base = q.base == 0 ? (int64_t)g.n_u : 0;  // endpoints share the pivot's side
-  for (uint32_t k = threadIdx.x; k < hi - lo; k += kSweepThreads) {
-    const unsigned long long v = window_value<PACK16>(c16, c32, k);
-    if (v) {
-      uint64_t eb = 0, eu = 0;
-      endpoint_contrib(v, eb, eu);
-      add_pair(vb, vu, end_base + lo + k, eb, eu);
-      pb += eb;
-      pu += eu;
+  if (VERT) {
+    const int64_t end_base = q.base == 0 ? (int64_t)g.n_u : 0;  // endpoints share the pivot's side
+    for (uint32_t k = threadIdx.x; k < hi - lo; k += kSweepThreads) {
+      const unsigned long long v = window_value<PACK16>(c16, c32, k);
+      if (v) {
+        uint64_t eb = 0, eu = 0;
+        endpoint_contrib(v, eb, eu);
+        add_pair(o.vb, o.vu, end_base + lo + k, eb, eu);
+        pb += eb;
+        pu += eu;
+      }
     }
   }
   for (uint32_t i = threadIdx.x; i < q.L; i += kSweepThreads) {
@@ -249,9 +275,14 @@ __device__ void vertex_window(const CsrView& g, const PivotGeom& q, int64_t* cur
     uint64_t sb = 0, su = 0;
     for (int64_t c = c0; c < c1; c++) {
       const uint32_t x = g.col[c];
-      middle_contrib(window_value<PACK16>(c16, c32, (x - lo2) >> 1), ((x ^ s1) & 1u) == 0, sb, su);
+      uint64_t cb, cu;
+      wedge_pairs(window_value<PACK16>(c16, c32, (x - lo2) >> 1), ((x ^ s1) & 1u) == 0, cb, cu);
+      if (EDGE) add_pair(o.eb, o.eu, c, cb, cu);
+      sb += cb;
+      su += cu;
     }
-    add_pair(vb, vu, q.base + (e >> 1), sb, su);
+    if (VERT) add_pair(o.vb, o.vu, q.base + (e >> 1), sb, su);
+    if (EDGE) add_pair(o.eb, o.eu, q.rb + i, sb, su);
     cur[3 * i] = c1;
   }
   __syncthreads();
@@ -260,11 +291,11 @@ __device__ void vertex_window(const CsrView& g, const PivotGeom& q, int64_t* cur
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSweepThreads) vertex_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
-                                                                     int64_t n_items, int* next_item,
-                                                                     int64_t* __restrict__ cursors, int64_t cur_cap,
-                                                                     unsigned long long* vb,
-                                                                     unsigned long long* vu) {
+template <bool VERT, bool EDGE>
+__global__ void __launch_bounds__(kSweepThreads) tips_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
+                                                                   int64_t n_items, int* next_item,
+                                                                   int64_t* __restrict__ cursors, int64_t cur_cap,
+                                                                   TipOut o) {
   extern __shared__ __align__(16) unsigned char sweep_smem[];
   uint32_t* c16 = reinterpret_cast<uint32_t*>(sweep_smem);
   unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
@@ -289,7 +320,7 @@ __global__ void __launch_bounds__(kSweepThreads) vertex_sweep_kernel(CsrView g, 
       const int64_t vrow = q.base + (e >> 1);
       int64_t b = g.row_ptr[vrow];
       const int64_t en = g.row_ptr[vrow + 1];
-      if (first) {
+      if (first) {  // lower_bound of `first` in the row
         int64_t lo = b, hi = en;
         while (lo < hi) {
           const int64_t mid = (lo + hi) >> 1;
@@ -304,24 +335,25 @@ __global__ void __launch_bounds__(kSweepThreads) vertex_sweep_kernel(CsrView g, 
     uint64_t pb = 0, pu = 0;
     for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
       const uint32_t hi = min(lo + H, item.hi);
-      if (wide) vertex_window<false>(g, q, cur, lo, hi, c16, c32, vb, vu, pb, pu);
-      else vertex_window<true>(g, q, cur, lo, hi, c16, c32, vb, vu, pb, pu);
+      if (wide) tips_window<false, VERT, EDGE>(g, q, cur, lo, hi, c16, c32, o, pb, pu);
+      else tips_window<true, VERT, EDGE>(g, q, cur, lo, hi, c16, c32, o, pb, pu);
     }
-    // the pivot's own share of this item
-    pb = warp_sum_u64(pb);
-    pu = warp_sum_u64(pu);
-    if (lane_id() == 0) {
-      red[0][tid >> 5] = pb;
-      red[1][tid >> 5] = pu;
+    if (VERT) {  // the pivot's share of this item
+      pb = warp_sum_u64(pb);
+      pu = warp_sum_u64(pu);
+      if (lane_id() == 0) {
+        red[0][tid >> 5] = pb;
+        red[1][tid >> 5] = pu;
+      }
+      __syncthreads();
+      if (tid < 32) {
+        uint64_t x = tid < kSweepThreads / 32 ? red[0][tid] : 0, y = tid < kSweepThreads / 32 ? red[1][tid] : 0;
+        x = warp_sum_u64(x);
+        y = warp_sum_u64(y);
+        if (tid == 0) add_pair(o.vb, o.vu, item.row, x, y);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (tid < 32) {
-      uint64_t x = tid < kSweepThreads / 32 ? red[0][tid] : 0, y = tid < kSweepThreads / 32 ? red[1][tid] : 0;
-      x = warp_sum_u64(x);
-      y = warp_sum_u64(y);
-      if (tid == 0) add_pair(vb, vu, item.row, x, y);
-    }
-    __syncthreads();
   }
 }
 
@@ -331,6 +363,90 @@ __global__ void rows_to_ids_kernel(const int32_t* __restrict__ vertex, int64_t n
     ob[vertex[r]] = rb[r];
     ou[vertex[r]] = ru[r];
   }
+}
+
+__global__ void row_of_id_kernel(const int32_t* __restrict__ vertex, int64_t n, int32_t* __restrict__ row_of) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    row_of[vertex[r]] = (int32_t)r;
+}
+
+// Position in [b, e) of a row whose entry has side rank r, or -1 (rows are
+// sorted by entry, and an entry is (side rank << 1) | negative).
+__device__ __forceinline__ int64_t find_in_row(const uint32_t* col, int64_t b, int64_t e, uint32_t r) {
+  const uint32_t key = r << 1;
+  const int64_t end = e;
+  while (b < e) {
+    const int64_t mid = (b + e) >> 1;
+    if (col[mid] < key) b = mid + 1; else e = mid;
+  }
+  return b < end && (col[b] >> 1) == r ? b : -1;
+}
+
+// Per queried pair (U id, V id): the sum of the counts at the edge's two CSR
+// positions, or zeros when the pair is not an edge; ids out of range set err.
+__global__ void edge_query_kernel(CsrView g, const int32_t* __restrict__ row_of, const int32_t* __restrict__ qu,
+                                  const int32_t* __restrict__ qv, int64_t k, const unsigned long long* eb,
+                                  const unsigned long long* eu, unsigned long long* ob, unsigned long long* ou,
+                                  unsigned* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = qu[i], b = qv[i];
+    unsigned long long xb = 0, xu = 0;
+    if (a < 0 || a >= g.n_u || b < 0 || (int64_t)b >= g.n - g.n_u) {
+      atomicOr(err, 1u);
+    } else {
+      const int64_t ru = row_of[a], rv = row_of[(int64_t)g.n_u + b];
+      const int64_t p1 = find_in_row(g.col, g.row_ptr[ru], g.row_ptr[ru + 1], (uint32_t)(rv - g.n_u));
+      const int64_t p2 = find_in_row(g.col, g.row_ptr[rv], g.row_ptr[rv + 1], (uint32_t)ru);
+      if (p1 >= 0 && p2 >= 0) {
+        xb = eb[p1] + eb[p2];
+        xu = eu[p1] + eu[p2];
+      }
+    }
+    ob[i] = xb;
+    ou[i] = xu;
+  }
+}
+
+template <bool VERT, bool EDGE>
+void enqueue_tips(const dbbc_graph* g, cudaStream_t s, const TipOut& o, unsigned* d_status, Scratch& sc) {
+  if (g->n_piv == 0) return;
+  const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
+  const int sms = num_sms();
+  if (g->n_light > 0) {
+    auto fn = tips_light_kernel<VERT, EDGE>;
+    const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
+    DBBC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
+    const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)fn, kLightWarps * 32, smem);
+    fn<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
+        view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, o, d_status);
+    DBBC_LAUNCH_CHECK();
+  }
+  if (g->n_medium > 0) {
+    auto fn = tips_medium_kernel<VERT, EDGE>;
+    const size_t smem = (size_t)kMediumSlots * 12;
+    DBBC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)fn, kMediumThreads, smem);
+    fn<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
+        view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, o, d_status);
+    DBBC_LAUNCH_CHECK();
+  }
+  if (g->n_hub > 0) {
+    auto fn = tips_sweep_kernel<VERT, EDGE>;
+    const size_t smem = (size_t)kSweepWindow16 * 4;
+    DBBC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = sms * blocks_per_sm((const void*)fn, kSweepThreads, smem);
+    int64_t* cursors = sc.get<int64_t>((size_t)grid * (size_t)g->sweep_max_lower * 3);
+    int* next = sc.get<int>(1);
+    DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
+    fn<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, next, cursors, g->sweep_max_lower,
+                                         o);
+    DBBC_LAUNCH_CHECK();
+  }
+}
+
+inline unsigned grid_1d(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
 }
 
 }  // namespace dbbc
@@ -349,42 +465,13 @@ extern "C" dbbc_status dbbc_count_vertices(const dbbc_graph* g, void* cuda_strea
     unsigned* d_status = sc.get<unsigned>(1);
     DBBC_CUDA(cudaMemsetAsync(rows, 0, (size_t)(2 * n) * 8, s));
     DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
-    unsigned long long* vb = rows;
-    unsigned long long* vu = rows + n;
-    const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
-    const int sms = num_sms();
-    if (g->n_light > 0) {
-      const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
-      DBBC_CUDA(cudaFuncSetAttribute(vertex_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
-      const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)vertex_light_kernel, kLightWarps * 32, smem);
-      vertex_light_kernel<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
-          view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, vb, vu, d_status);
-      DBBC_LAUNCH_CHECK();
-    }
-    if (g->n_medium > 0) {
-      const size_t smem = (size_t)kMediumSlots * 12;
-      DBBC_CUDA(cudaFuncSetAttribute(vertex_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)vertex_medium_kernel, kMediumThreads, smem);
-      vertex_medium_kernel<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
-          view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, vb, vu, d_status);
-      DBBC_LAUNCH_CHECK();
-    }
-    if (g->n_hub > 0) {
-      const size_t smem = (size_t)kSweepWindow16 * 4;
-      DBBC_CUDA(cudaFuncSetAttribute(vertex_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      const int grid = sms * blocks_per_sm((const void*)vertex_sweep_kernel, kSweepThreads, smem);
-      int64_t* cursors = sc.get<int64_t>((size_t)grid * (size_t)g->sweep_max_lower * 3);
-      int* next = sc.get<int>(1);
-      DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
-      vertex_sweep_kernel<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, next, cursors,
-                                                            g->sweep_max_lower, vb, vu);
-      DBBC_LAUNCH_CHECK();
-    }
+    TipOut o;
+    o.vb = rows;
+    o.vu = rows + n;
+    enqueue_tips<true, false>(g, s, o, d_status, sc);
     unsigned long long* ob = rows + 2 * n;
     unsigned long long* ou = rows + 3 * n;
-    rows_to_ids_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(g->vertex, n, vb, vu, ob,
-                                                                                          ou);
+    rows_to_ids_kernel<<<grid_1d(n), 256, 0, s>>>(g->vertex, n, o.vb, o.vu, ob, ou);
     DBBC_LAUNCH_CHECK();
     DBBC_CUDA(cudaMemcpyAsync(balanced_v, ob, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
     DBBC_CUDA(cudaMemcpyAsync(unbalanced_v, ou, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -392,6 +479,61 @@ extern "C" dbbc_status dbbc_count_vertices(const dbbc_graph* g, void* cuda_strea
     DBBC_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
     DBBC_CUDA(cudaStreamSynchronize(s));
     if (h) return DBBC_EINTERNAL;
+  } catch (const Error& e) {
+    return e.status;
+  } catch (...) {
+    return DBBC_EINTERNAL;
+  }
+  return DBBC_OK;
+}
+
+extern "C" dbbc_status dbbc_count_edges(const dbbc_graph* g, void* cuda_stream, const int32_t* qu, const int32_t* qv,
+                                        int64_t k, uint32_t flags, uint64_t* balanced_e, uint64_t* unbalanced_e) {
+  if (!g || k < 0 || (flags & ~(uint32_t)DBBC_INPUT_DEVICE) != 0) return DBBC_EINVAL;
+  if (k == 0) return DBBC_OK;
+  if (!qu || !qv || !balanced_e || !unbalanced_e) return DBBC_EINVAL;
+  if (g->n_u == 0 || g->n == g->n_u) return DBBC_EINVAL;  // no pair is in range
+  const bool on_device = (flags & DBBC_INPUT_DEVICE) != 0;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  try {
+    Scratch sc(s);
+    const int64_t n = g->n, nnz = g->nnz;
+    unsigned long long* acc = sc.get<unsigned long long>((size_t)(2 * nnz));
+    unsigned* d_status = sc.get<unsigned>(2);  // [0] device checks, [1] ids out of range
+    int32_t* row_of = sc.get<int32_t>((size_t)n);
+    DBBC_CUDA(cudaMemsetAsync(acc, 0, (size_t)(2 * nnz) * 8, s));
+    DBBC_CUDA(cudaMemsetAsync(d_status, 0, 2 * sizeof(unsigned), s));
+    TipOut o;
+    o.eb = acc;
+    o.eu = acc + nnz;
+    enqueue_tips<false, true>(g, s, o, d_status, sc);
+    row_of_id_kernel<<<grid_1d(n), 256, 0, s>>>(g->vertex, n, row_of);
+    DBBC_LAUNCH_CHECK();
+    const int32_t* dqu = qu;
+    const int32_t* dqv = qv;
+    unsigned long long* ob = reinterpret_cast<unsigned long long*>(balanced_e);
+    unsigned long long* ou = reinterpret_cast<unsigned long long*>(unbalanced_e);
+    if (!on_device) {
+      int32_t* q = sc.get<int32_t>((size_t)(2 * k));
+      DBBC_CUDA(cudaMemcpyAsync(q, qu, (size_t)k * 4, cudaMemcpyHostToDevice, s));
+      DBBC_CUDA(cudaMemcpyAsync(q + k, qv, (size_t)k * 4, cudaMemcpyHostToDevice, s));
+      dqu = q;
+      dqv = q + k;
+      ob = sc.get<unsigned long long>((size_t)(2 * k));
+      ou = ob + k;
+    }
+    const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
+    edge_query_kernel<<<grid_1d(k), 256, 0, s>>>(view, row_of, dqu, dqv, k, o.eb, o.eu, ob, ou, d_status + 1);
+    DBBC_LAUNCH_CHECK();
+    if (!on_device) {
+      DBBC_CUDA(cudaMemcpyAsync(balanced_e, ob, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+      DBBC_CUDA(cudaMemcpyAsync(unbalanced_e, ou, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+    }
+    unsigned h[2] = {0, 0};
+    DBBC_CUDA(cudaMemcpyAsync(h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    DBBC_CUDA(cudaStreamSynchronize(s));
+    if (h[1]) return DBBC_EINVAL;
+    if (h[0]) return DBBC_EINTERNAL;
   } catch (const Error& e) {
     return e.status;
   } catch (...) {

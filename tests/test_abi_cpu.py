@@ -61,6 +61,8 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.dbbc_graph_from_coo(None, None, None, 1 << 31, 2, 2, 0, None, ctypes.byref(h)) == dbbc.DBBC_EINVAL
     assert L.dbbc_count(None, None, None, None) == dbbc.DBBC_EINVAL
     assert L.dbbc_count_async(None, None, None) == dbbc.DBBC_EINVAL
+    assert L.dbbc_count_vertices(None, None, None, None) == dbbc.DBBC_EINVAL
+    assert L.dbbc_count_edges(None, None, None, None, 0, 0, None, None) == dbbc.DBBC_EINVAL
     assert L.dbbc_count_batch(None, -1, None, None, None) == dbbc.DBBC_EINVAL
     assert L.dbbc_graph_get_info(None, None) == dbbc.DBBC_EINVAL
     assert L.dbbc_graph_export(None, None, None, None, None, None, None) == dbbc.DBBC_EINVAL

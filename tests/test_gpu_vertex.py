@@ -210,3 +210,133 @@ def test_chunglu_full_size_sums_match_stored_totals():
     assert int(vu.sum(dtype=np.uint64)) == 4 * exp[1]
     vb2, vu2, _, _ = gpu_vertices(g.u, g.v, g.s, g.n_u, g.n_v)
     assert np.array_equal(vb, vb2) and np.array_equal(vu, vu2)
+
+
+# ------------------------------------------------------------- per-edge counts
+def gpu_edges(u, v, s, n_u, n_v, qu=None, qv=None, device=False):
+    if qu is None:
+        qu, qv = u, v
+    with dbbc.dbbc_graph_from_coo(u, v, s, n_u, n_v) as g:
+        if device:
+            import torch
+            eb, eu = dbbc.dbbc_count_edges(g, torch.as_tensor(np.asarray(qu, np.int32)).cuda(),
+                                           torch.as_tensor(np.asarray(qv, np.int32)).cuda())
+            eb, eu = eb.cpu().numpy(), eu.cpu().numpy()
+        else:
+            eb, eu = dbbc.dbbc_count_edges(g, qu, qv)
+        tot = dbbc.dbbc_count(g)
+    return eb, eu, tot
+
+
+def assert_edge_parity(u, v, s, n_u, n_v, brute=False, device=False):
+    fn = oracle.brute_force_per_edge if brute else oracle.count_per_edge
+    # every distinct input pair once, in a shuffled order, plus some non-edges
+    rng = np.random.default_rng(len(u))
+    pairs = np.unique(np.asarray(u, np.int64) * n_v + np.asarray(v, np.int64))
+    rng.shuffle(pairs)
+    extra = rng.integers(0, n_u * n_v, size=min(64, n_u * n_v)) if n_u * n_v else np.zeros(0, np.int64)
+    q = np.concatenate([pairs, extra])
+    qu, qv = (q // n_v).astype(np.int32), (q % n_v).astype(np.int32)
+    want_b, want_u = fn(u, v, s, n_u, n_v, qu, qv)
+    eb, eu, tot = gpu_edges(u, v, s, n_u, n_v, qu, qv, device=device)
+    bad = np.flatnonzero((eb != want_b) | (eu != want_u))
+    assert bad.size == 0, f"{bad.size} edges differ, first {bad[:5]}: GPU {eb[bad[:5]]}/{eu[bad[:5]]} " \
+                          f"oracle {want_b[bad[:5]]}/{want_u[bad[:5]]}"
+    k = pairs.shape[0]
+    assert int(eb[:k].sum(dtype=np.uint64)) == 4 * tot[0] and int(eu[:k].sum(dtype=np.uint64)) == 4 * tot[1]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_edges_random_small_vs_brute_force(seed):
+    rng = np.random.default_rng(400 + seed)
+    n_u, n_v = int(rng.integers(2, 40)), int(rng.integers(2, 40))
+    u, v, s = _rand(rng, n_u, n_v, int(rng.integers(1, n_u * n_v + 1)), p_plus=rng.random())
+    assert_edge_parity(u, v, s, n_u, n_v, brute=True)
+
+
+def test_edges_complete_bipartite_closed_form():
+    a, b = 300, 200
+    rng = np.random.default_rng(9)
+    cu, cv = rng.choice([-1, 1], size=a), rng.choice([-1, 1], size=b)
+    u, v, s = _kab(a, b, lambda x, y: cu[x] * cv[y])
+    eb, eu, _ = gpu_edges(u, v, s, a, b)
+    assert eb.tolist() == [(a - 1) * (b - 1)] * (a * b) and not eu.any()
+
+
+def test_edges_repeated_pairs_and_non_edges():
+    u, v, s = [0, 0, 0, 1, 1], [0, 0, 1, 0, 1], [-1, 1, 1, 1, 1]
+    eb, eu, _ = gpu_edges(u, v, s, 3, 3, qu=[0, 0, 0, 1, 1, 2, 2, 0], qv=[0, 0, 1, 0, 1, 2, 0, 2])
+    assert eb.tolist() == [1, 1, 1, 1, 1, 0, 0, 0] and not eu.any()
+
+
+def test_edges_out_of_range_is_einval():
+    with dbbc.dbbc_graph_from_coo([0, 1], [0, 1], [1, 1], 2, 2) as g:
+        for qu, qv in (([2], [0]), ([0], [2]), ([-1], [0])):
+            with pytest.raises(dbbc.DbbcError):
+                dbbc.dbbc_count_edges(g, qu, qv)
+        eb, eu = dbbc.dbbc_count_edges(g, [], [])
+        assert eb.shape == (0,)
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_edges_uniform_2k_3k_20k(device):
+    g = synth.workload("uniform-2k-3k-20k")
+    assert_edge_parity(g.u, g.v, g.s, g.n_u, g.n_v, device=device)
+
+
+def test_edges_spanning_tiers():
+    rng = np.random.default_rng(5)
+    a, b = 260, 180
+    u, v, s = _kab(a, b, lambda x, y: rng.choice([-1, 1], size=x.shape))
+    assert_edge_parity(u, v, s, a, b)
+
+
+@pytest.mark.parametrize("scale", [0.002, 0.01])
+def test_edges_chunglu_scaled(scale):
+    g = synth.workload("chunglu-1m-200k-20m", scale=scale)
+    assert_edge_parity(g.u, g.v, g.s, g.n_u, g.n_v)
+
+
+def test_edges_polarized_scaled():
+    g = synth.workload("polarized-20m-2m-300m", scale=0.0005)
+    assert_edge_parity(g.u, g.v, g.s, g.n_u, g.n_v)
+
+
+def test_edges_dense_and_wide_hubs():
+    rng = np.random.default_rng(77)
+    n_u, n_v = 3001, 1777
+    hubs = rng.choice(n_u, 7, replace=False)
+    bu, bv, _ = _rand(rng, n_u, n_v, 30_000)
+    u = np.concatenate([np.repeat(hubs, n_v), bu]).astype(np.int32)
+    v = np.concatenate([np.tile(np.arange(n_v), hubs.shape[0]), bv]).astype(np.int32)
+    s = np.where(rng.random(u.shape[0]) < 0.6, 1, -1).astype(np.int8)
+    assert_edge_parity(u, v, s, n_u, n_v)
+    n_u, n_v = 101, 70_000
+    other = rng.integers(1, n_u, size=n_v)
+    u = np.concatenate([np.zeros(n_v, np.int64), other]).astype(np.int32)
+    v = np.concatenate([np.arange(n_v), np.arange(n_v)]).astype(np.int32)
+    s = np.where(rng.random(u.shape[0]) < 0.5, 1, -1).astype(np.int8)
+    assert_edge_parity(u, v, s, n_u, n_v)
+
+
+def test_edges_do_not_depend_on_tuning():
+    base = dbbc.dbbc_get_tuning()
+    g = synth.workload("chunglu-1m-200k-20m", scale=0.005)
+    want_b, want_u = oracle.count_per_edge(g.u, g.v, g.s, g.n_u, g.n_v)
+    try:
+        dbbc.dbbc_set_tuning(dict(light_max_work=1, medium_max_work=1, hub_item_work=1024,
+                                  group_density=[40.0, 16.0, 6.0, 2.0], hash_mult_log=1))
+        eb, eu, _ = gpu_edges(g.u, g.v, g.s, g.n_u, g.n_v)
+    finally:
+        dbbc.dbbc_set_tuning(base)
+    assert np.array_equal(eb, want_b) and np.array_equal(eu, want_u)
+
+
+def test_edges_chunglu_full_size_sums():
+    g = synth.workload("chunglu-1m-200k-20m")
+    exp = read_golden("expected_counts.txt")["chunglu-1m-200k-20m"][0]
+    pairs = np.unique(g.u.astype(np.int64) * g.n_v + g.v)
+    eb, eu, tot = gpu_edges(g.u, g.v, g.s, g.n_u, g.n_v, (pairs // g.n_v).astype(np.int32),
+                            (pairs % g.n_v).astype(np.int32))
+    assert tot == (exp[0], exp[1])
+    assert int(eb.sum(dtype=np.uint64)) == 4 * exp[0] and int(eu.sum(dtype=np.uint64)) == 4 * exp[1]
