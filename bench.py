@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dbbc", "reference"], default="dbbc")
-    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS) + ["batch-4096", "serve", "sign-sweep"])
+    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS) + ["batch-4096", "serve", "sign-sweep", "tips"])
     ap.add_argument("--n-graphs", type=int, default=4096, help="graphs in the batch-4096 workload")
     ap.add_argument("--requests", type=int, default=4000, help="requests of the served workload")
     ap.add_argument("--large-pool", type=int, default=4, help="distinct large graphs cycled by the served stream")
@@ -519,6 +519,73 @@ def run_sign_sweep(a, torch, dbbc, world, rank, local, dist, barrier):
         print(json.dumps(line), flush=True)
 
 
+def run_tips(a, torch, dbbc, world, rank, local, dist, barrier):
+    """Per-vertex ("tip") and per-edge ("wing") butterfly counts of the
+    Chung-Lu 1M x 200k x 20M graph, built once: one step is one
+    dbbc_count_vertices call (host output arrays) and one dbbc_count_edges
+    call over every distinct edge (device queries and outputs). Both walk every
+    accepted wedge twice (count, then credit)."""
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    g = synth.workload("chunglu-1m-200k-20m")
+    pairs = np.unique(g.u.astype(np.int64) * g.n_v + g.v)
+    qu = torch.from_numpy((pairs // g.n_v).astype(np.int32)).to(dev)
+    qv = torch.from_numpy((pairs % g.n_v).astype(np.int32)).to(dev)
+    du, dv, ds = (torch.from_numpy(x).to(dev) for x in (g.u, g.v, g.s))
+    want = expected_counts("chunglu-1m-200k-20m")
+    h = dbbc.dbbc_graph_from_coo(du, dv, ds, g.n_u, g.n_v, stream=stream)
+    wedges = h.info["wedges"]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tv, te = [], []
+    launches0 = 0
+    sampler = ClockSampler(local)
+    for k in range(a.warmup + a.steps):
+        if k == a.warmup:
+            barrier()
+            torch.cuda.synchronize(dev)
+            sampler.start()
+            time.sleep(0.3)
+            launches0 = dbbc.dbbc_kernel_launches()
+        ev[0].record(stream)
+        vb, vu = dbbc.dbbc_count_vertices(h, stream)
+        ev[1].record(stream)
+        eb, eu = dbbc.dbbc_count_edges(h, qu, qv, stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        if k >= a.warmup:
+            tv.append(ev[0].elapsed_time(ev[1]))
+            te.append(ev[1].elapsed_time(ev[2]))
+    launches = dbbc.dbbc_kernel_launches() - launches0
+    clocks = sampler.stop()
+    sums = (int(vb.sum(dtype=np.uint64)), int(vu.sum(dtype=np.uint64)), int(eb.sum().item()), int(eu.sum().item()))
+    h.free()
+    verified = None if want is None else sums == (4 * want[0], 4 * want[1], 4 * want[0], 4 * want[1])
+    ms_v, ms_e = sum(tv) / len(tv), sum(te) / len(te)
+    line = {"metric": METRIC, "value": world * wedges / (ms_v / 1e3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_v + ms_e, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "tips", "graph": "chunglu-1m-200k-20m", "wedges": wedges,
+                       "edge_queries": int(pairs.shape[0]), "tuning": dbbc.dbbc_get_tuning(),
+                       "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB)" % ((2 * g.m * 4 + (g.n_u + g.n_v) * 8) / 1e6)},
+            "per_vertex": {"ms": ms_v, "gwedges_per_s": wedges / (ms_v / 1e3) / 1e9,
+                           "output": "host arrays, 2 x 8 B per vertex"},
+            "per_edge": {"ms": ms_e, "gwedges_per_s": wedges / (ms_e / 1e3) / 1e9,
+                         "output": "device arrays, 2 x 8 B per queried edge"},
+            "verified": verified, "e2e": None, "roofline": None, "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        gs = synth.workload("chunglu-1m-200k-20m", scale=0.05)
+        w = oracle.count(gs.u, gs.v, gs.s, gs.n_u, gs.n_v, threads=1)[2]
+        t0 = time.perf_counter()
+        oracle.count_per_vertex(gs.u, gs.v, gs.s, gs.n_u, gs.n_v)
+        t = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": w / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"oracle per-vertex counts of the 5% Chung-Lu graph ({w} wedges, {t:.1f} s, "
+                                          "1 thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -534,8 +601,8 @@ def main():
     # the autotuner's record for this workload on this GPU, if there is one
     from paper_2609_21848_gb300 import autotune
     dbbc.lib()
-    tuned = autotune.apply_saved({"serve": "batch-4096", "sign-sweep": "chunglu-1m-200k-20m"}.get(a.workload,
-                                                                                                  a.workload))
+    tuned = autotune.apply_saved({"serve": "batch-4096", "sign-sweep": "chunglu-1m-200k-20m",
+                                  "tips": "chunglu-1m-200k-20m"}.get(a.workload, a.workload))
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -545,8 +612,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    if a.workload in ("batch-4096", "serve", "sign-sweep"):
-        fn = {"batch-4096": run_batch, "serve": run_serve, "sign-sweep": run_sign_sweep}[a.workload]
+    if a.workload in ("batch-4096", "serve", "sign-sweep", "tips"):
+        fn = {"batch-4096": run_batch, "serve": run_serve, "sign-sweep": run_sign_sweep, "tips": run_tips}[a.workload]
         fn(a, torch, dbbc, world, rank, local, dist, barrier)
         if dist is not None:
             dist.destroy_process_group()
