@@ -145,11 +145,12 @@ DBBC_API dbbc_status dbbc_count_async(const dbbc_graph* g, void* cuda_stream, ui
 
 /* Per-tier timings of one count, measured with CUDA events on the call's
  * stream around the tier's kernels (milliseconds), with launch counts and the
- * number of endpoints the hub tier touched (each read and reset once). */
+ * number of (lower neighbour, window) visits the hub sweep made in list mode
+ * (the visits of the other hub items are dbbc_graph_info.hub_cursor_steps). */
 typedef struct {
   float ms_light, ms_medium, ms_hub_aggregate, ms_hub_finalize, ms_total;
   int64_t launches_light, launches_medium, launches_hub_aggregate, launches_hub_finalize;
-  uint64_t hub_touched;
+  uint64_t hub_list_visits;
 } dbbc_count_profile;
 
 /* dbbc_count plus per-tier timings in *prof (may be NULL). Synchronous. */
@@ -218,7 +219,9 @@ typedef struct {
   int64_t lower_light, lower_medium, lower_hub; /* lower neighbours summed over the tier's pivots */
   int64_t hub_items;         /* hub work items (a hub and a span of its endpoint windows) */
   int64_t hub_cursor_inits;  /* sum over hub items of the hub's lower neighbours */
-  int64_t hub_cursor_steps;  /* sum over hub items of lower neighbours x windows */
+  int64_t hub_cursor_steps;  /* sum over hub items swept by cursors of lower neighbours x windows (list-mode
+                                items visit only the windows that hold a neighbour's entries; see
+                                dbbc_count_profile.hub_list_visits) */
   size_t device_bytes; /* device memory held by the handle */
   int32_t n_components; /* graphs in a dbbc_graph_from_coo_multi handle, else 1 */
 } dbbc_graph_info;
@@ -282,13 +285,20 @@ DBBC_API dbbc_status dbbc_count_partition(const dbbc_graph* g, void* cuda_stream
  *                     32, 16, 8 and 4 lanes walk a segment (descending);
  *   hash_mult_log   : shared hash tables get at least 2^hash_mult_log slots
  *                     per accepted wedge of the pivot (1..3; capped by the
- *                     tier's table size, never below 2 per wedge). */
+ *                     tier's table size, never below 2 per wedge);
+ *   list_density    : hubs whose mean (lower neighbour, window) segment is
+ *                     shorter than this (>= 0; 0 turns it off) sweep in list
+ *                     mode, visiting a neighbour only in the windows that
+ *                     hold its entries;
+ *   list_group_log  : lanes per neighbour segment in list mode, log2 (0..5). */
 typedef struct {
   uint64_t light_max_work;
   uint64_t medium_max_work;
   uint64_t hub_item_work;
   double group_density[4];
   int32_t hash_mult_log;
+  double list_density;
+  int32_t list_group_log;
 } dbbc_tuning;
 DBBC_API dbbc_status dbbc_set_tuning(const dbbc_tuning* t); /* NULL restores the defaults; DBBC_EINVAL if out of range */
 DBBC_API void dbbc_get_tuning(dbbc_tuning* t);

@@ -26,7 +26,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 TUNING_DIR = os.path.join(HERE, "tuning")
 
 DEFAULT = {"light_max_work": 512, "medium_max_work": 4096, "hub_item_work": 1 << 20,
-           "group_density": [40.0, 16.0, 6.0, 2.0], "hash_mult_log": 1}
+           "group_density": [40.0, 16.0, 6.0, 2.0], "hash_mult_log": 1, "list_density": 8.0, "list_group_log": 2}
 
 SPACE = [
     ("light_max_work", [128, 256, 512]),
@@ -34,6 +34,8 @@ SPACE = [
     ("hash_mult_log", [1, 2]),
     ("hub_item_work", [1 << 19, 1 << 20, 1 << 21, 1 << 22]),
     ("group_density", [[40.0, 16.0, 6.0, 2.0], [64.0, 24.0, 8.0, 3.0], [24.0, 10.0, 4.0, 1.5]]),
+    ("list_density", [0.0, 4.0, 8.0, 16.0, 32.0]),
+    ("list_group_log", [2, 3, 4, 5]),
 ]
 
 

@@ -93,7 +93,8 @@ dbbc_status dbbc_set_tuning(const dbbc_tuning* t) {
   }
   if (t->light_max_work < 1 || t->light_max_work > kLightMaxWork || t->medium_max_work < t->light_max_work ||
       t->medium_max_work > kMediumMaxWork || t->hub_item_work < 1024 || t->hash_mult_log < 1 ||
-      t->hash_mult_log > 3)
+      t->hash_mult_log > 3 || !(t->list_density >= 0) || t->list_group_log < 0 || t->list_group_log > 5 ||
+      t->list_group_log == 1)
     return DBBC_EINVAL;
   for (int i = 0; i < 4; i++)
     if (!(t->group_density[i] >= 0) || (i > 0 && t->group_density[i] > t->group_density[i - 1])) return DBBC_EINVAL;
@@ -103,6 +104,8 @@ dbbc_status dbbc_set_tuning(const dbbc_tuning* t) {
   n.hub_item_work = t->hub_item_work;
   for (int i = 0; i < 4; i++) n.group_density[i] = t->group_density[i];
   n.hash_mult_log = t->hash_mult_log;
+  n.list_density = t->list_density;
+  n.list_group_log = t->list_group_log;
   g_tuning = n;
   return DBBC_OK;
 }
@@ -114,6 +117,8 @@ void dbbc_get_tuning(dbbc_tuning* t) {
   t->hub_item_work = g_tuning.hub_item_work;
   for (int i = 0; i < 4; i++) t->group_density[i] = g_tuning.group_density[i];
   t->hash_mult_log = g_tuning.hash_mult_log;
+  t->list_density = g_tuning.list_density;
+  t->list_group_log = g_tuning.list_group_log;
 }
 
 void dbbc_set_allocator(void* (*alloc_fn)(size_t, void*, void*), void (*free_fn)(void*, void*, void*), void* ctx) {

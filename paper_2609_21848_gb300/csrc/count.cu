@@ -104,29 +104,43 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
 }
 
 // ------------------------------------------------------------------ hub tier
+// Items are pulled dynamically in descending estimated work (LPT). An item in
+// list mode (count_device.cuh) uses per-window neighbour lists in `lists`
+// (list_cap slots per CTA); with no room for them (list_cap too small) it is
+// swept by cursors like every other item, which gives the same counts.
 __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
                                                                       int64_t n_items, int* next_item,
                                                                       int64_t* __restrict__ cursors, int64_t cur_cap,
-                                                                      unsigned long long* out) {
+                                                                      uint32_t* __restrict__ lists, int64_t list_cap,
+                                                                      unsigned long long* out,
+                                                                      unsigned long long* visits) {
   extern __shared__ __align__(16) unsigned char sweep_smem[];
   uint32_t* c16 = reinterpret_cast<uint32_t*>(sweep_smem);
   unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
   __shared__ int item_sh;
+  __shared__ int cnt[kListMaxWindows];
   const int tid = threadIdx.x;
   for (int i = tid; i < (int)kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
   int64_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
-  uint64_t bal = 0, unb = 0;
+  uint32_t* my_lists = lists ? lists + (int64_t)blockIdx.x * list_cap : nullptr;
+  uint64_t bal = 0, unb = 0, n_visits = 0;
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
+    if (tid < kListMaxWindows) cnt[tid] = 0;
     __syncthreads();  // also orders the zeroing above / below before reuse
     const int64_t it = item_sh;
     __syncthreads();
     if (it >= n_items) break;
     const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    const bool wide = item.wide != 0;
+    const bool wide = (item.flags & kItemWide) != 0;
     const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
-    // cursors: first entry at or after rank item.lo, and the row end
+    const uint32_t R = (item.hi - item.lo + H - 1) / H;
+    const bool listed = (item.flags & kItemList) != 0 && my_lists != nullptr && R <= (uint32_t)kListMaxWindows &&
+                        (int64_t)R * q.L <= list_cap;
+    const ListItem li{my_lists, cnt, q.L, item.lo, H, item.hi << 1};
+    // cursors: first entry at or after rank item.lo, and the row end; in list
+    // mode the neighbour also joins the list of the window of that entry
     const uint32_t first = item.lo << 1;
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       const uint32_t e = g.col[q.rb + i];
@@ -143,19 +157,30 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
       }
       cur[2 * i] = b;
       cur[2 * i + 1] = en;
+      if (listed && b < en) list_append(li, g.col[b], i);
     }
     __syncthreads();
-    for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
+    for (uint32_t r = 0; r < R; r++) {
+      const uint32_t lo = item.lo + r * H;
       const uint32_t hi = min(lo + H, item.hi);
-      if (wide) sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      else sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      __syncthreads();
+      if (listed) {
+        const uint32_t n = (uint32_t)cnt[r];
+        const uint32_t* list = my_lists + (size_t)r * q.L;
+        if (wide) list_window_dispatch<false>(item.group_log, g, q, cur, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+        else list_window_dispatch<true>(item.group_log, g, q, cur, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+        n_visits += tid == 0 ? n : 0;
+      } else {
+        if (wide) sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+        else sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      }
+      __syncthreads();  // also publishes the appends made to later windows' lists
       const uint32_t words = wide ? 2 * (hi - lo) : (hi - lo);  // 32-bit words to clear
       for (uint32_t j = tid; j < words; j += kSweepThreads) c16[j] = 0u;
       __syncthreads();
     }
   }
   block_add_pair<kSweepThreads>(bal, unb, out);
+  if (visits && tid == 0 && n_visits) atomicAdd(visits, (unsigned long long)n_visits);
 }
 
 // ------------------------------------------------------------------ host
@@ -180,8 +205,7 @@ void CountProfiler::summarize(dbbc_count_profile* out) {
     DBBC_CUDA(cudaEventElapsedTime(&t, mk.a, mk.b));
     ms[mk.tier] += t;
   }
-  uint64_t touched = 0;
-  for (uint32_t x : hub_touched) touched += x;
+  if (d_visits) DBBC_CUDA(cudaMemcpy(&list_visits, d_visits, sizeof(list_visits), cudaMemcpyDeviceToHost));
   out->ms_light = ms[LIGHT];
   out->ms_medium = ms[MEDIUM];
   out->ms_hub_aggregate = ms[HUB_AGG];
@@ -191,7 +215,7 @@ void CountProfiler::summarize(dbbc_count_profile* out) {
   out->launches_medium = launches[MEDIUM];
   out->launches_hub_aggregate = launches[HUB_AGG];
   out->launches_hub_finalize = launches[HUB_FIN];
-  out->hub_touched = touched;
+  out->hub_list_visits = list_visits;
 }
 
 CountProfiler::~CountProfiler() {
@@ -241,11 +265,17 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
     DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = sms * blocks_per_sm((const void*)hub_sweep_kernel, kSweepThreads, smem);
     int64_t* cursors = sc.get<int64_t>((size_t)grid * (size_t)g->sweep_max_lower * 2);
+    uint32_t* lists = g->sweep_list_cap > 0 ? sc.get<uint32_t>((size_t)grid * (size_t)g->sweep_list_cap) : nullptr;
     int* next = sc.get<int>(1);
     DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
-    if (prof) t0 = prof->begin(s);
+    if (prof) {
+      prof->d_visits = sc.get<unsigned long long>(1);
+      DBBC_CUDA(cudaMemsetAsync(prof->d_visits, 0, sizeof(unsigned long long), s));
+      t0 = prof->begin(s);
+    }
     hub_sweep_kernel<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, next, cursors,
-                                                       g->sweep_max_lower, d_out);
+                                                       g->sweep_max_lower, lists, g->sweep_list_cap, d_out,
+                                                       prof ? prof->d_visits : nullptr);
     DBBC_LAUNCH_CHECK();
     if (prof) {
       prof->end(CountProfiler::HUB_AGG, t0, s);
@@ -301,7 +331,7 @@ void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t s, unsigned long l
     const int grid = (int)std::min<int64_t>(full, hub_grid);
     DBBC_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
     hub_sweep_kernel<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, d_next, cursors,
-                                                       g->sweep_max_lower, d_out);
+                                                       g->sweep_max_lower, nullptr, 0, d_out, nullptr);
     DBBC_LAUNCH_CHECK();
   }
 }

@@ -221,6 +221,115 @@ __device__ __forceinline__ void sweep_window_dispatch(int group_log, const CsrVi
   }
 }
 
+// ------------------------------------------------------------------ hub tier, list mode
+// In a sparse hub most (lower neighbour, window) pairs are empty: the
+// neighbour's row has no entry in that window, yet the cursor sweep above
+// still reads its cursor there. In list mode a neighbour is visited only in the
+// windows that hold its entries. Window r of an item keeps a list (global
+// memory, L slots per window) of the neighbours whose next entry falls in it;
+// after walking its entries in window r, a neighbour is appended to the list of
+// the window of its next entry (always a later window), or drops out at the end
+// of its row or of the item. Each neighbour is in at most one list at a time
+// and in each list at most once, so L slots per window never overflow.
+struct ListItem {
+  uint32_t* lists;   // [windows][L] neighbour indices
+  int* cnt;          // [windows] list lengths (shared memory)
+  uint32_t L;
+  uint32_t lo;       // first rank of the item
+  uint32_t H;        // ranks per window
+  uint32_t hl;       // (last rank of the item + 1) << 1
+};
+
+__device__ __forceinline__ void list_append(const ListItem& li, uint32_t x, uint32_t i) {
+  if (x < li.hl) {
+    const uint32_t r = ((x >> 1) - li.lo) / li.H;
+    const int pos = atomicAdd(&li.cnt[r], 1);
+    li.lists[(size_t)r * li.L + (uint32_t)pos] = i;
+  }
+}
+
+// One window of a list-mode item: groups of G lanes take the listed
+// neighbours j = gid, gid + groups, ... of `list` (n of them), walk each from
+// its cursor like sweep_window, then requeue it by its first entry past the
+// window.
+template <int G, bool PACK16>
+__device__ __forceinline__ void list_window(const CsrView& g, const PivotGeom& q, int64_t* cur, const ListItem& li,
+                                            const uint32_t* list, uint32_t n, uint32_t lo, uint32_t hl,
+                                            uint32_t* c16, unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
+  const int tid = threadIdx.x;
+  const int gl = tid & (G - 1);
+  const uint32_t gid = (uint32_t)tid / G;
+  constexpr uint32_t groups = kSweepThreads / G;
+  const unsigned lane = lane_id();
+  const unsigned gmask = G == 32 ? kFullMask : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+  const uint32_t lo2 = lo << 1;
+  uint32_t i_nx = 0;
+  int64_t c_nx = 0, en_nx = 0;
+  uint32_t s1_nx = 0;
+  if (gid < n) {
+    i_nx = list[gid];
+    c_nx = cur[2 * i_nx];
+    en_nx = cur[2 * i_nx + 1];
+    s1_nx = g.col[q.rb + i_nx] & 1u;
+  }
+  for (uint32_t j = gid; j < n; j += groups) {
+    const uint32_t i = i_nx;
+    int64_t c = c_nx;
+    const int64_t en = en_nx;
+    const uint32_t s1 = s1_nx;
+    if (j + groups < n) {
+      i_nx = list[j + groups];
+      c_nx = cur[2 * i_nx];
+      en_nx = cur[2 * i_nx + 1];
+      s1_nx = g.col[q.rb + i_nx] & 1u;
+    }
+    for (;;) {
+      uint32_t x[kSweepUnroll];
+#pragma unroll
+      for (int u = 0; u < kSweepUnroll; u++) {
+        const int64_t pos = c + u * G + gl;
+        x[u] = pos < en ? g.col[pos] : 0xFFFFFFFFu;
+      }
+      int n_ok = 0;
+#pragma unroll
+      for (int u = 0; u < kSweepUnroll; u++) {
+        const bool ok = x[u] < hl;
+        if (ok) {
+          const bool sym = ((x[u] ^ s1) & 1u) == 0;
+          const uint32_t k = (x[u] - lo2) >> 1;
+          if (PACK16) {
+            sweep_contrib16(atomicAdd(&c16[k], sym ? 1u : 0x10000u), sym, bal, unb);
+          } else {
+            const unsigned long long inc = sym ? 1ull : (1ull << 32);
+            wedge_contrib(atomicAdd(&c32[k], inc), inc, bal, unb);
+          }
+        }
+        n_ok += __popc(__ballot_sync(gmask, ok));  // accepted entries are a prefix
+      }
+      c += n_ok;
+      if (n_ok < G * kSweepUnroll) break;
+    }
+    if (gl == 0) {
+      cur[2 * i] = c;
+      if (c < en) list_append(li, g.col[c], i);
+    }
+  }
+}
+
+template <bool PACK16>
+__device__ __forceinline__ void list_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
+                                                     int64_t* cur, const ListItem& li, const uint32_t* list,
+                                                     uint32_t n, uint32_t lo, uint32_t hl, uint32_t* c16,
+                                                     unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
+  switch (group_log) {
+    case 0: list_window<1, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 2: list_window<4, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 3: list_window<8, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 4: list_window<16, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    default: list_window<32, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
+  }
+}
+
 inline int blocks_per_sm(const void* fn, int threads, size_t smem) {
   int b = 0;
   DBBC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem));

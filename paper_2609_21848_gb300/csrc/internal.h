@@ -46,6 +46,10 @@ constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per wor
 #define DBBC_GROUP_T4 2
 #endif
 constexpr double kGroupThreshold[4] = {DBBC_GROUP_T32, DBBC_GROUP_T16, DBBC_GROUP_T8, DBBC_GROUP_T4};
+// Hub items in list mode (see count_device.cuh): at most this many windows per
+// item, and at most kListCapEntries (window, neighbour) list slots per CTA.
+constexpr int kListMaxWindows = 64;
+constexpr int64_t kListCapEntries = int64_t{1} << 22;
 
 // Runtime tuning (dbbc_set_tuning), snapshotted into every graph at build.
 struct Tuning {
@@ -54,6 +58,8 @@ struct Tuning {
   uint64_t hub_item_work = kSweepItemWork;
   double group_density[4] = {DBBC_GROUP_T32, DBBC_GROUP_T16, DBBC_GROUP_T8, DBBC_GROUP_T4};
   int32_t hash_mult_log = 1;
+  double list_density = 8.0;  // hubs with a mean (neighbour, window) segment shorter than this use list mode
+  int32_t list_group_log = 2; // lanes per neighbour segment in list mode (log2)
 };
 const Tuning& current_tuning();
 
@@ -70,8 +76,10 @@ struct SweepItem {
   uint32_t lo;
   uint32_t hi;
   int16_t group_log;
-  int16_t wide;
+  int16_t flags;  // kItemWide | kItemList
 };
+constexpr int16_t kItemWide = 1;  // 32-bit counter halves (kSweepWindow32 ranks per window)
+constexpr int16_t kItemList = 2;  // list mode: visit a neighbour only in windows holding its entries
 
 // Read-only view of the device CSR passed to kernels by value.
 // Rows [0, n_u) are U vertices in ascending Def. 3 priority, rows [n_u, n)
@@ -118,6 +126,7 @@ struct dbbc_graph {
   std::vector<dbbc::SweepItem> sweep_items_host;  // same items on the host (batch planning)
   std::vector<uint64_t> sweep_est_host;           // their estimated accepted wedges
   int64_t sweep_max_lower = 0;  // largest lower-neighbour count of a hub (cursor scratch per CTA)
+  int64_t sweep_list_cap = 0;   // largest windows x lower neighbours of a list-mode item (list slots per CTA)
   int64_t narrow_ranks_u = 0, narrow_ranks_v = 0;  // per side: vertices of degree < 2^16 (a rank prefix)
   // disjoint union of several graphs (dbbc_graph_from_coo_multi): component
   // of every row, 0 for a plain handle (n_components == 1)
@@ -156,7 +165,8 @@ struct CountProfiler {
     cudaEvent_t a, b;
   };
   std::vector<Mark> marks;
-  std::vector<uint32_t> hub_touched;  // filled asynchronously
+  unsigned long long* d_visits = nullptr;  // device counter of list-mode (neighbour, window) visits
+  uint64_t list_visits = 0;
   int64_t launches[NTIERS] = {0, 0, 0, 0, 0};
   cudaEvent_t begin(cudaStream_t s);
   void end(int tier, cudaEvent_t a, cudaStream_t s);

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kSweepThreads) tips_sweep_kernel(CsrView g, co
     if (it >= n_items) break;
     const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    const bool wide = item.wide != 0;
+    const bool wide = (item.flags & kItemWide) != 0;
     const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
     const uint32_t first = item.lo << 1;
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {

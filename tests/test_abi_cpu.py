@@ -81,15 +81,18 @@ def test_tuning_round_trip_and_validation(lib):
     base = dbbc.dbbc_get_tuning()
     try:
         t = dict(light_max_work=128, medium_max_work=2048, hub_item_work=1 << 19,
-                 group_density=[64.0, 24.0, 8.0, 3.0], hash_mult_log=2)
+                 group_density=[64.0, 24.0, 8.0, 3.0], hash_mult_log=2, list_density=12.0, list_group_log=4)
         dbbc.dbbc_set_tuning(t)
         assert dbbc.dbbc_get_tuning() == t
         for bad in (dict(t, light_max_work=0), dict(t, light_max_work=1024), dict(t, medium_max_work=64),
                     dict(t, medium_max_work=8192), dict(t, hub_item_work=10), dict(t, hash_mult_log=0),
-                    dict(t, hash_mult_log=4), dict(t, group_density=[1.0, 2.0, 3.0, 4.0])):
+                    dict(t, hash_mult_log=4), dict(t, group_density=[1.0, 2.0, 3.0, 4.0]),
+                    dict(t, list_density=-1.0), dict(t, list_group_log=1), dict(t, list_group_log=6)):
             with pytest.raises(dbbc.DbbcError):
                 dbbc.dbbc_set_tuning(bad)
         assert dbbc.dbbc_get_tuning() == t  # rejected settings change nothing
+        dbbc.dbbc_set_tuning({"hash_mult_log": 3})  # keys left out keep their values
+        assert dbbc.dbbc_get_tuning() == dict(t, hash_mult_log=3)
         dbbc.dbbc_set_tuning(None)
         from paper_2609_21848_gb300 import autotune
         assert dbbc.dbbc_get_tuning() == autotune.DEFAULT
