@@ -175,7 +175,7 @@ DBBC_API uint64_t dbbc_kernel_launches(void);
  * share the array and it keeps the previous call's contents (the parts that
  * must start at zero are cleared by each call); calls that overlap on the GPU,
  * on any streams, race on it, so serialize them. Graphs whose largest hub
- * needs more cursor scratch than the array holds (16 bytes per lower
+ * needs more cursor scratch than the array holds (8 bytes per lower
  * neighbour of that hub for even one CTA) are rejected with DBBC_EOVERFLOW;
  * below that limit fewer CTAs run the hub tier when the array cannot hold
  * cursors for all of them. */

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_batch_kernel(cons
 __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const GraphDesc* __restrict__ desc,
                                                                         const BatchHubItem* __restrict__ items,
                                                                         int64_t n_items, int* next_item,
-                                                                        int64_t* __restrict__ cursors, int64_t cur_cap,
+                                                                        uint32_t* __restrict__ cursors, int64_t cur_cap,
                                                                         unsigned long long* out) {
   extern __shared__ __align__(16) unsigned char sweep_smem[];
   uint32_t* c16 = reinterpret_cast<uint32_t*>(sweep_smem);
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
   __shared__ int item_sh;
   const int tid = threadIdx.x;
   for (int i = tid; i < (int)kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
-  int64_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
+  uint32_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
     __syncthreads();
@@ -214,22 +214,9 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     const PivotGeom q = pivot_geom(g, item.row);
     const bool wide = (item.flags & kItemWide) != 0;
     const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
-    const uint32_t first = item.lo << 1;
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
-      const uint32_t e = g.col[q.rb + i];
-      const int64_t vrow = q.base + (e >> 1);
-      int64_t b = g.row_ptr[vrow];
-      const int64_t en = g.row_ptr[vrow + 1];
-      if (first) {
-        int64_t lo = b, hi = en;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (g.col[mid] < first) lo = mid + 1; else hi = mid;
-        }
-        b = lo;
-      }
-      cur[2 * i] = b;
-      cur[2 * i + 1] = en;
+      uint32_t b, en;
+      init_cursor(g, q, i, item.lo, cur, b, en);
     }
     __syncthreads();
     uint64_t bal = 0, unb = 0;
@@ -259,7 +246,7 @@ struct dbbc_batch {
   dbbc::BatchHubItem* hub = nullptr;
   int64_t n_light = 0, n_medium = 0, n_hub_items = 0, max_lower = 1;
   unsigned long long* out = nullptr;  // [n_graphs][2]
-  int64_t* cursors = nullptr;
+  uint32_t* cursors = nullptr;
   int* counters = nullptr;  // [0] light chunks, [1] hub items
   unsigned* status = nullptr;
   int hub_grid = 0, light_grid = 0, medium_grid = 0;
@@ -372,7 +359,7 @@ static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector
   const size_t smem = (size_t)kSweepWindow16 * 4;
   b->hub_grid = num_sms() * blocks_per_sm((const void*)hub_sweep_batch_kernel, kSweepThreads, smem);
   if (b->n_hub_items > 0)
-    b->cursors = static_cast<int64_t*>(batch_alloc(b, (size_t)b->hub_grid * (size_t)b->max_lower * 16));
+    b->cursors = static_cast<uint32_t*>(batch_alloc(b, (size_t)b->hub_grid * (size_t)b->max_lower * 8));
   {
     const int sms = num_sms();
     const int64_t want = ceil_div<int64_t>(ceil_div<int64_t>(b->n_light, 32), kLightWarps);

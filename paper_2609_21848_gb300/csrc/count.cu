@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
 // swept by cursors like every other item, which gives the same counts.
 __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
                                                                       int64_t n_items, int* next_item,
-                                                                      int64_t* __restrict__ cursors, int64_t cur_cap,
+                                                                      uint32_t* __restrict__ cursors, int64_t cur_cap,
                                                                       uint32_t* __restrict__ lists, int64_t list_cap,
                                                                       unsigned long long* out,
                                                                       unsigned long long* visits) {
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
   __shared__ int cnt[kListMaxWindows];
   const int tid = threadIdx.x;
   for (int i = tid; i < (int)kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
-  int64_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
+  uint32_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
   uint32_t* my_lists = lists ? lists + (int64_t)blockIdx.x * list_cap : nullptr;
   uint64_t bal = 0, unb = 0, n_visits = 0;
   for (;;) {
@@ -139,24 +139,11 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     const bool listed = (item.flags & kItemList) != 0 && my_lists != nullptr && R <= (uint32_t)kListMaxWindows &&
                         (int64_t)R * q.L <= list_cap;
     const ListItem li{my_lists, cnt, q.L, item.lo, H, item.hi << 1};
-    // cursors: first entry at or after rank item.lo, and the row end; in list
-    // mode the neighbour also joins the list of the window of that entry
-    const uint32_t first = item.lo << 1;
+    // cursors; in list mode each neighbour also joins the list of the window
+    // of its first entry
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
-      const uint32_t e = g.col[q.rb + i];
-      const int64_t vrow = q.base + (e >> 1);
-      int64_t b = g.row_ptr[vrow];
-      const int64_t en = g.row_ptr[vrow + 1];
-      if (first) {  // lower_bound of `first` in the row
-        int64_t lo = b, hi = en;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (g.col[mid] < first) lo = mid + 1; else hi = mid;
-        }
-        b = lo;
-      }
-      cur[2 * i] = b;
-      cur[2 * i + 1] = en;
+      uint32_t b, en;
+      init_cursor(g, q, i, item.lo, cur, b, en);
       if (listed && b < en) list_append(li, g.col[b], i);
     }
     __syncthreads();
@@ -264,7 +251,7 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
     const size_t smem = (size_t)kSweepWindow16 * 4;
     DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = sms * blocks_per_sm((const void*)hub_sweep_kernel, kSweepThreads, smem);
-    int64_t* cursors = sc.get<int64_t>((size_t)grid * (size_t)g->sweep_max_lower * 2);
+    uint32_t* cursors = sc.get<uint32_t>((size_t)grid * (size_t)g->sweep_max_lower * 2);
     uint32_t* lists = g->sweep_list_cap > 0 ? sc.get<uint32_t>((size_t)grid * (size_t)g->sweep_list_cap) : nullptr;
     int* next = sc.get<int>(1);
     DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
@@ -295,7 +282,7 @@ namespace dbbc {
 // bounds how many CTAs it can run. Throws DBBC_EOVERFLOW when not even one
 // CTA's cursors fit.
 void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_out, unsigned* d_status,
-                            int* d_next, int64_t* cursors, size_t cursor_bytes) {
+                            int* d_next, uint32_t* cursors, size_t cursor_bytes) {
   DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
   DBBC_CUDA(cudaMemsetAsync(d_out, 0, 2 * sizeof(unsigned long long), s));
   if (g->n_piv == 0) return;
@@ -303,7 +290,7 @@ void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t s, unsigned long l
   const int sms = num_sms();
   int64_t hub_grid = 0;
   if (g->n_hub > 0) {
-    const size_t per_cta = (size_t)g->sweep_max_lower * 2 * sizeof(int64_t);
+    const size_t per_cta = (size_t)g->sweep_max_lower * 2 * sizeof(uint32_t);
     hub_grid = (int64_t)(cursor_bytes / per_cta);
     if (hub_grid < 1) throw Error{DBBC_EOVERFLOW, "hub cursors exceed the fixed scratch"};
   }

@@ -133,84 +133,123 @@ constexpr int kMediumWarps = kMediumThreads / 32;
 // work item is one hub and a span of its windows, owned by one CTA, so the
 // counts of every endpoint in a window are complete inside that CTA: they live
 // in shared memory, and the Lemma 1 contributions come from the value each
-// atomic returns. Each lower neighbour v keeps a cursor into its row; rows
-// ascend, so sweeping the windows in order moves every cursor forward only.
-// Counters pack (asym << 16) | sym when the hub has fewer than 2^16 lower
-// neighbours (no count can exceed that), else (asym << 32) | sym.
+// atomic returns. Each lower neighbour v keeps a cursor into its row (uint32
+// positions: a CSR has fewer than 2^32 entries); rows ascend, so sweeping the
+// windows in order moves every cursor forward only. Counters pack
+// (asym << 16) | sym when the hub has fewer than 2^16 lower neighbours (no
+// count can exceed that), else (asym << 32) | sym.
 constexpr int kSweepThreads = DBBC_SWEEP_THREADS;
 constexpr int kSweepUnroll = DBBC_SWEEP_UNROLL;
+constexpr int kSweepBatch = DBBC_SWEEP_BATCH;
 
-__device__ __forceinline__ void sweep_contrib16(uint32_t old, bool sym, uint64_t& bal, uint64_t& unb) {
-  const uint64_t p = old & 0xFFFFu, q = old >> 16;
-  bal += sym ? p : q;
-  unb += sym ? q : p;
+// x[u] = entry at position c + u*G + gl of a row ending at en, or ~0 past it.
+template <int G>
+__device__ __forceinline__ void load_chunk(const uint32_t* col, uint32_t c, uint32_t en, int gl,
+                                           uint32_t (&x)[kSweepUnroll]) {
+#pragma unroll
+  for (int u = 0; u < kSweepUnroll; u++) {
+    const uint32_t off = (uint32_t)(u * G + gl);
+    x[u] = en - c > off ? col[c + off] : 0xFFFFFFFFu;
+  }
+}
+
+// A group of G lanes walks one neighbour's entries inside the window [lo,
+// hl >> 1) from cursor c (the first chunk already in x) and returns the cursor
+// past the window. Entries of the window are a prefix of what is left of the
+// row, so the lanes stop at the first chunk that is not full.
+// Narrow counters: the old value of the wedge's own class (B1 for a symmetric
+// wedge, B2 for an asymmetric one) closes balanced butterflies and the other
+// class unbalanced ones (Lemma 1, incremental); rotating the packed counter by
+// 16 bits for an asymmetric wedge puts its own class in the low half. One
+// segment adds fewer than 2^32 to each (< 57344 wedges, each < 2^16), so the
+// sums run in 32 bits and are added once per segment.
+template <int G, bool PACK16>
+__device__ __forceinline__ uint32_t walk_segment(const uint32_t* col, uint32_t c, uint32_t en, uint32_t s1,
+                                                 uint32_t (&x)[kSweepUnroll], uint32_t lo2, uint32_t hl, int gl,
+                                                 unsigned gmask, uint32_t* c16, unsigned long long* c32,
+                                                 uint64_t& bal, uint64_t& unb) {
+  uint32_t acc_same = 0, acc_other = 0;
+  for (;;) {
+    int n_ok = 0;
+#pragma unroll
+    for (int u = 0; u < kSweepUnroll; u++) {
+      const bool ok = x[u] < hl;
+      if (ok) {
+        const uint32_t asym = (x[u] ^ s1) & 1u;
+        const uint32_t k = (x[u] - lo2) >> 1;
+        if (PACK16) {
+          const uint32_t sh = asym << 4;
+          const uint32_t old = atomicAdd(&c16[k], 1u << sh);
+          const uint32_t v = __funnelshift_l(old, old, sh);  // (other class << 16) | own class
+          acc_same += v & 0xFFFFu;
+          acc_other += v >> 16;
+        } else {
+          const unsigned long long inc = asym ? (1ull << 32) : 1ull;
+          wedge_contrib(atomicAdd(&c32[k], inc), inc, bal, unb);
+        }
+      }
+      n_ok += __popc(__ballot_sync(gmask, ok));
+    }
+    c += (uint32_t)n_ok;
+    if (n_ok < G * kSweepUnroll) break;
+    load_chunk<G>(col, c, en, gl, x);
+  }
+  bal += acc_same;
+  unb += acc_other;
+  return c;
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  const unsigned lane = lane_id();
+  return G == 32 ? kFullMask : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
 }
 
 // One window of one item: every group of G lanes takes lower neighbours
-// gid, gid + groups, ... and walks the neighbour's row from its cursor, G
-// consecutive entries at a time, until an entry leaves the window.
+// gid, gid + groups, ... and walks the neighbour's row from its cursor until
+// an entry leaves the window. A group takes kSweepBatch neighbours at a time
+// and issues all their cursor loads, then all their first-chunk loads, before
+// walking any of them, so that kSweepBatch dependent load chains are in flight
+// per group instead of one.
 template <int G, bool PACK16>
-__device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& q, int64_t* cur, uint32_t lo,
+__device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& q, uint32_t* cur, uint32_t lo,
                                              uint32_t hl, uint32_t* c16, unsigned long long* c32, uint64_t& bal,
                                              uint64_t& unb) {
-  const int tid = threadIdx.x;
-  const int gl = tid & (G - 1);
-  const uint32_t gid = (uint32_t)tid / G;
+  const int gl = threadIdx.x & (G - 1);
+  const uint32_t gid = threadIdx.x / G;
   constexpr uint32_t groups = kSweepThreads / G;
-  const unsigned lane = lane_id();
-  const unsigned gmask = G == 32 ? kFullMask : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+  const unsigned gmask = group_mask<G>();
   const uint32_t lo2 = lo << 1;
-  // the next neighbour's cursor and edge sign are loaded while this one is walked
-  int64_t c_nx = 0, en_nx = 0;
-  uint32_t s1_nx = 0;
-  if (gid < q.L) {
-    c_nx = cur[2 * gid];
-    en_nx = cur[2 * gid + 1];
-    s1_nx = g.col[q.rb + gid] & 1u;
-  }
-  for (uint32_t i = gid; i < q.L; i += groups) {
-    int64_t c = c_nx;
-    const int64_t en = en_nx;
-    const uint32_t s1 = s1_nx;
-    const uint32_t i_nx = i + groups;
-    if (i_nx < q.L) {
-      c_nx = cur[2 * i_nx];
-      en_nx = cur[2 * i_nx + 1];
-      s1_nx = g.col[q.rb + i_nx] & 1u;
-    }
-    for (;;) {
-      uint32_t x[kSweepUnroll];
+  const uint32_t* col = g.col;
+  for (uint32_t i0 = gid; i0 < q.L; i0 += groups * kSweepBatch) {
+    uint32_t c[kSweepBatch], en[kSweepBatch], s1[kSweepBatch], x[kSweepBatch][kSweepUnroll];
 #pragma unroll
-      for (int u = 0; u < kSweepUnroll; u++) {
-        const int64_t pos = c + u * G + gl;
-        x[u] = pos < en ? g.col[pos] : 0xFFFFFFFFu;
+    for (int k = 0; k < kSweepBatch; k++) {
+      const uint32_t i = i0 + k * groups;
+      c[k] = en[k] = s1[k] = 0;
+      if (i < q.L) {
+        c[k] = cur[2 * i];
+        en[k] = cur[2 * i + 1];
+        s1[k] = col[q.rb + i] & 1u;
       }
-      int n_ok = 0;
-#pragma unroll
-      for (int u = 0; u < kSweepUnroll; u++) {
-        const bool ok = x[u] < hl;
-        if (ok) {
-          const bool sym = ((x[u] ^ s1) & 1u) == 0;
-          const uint32_t k = (x[u] - lo2) >> 1;
-          if (PACK16) {
-            sweep_contrib16(atomicAdd(&c16[k], sym ? 1u : 0x10000u), sym, bal, unb);
-          } else {
-            const unsigned long long inc = sym ? 1ull : (1ull << 32);
-            wedge_contrib(atomicAdd(&c32[k], inc), inc, bal, unb);
-          }
-        }
-        n_ok += __popc(__ballot_sync(gmask, ok));  // accepted entries are a prefix
-      }
-      c += n_ok;
-      if (n_ok < G * kSweepUnroll) break;
     }
-    if (gl == 0) cur[2 * i] = c;
+#pragma unroll
+    for (int k = 0; k < kSweepBatch; k++) load_chunk<G>(col, c[k], en[k], gl, x[k]);
+#pragma unroll
+    for (int k = 0; k < kSweepBatch; k++) {
+      const uint32_t i = i0 + k * groups;
+      if (i < q.L) {
+        const uint32_t cn = walk_segment<G, PACK16>(col, c[k], en[k], s1[k], x[k], lo2, hl, gl, gmask, c16, c32,
+                                                    bal, unb);
+        if (gl == 0 && cn != c[k]) cur[2 * i] = cn;
+      }
+    }
   }
 }
 
 template <bool PACK16>
 __device__ __forceinline__ void sweep_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
-                                                      int64_t* cur, uint32_t lo, uint32_t hl, uint32_t* c16,
+                                                      uint32_t* cur, uint32_t lo, uint32_t hl, uint32_t* c16,
                                                       unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
   switch (group_log) {
     case 0: sweep_window<1, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
@@ -219,6 +258,29 @@ __device__ __forceinline__ void sweep_window_dispatch(int group_log, const CsrVi
     case 4: sweep_window<16, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
     default: sweep_window<32, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
   }
+}
+
+// Cursors of an item: the first entry of each lower neighbour's row at or
+// after rank `lo_rank`, and the row end.
+__device__ __forceinline__ void init_cursor(const CsrView& g, const PivotGeom& q, uint32_t i, uint32_t lo_rank,
+                                            uint32_t* cur, uint32_t& b_out, uint32_t& en_out) {
+  const uint32_t e = g.col[q.rb + i];
+  const int64_t vrow = q.base + (e >> 1);
+  int64_t b = g.row_ptr[vrow];
+  const int64_t en = g.row_ptr[vrow + 1];
+  const uint32_t first = lo_rank << 1;
+  if (first) {  // lower_bound of `first` in the row
+    int64_t lo = b, hi = en;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (g.col[mid] < first) lo = mid + 1; else hi = mid;
+    }
+    b = lo;
+  }
+  b_out = (uint32_t)b;
+  en_out = (uint32_t)en;
+  cur[2 * i] = b_out;
+  cur[2 * i + 1] = en_out;
 }
 
 // ------------------------------------------------------------------ hub tier, list mode
@@ -251,74 +313,47 @@ __device__ __forceinline__ void list_append(const ListItem& li, uint32_t x, uint
 // One window of a list-mode item: groups of G lanes take the listed
 // neighbours j = gid, gid + groups, ... of `list` (n of them), walk each from
 // its cursor like sweep_window, then requeue it by its first entry past the
-// window.
+// window. The next listed neighbour and its cursor are loaded while the
+// current one is walked (the list, cursor, entry loads form a chain, so one
+// stage ahead beats loading several neighbours at once here).
 template <int G, bool PACK16>
-__device__ __forceinline__ void list_window(const CsrView& g, const PivotGeom& q, int64_t* cur, const ListItem& li,
+__device__ __forceinline__ void list_window(const CsrView& g, const PivotGeom& q, uint32_t* cur, const ListItem& li,
                                             const uint32_t* list, uint32_t n, uint32_t lo, uint32_t hl,
                                             uint32_t* c16, unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
-  const int tid = threadIdx.x;
-  const int gl = tid & (G - 1);
-  const uint32_t gid = (uint32_t)tid / G;
+  const int gl = threadIdx.x & (G - 1);
+  const uint32_t gid = threadIdx.x / G;
   constexpr uint32_t groups = kSweepThreads / G;
-  const unsigned lane = lane_id();
-  const unsigned gmask = G == 32 ? kFullMask : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+  const unsigned gmask = group_mask<G>();
   const uint32_t lo2 = lo << 1;
-  uint32_t i_nx = 0;
-  int64_t c_nx = 0, en_nx = 0;
-  uint32_t s1_nx = 0;
+  const uint32_t* col = g.col;
+  uint32_t i_nx = 0, c_nx = 0, en_nx = 0, s1_nx = 0;
   if (gid < n) {
     i_nx = list[gid];
     c_nx = cur[2 * i_nx];
     en_nx = cur[2 * i_nx + 1];
-    s1_nx = g.col[q.rb + i_nx] & 1u;
+    s1_nx = col[q.rb + i_nx] & 1u;
   }
   for (uint32_t j = gid; j < n; j += groups) {
-    const uint32_t i = i_nx;
-    int64_t c = c_nx;
-    const int64_t en = en_nx;
-    const uint32_t s1 = s1_nx;
+    const uint32_t i = i_nx, c0 = c_nx, en = en_nx, s1 = s1_nx;
     if (j + groups < n) {
       i_nx = list[j + groups];
       c_nx = cur[2 * i_nx];
       en_nx = cur[2 * i_nx + 1];
-      s1_nx = g.col[q.rb + i_nx] & 1u;
+      s1_nx = col[q.rb + i_nx] & 1u;
     }
-    for (;;) {
-      uint32_t x[kSweepUnroll];
-#pragma unroll
-      for (int u = 0; u < kSweepUnroll; u++) {
-        const int64_t pos = c + u * G + gl;
-        x[u] = pos < en ? g.col[pos] : 0xFFFFFFFFu;
-      }
-      int n_ok = 0;
-#pragma unroll
-      for (int u = 0; u < kSweepUnroll; u++) {
-        const bool ok = x[u] < hl;
-        if (ok) {
-          const bool sym = ((x[u] ^ s1) & 1u) == 0;
-          const uint32_t k = (x[u] - lo2) >> 1;
-          if (PACK16) {
-            sweep_contrib16(atomicAdd(&c16[k], sym ? 1u : 0x10000u), sym, bal, unb);
-          } else {
-            const unsigned long long inc = sym ? 1ull : (1ull << 32);
-            wedge_contrib(atomicAdd(&c32[k], inc), inc, bal, unb);
-          }
-        }
-        n_ok += __popc(__ballot_sync(gmask, ok));  // accepted entries are a prefix
-      }
-      c += n_ok;
-      if (n_ok < G * kSweepUnroll) break;
-    }
+    uint32_t x[kSweepUnroll];
+    load_chunk<G>(col, c0, en, gl, x);
+    const uint32_t c = walk_segment<G, PACK16>(col, c0, en, s1, x, lo2, hl, gl, gmask, c16, c32, bal, unb);
     if (gl == 0) {
       cur[2 * i] = c;
-      if (c < en) list_append(li, g.col[c], i);
+      if (c < en) list_append(li, col[c], i);
     }
   }
 }
 
 template <bool PACK16>
 __device__ __forceinline__ void list_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
-                                                     int64_t* cur, const ListItem& li, const uint32_t* list,
+                                                     uint32_t* cur, const ListItem& li, const uint32_t* list,
                                                      uint32_t n, uint32_t lo, uint32_t hl, uint32_t* c16,
                                                      unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
   switch (group_log) {

@@ -29,6 +29,10 @@ constexpr int kMediumSlots = 8192;
 #ifndef DBBC_SWEEP_UNROLL
 #define DBBC_SWEEP_UNROLL 2
 #endif
+// neighbours a lane group loads together before walking them
+#ifndef DBBC_SWEEP_BATCH
+#define DBBC_SWEEP_BATCH 4
+#endif
 constexpr uint32_t kSweepWindow16 = DBBC_SWEEP_WINDOW16;     // 32-bit counters packing two 16-bit halves
 constexpr uint32_t kSweepWindow32 = DBBC_SWEEP_WINDOW16 / 2;  // 64-bit counters packing two 32-bit halves
 constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per work item
@@ -182,6 +186,6 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t stream, unsigned long long*
 
 // count.cu: the same kernels with caller-supplied scratch (see noalloc.cu).
 void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t stream, unsigned long long* d_out, unsigned* d_status,
-                            int* d_next, int64_t* cursors, size_t cursor_bytes);
+                            int* d_next, uint32_t* cursors, size_t cursor_bytes);
 
 }  // namespace dbbc

@@ -57,7 +57,7 @@ extern "C" dbbc_status dbbc_count_noalloc(const dbbc_graph* g, void* cuda_stream
     unsigned char* base = noalloc_scratch_address();
     unsigned* d_status = reinterpret_cast<unsigned*>(base);
     int* d_next = reinterpret_cast<int*>(base + 64);
-    int64_t* cursors = reinterpret_cast<int64_t*>(base + kNoAllocHeaderBytes);
+    uint32_t* cursors = reinterpret_cast<uint32_t*>(base + kNoAllocHeaderBytes);
     enqueue_count_prealloc(g, s, reinterpret_cast<unsigned long long*>(d_out), d_status, d_next, cursors,
                            kNoAllocScratchBytes - kNoAllocHeaderBytes);
     return DBBC_OK;
