@@ -41,14 +41,7 @@ __global__ void __launch_bounds__(kLightWarps * 32) count_light_kernel(CsrView g
     const int32_t p = piv[t];
     const int log_h = table_log(work[p], max_log, hash_mult_log);
     const PivotGeom q = pivot_geom(g, p);
-    warp_walk<1>(g, q, 0, q.L, 32, [&](const uint32_t (&x)[1], uint32_t s1) {
-      if (x[0] != 0xFFFFFFFFu) {
-        const unsigned long long inc = wedge_inc(x[0], s1);
-        unsigned long long old;
-        if (smem_hash_add(keys, vals, log_h, x[0] >> 1, inc, &old)) wedge_contrib(old, inc, bal, unb);
-        else full = true;
-      }
-    });
+    full |= !hash_walk_dispatch(hash_group_log(work[p], q.L, 5), lane, 32u, g, q, keys, vals, log_h, bal, unb);
     __syncwarp();
     for (int i = lane; i < (1 << log_h); i += 32) {
       keys[i] = kEmptyKey;
@@ -74,24 +67,14 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
   }
   __syncthreads();
   constexpr int max_log = 13;  // log2(kMediumSlots)
-  const int w = threadIdx.x >> 5;
   uint64_t bal = 0, unb = 0;
   bool full = false;
   for (int64_t t = blockIdx.x; t < n_piv; t += gridDim.x) {
     const int32_t p = piv[t];
     const int log_h = table_log(work[p], max_log, hash_mult_log);
     const PivotGeom q = pivot_geom(g, p);
-    warp_walk<2>(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u, [&](const uint32_t (&x)[2], uint32_t s1) {
-#pragma unroll
-      for (int u = 0; u < 2; u++) {
-        if (x[u] != 0xFFFFFFFFu) {
-          const unsigned long long inc = wedge_inc(x[u], s1);
-          unsigned long long old;
-          if (smem_hash_add(keys, vals, log_h, x[u] >> 1, inc, &old)) wedge_contrib(old, inc, bal, unb);
-          else full = true;
-        }
-      }
-    });
+    full |= !hash_walk_dispatch(hash_group_log(work[p], q.L, 5), threadIdx.x, (uint32_t)kMediumThreads, g, q, keys,
+                                vals, log_h, bal, unb);
     __syncthreads();
     for (int i = threadIdx.x; i < (1 << log_h); i += kMediumThreads) {
       keys[i] = kEmptyKey;

@@ -122,6 +122,79 @@ __device__ __forceinline__ void warp_walk(const CsrView& g, const PivotGeom& q, 
   }
 }
 
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  const unsigned lane = lane_id();
+  return G == 32 ? kFullMask : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+}
+
+// Hash tiers: groups of G lanes (group gid of `groups`) take lower neighbours
+// gid, gid + groups, ... of the pivot; a group walks its neighbour's accepted
+// prefix G entries at a time and adds every wedge to the shared hash table,
+// accumulating the Lemma 1 contributions. The next neighbour's row bounds are
+// loaded while the current one is walked. Returns false if the table ran out
+// of slots. G is chosen from the pivot's mean accepted segment (work / L) so
+// that short segments do not leave most lanes of a warp idle.
+template <int G>
+__device__ __forceinline__ bool hash_walk(uint32_t gid, uint32_t groups, const CsrView& g, const PivotGeom& q,
+                                          uint32_t* keys, unsigned long long* vals, int log_h, uint64_t& bal,
+                                          uint64_t& unb) {
+  const int gl = threadIdx.x & (G - 1);
+  const unsigned gmask = group_mask<G>();
+  bool fits = true;
+  int64_t b_nx = 0, en_nx = 0;
+  uint32_t s1_nx = 0;
+  if (gid < q.L) {
+    const uint32_t e = g.col[q.rb + gid];
+    const int64_t vrow = q.base + (e >> 1);
+    b_nx = g.row_ptr[vrow];
+    en_nx = g.row_ptr[vrow + 1];
+    s1_nx = e & 1u;
+  }
+  for (uint32_t i = gid; i < q.L; i += groups) {
+    const int64_t b = b_nx, en = en_nx;
+    const uint32_t s1 = s1_nx;
+    if (i + groups < q.L) {
+      const uint32_t e = g.col[q.rb + i + groups];
+      const int64_t vrow = q.base + (e >> 1);
+      b_nx = g.row_ptr[vrow];
+      en_nx = g.row_ptr[vrow + 1];
+      s1_nx = e & 1u;
+    }
+    for (int64_t c = b; c < en; c += G) {
+      const int64_t j = c + gl;
+      const uint32_t x = j < en ? g.col[j] : 0xFFFFFFFFu;
+      const bool ok = x < q.lim;
+      if (ok) {
+        const unsigned long long inc = wedge_inc(x, s1);
+        unsigned long long old;
+        if (smem_hash_add(keys, vals, log_h, x >> 1, inc, &old)) wedge_contrib(old, inc, bal, unb);
+        else fits = false;
+      }
+      if (__ballot_sync(gmask, !ok)) break;  // rows ascend: nothing accepted beyond
+    }
+  }
+  return fits;
+}
+
+// log2 of the lanes per neighbour for a pivot whose lower neighbours carry
+// `work` accepted wedges in all (at least 4 lanes, at most `max_log`).
+__device__ __forceinline__ int hash_group_log(uint64_t work, uint32_t L, int max_log) {
+  const uint64_t mean = work / (L ? L : 1);
+  const int lg = mean >= 24 ? 5 : mean >= 12 ? 4 : mean >= 6 ? 3 : 2;
+  return lg < max_log ? lg : max_log;
+}
+
+template <typename... A>
+__device__ __forceinline__ bool hash_walk_dispatch(int group_log, uint32_t tid, uint32_t threads, A&&... a) {
+  switch (group_log) {
+    case 2: return hash_walk<4>(tid >> 2, threads >> 2, a...);
+    case 3: return hash_walk<8>(tid >> 3, threads >> 3, a...);
+    case 4: return hash_walk<16>(tid >> 4, threads >> 4, a...);
+    default: return hash_walk<32>(tid >> 5, threads >> 5, a...);
+  }
+}
+
 constexpr int kLightWarps = 8;
 
 constexpr int kMediumThreads = 256;
@@ -197,12 +270,6 @@ __device__ __forceinline__ uint32_t walk_segment(const uint32_t* col, uint32_t c
   bal += acc_same;
   unb += acc_other;
   return c;
-}
-
-template <int G>
-__device__ __forceinline__ unsigned group_mask() {
-  const unsigned lane = lane_id();
-  return G == 32 ? kFullMask : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
 }
 
 // One window of one item: every group of G lanes takes lower neighbours
