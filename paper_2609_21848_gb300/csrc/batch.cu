@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
   unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
   __shared__ int item_sh;
   const int tid = threadIdx.x;
-  for (int i = tid; i < (int)kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
+  zero_words(c16, kSweepWindow16);
   uint32_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
       else sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
       __syncthreads();
       const uint32_t words = wide ? 2 * (hi - lo) : (hi - lo);
-      for (uint32_t j = tid; j < words; j += kSweepThreads) c16[j] = 0u;
+      zero_words(c16, words);
       __syncthreads();
     }
     block_add_pair<kSweepThreads>(bal, unb, out + 2 * bi.graph);

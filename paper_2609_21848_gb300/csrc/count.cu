@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
   __shared__ int item_sh;
   __shared__ int cnt[kListMaxWindows];
   const int tid = threadIdx.x;
-  for (int i = tid; i < (int)kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
+  zero_words(c16, kSweepWindow16);
   uint32_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
   uint32_t* my_lists = lists ? lists + (int64_t)blockIdx.x * list_cap : nullptr;
   uint64_t bal = 0, unb = 0, n_visits = 0;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
       }
       __syncthreads();  // also publishes the appends made to later windows' lists
       const uint32_t words = wide ? 2 * (hi - lo) : (hi - lo);  // 32-bit words to clear
-      for (uint32_t j = tid; j < words; j += kSweepThreads) c16[j] = 0u;
+      zero_words(c16, words);
       __syncthreads();
     }
   }

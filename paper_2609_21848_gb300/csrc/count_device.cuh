@@ -214,6 +214,15 @@ constexpr int kMediumWarps = kMediumThreads / 32;
 constexpr int kSweepThreads = DBBC_SWEEP_THREADS;
 constexpr int kSweepUnroll = DBBC_SWEEP_UNROLL;
 constexpr int kSweepBatch = DBBC_SWEEP_BATCH;
+static_assert(kSweepWindow16 % 4 == 0, "window buffers are cleared 16 bytes at a time");
+
+// Clear the first `words` 32-bit words of a window (16 bytes per store; the
+// window buffer holds a multiple of 4 words).
+__device__ __forceinline__ void zero_words(uint32_t* w, uint32_t words) {
+  uint4* q = reinterpret_cast<uint4*>(w);
+  const uint32_t quads = (words + 3) >> 2;
+  for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) q[j] = make_uint4(0u, 0u, 0u, 0u);
+}
 
 // x[u] = entry at position c + u*G + gl of a row ending at en, or ~0 past it.
 template <int G>
@@ -229,7 +238,10 @@ __device__ __forceinline__ void load_chunk(const uint32_t* col, uint32_t c, uint
 // A group of G lanes walks one neighbour's entries inside the window [lo,
 // hl >> 1) from cursor c (the first chunk already in x) and returns the cursor
 // past the window. Entries of the window are a prefix of what is left of the
-// row, so the lanes stop at the first chunk that is not full.
+// row, so the group stops at the first chunk that is not full. All groups of a
+// warp run the loop in lockstep until the last of them is done (warp-wide
+// votes, the atomic the only predicated step), which keeps the warp converged;
+// a group that is not `active` (no neighbour) only votes.
 // Narrow counters: the old value of the wedge's own class (B1 for a symmetric
 // wedge, B2 for an asymmetric one) closes balanced butterflies and the other
 // class unbalanced ones (Lemma 1, incremental); rotating the packed counter by
@@ -239,33 +251,37 @@ __device__ __forceinline__ void load_chunk(const uint32_t* col, uint32_t c, uint
 template <int G, bool PACK16>
 __device__ __forceinline__ uint32_t walk_segment(const uint32_t* col, uint32_t c, uint32_t en, uint32_t s1,
                                                  uint32_t (&x)[kSweepUnroll], uint32_t lo2, uint32_t hl, int gl,
-                                                 unsigned gmask, uint32_t* c16, unsigned long long* c32,
+                                                 bool active, uint32_t* c16, unsigned long long* c32,
                                                  uint64_t& bal, uint64_t& unb) {
+  const unsigned gshift = lane_id() & ~(unsigned)(G - 1);
+  const unsigned gbits = G == 32 ? kFullMask : (1u << G) - 1u;
   uint32_t acc_same = 0, acc_other = 0;
   for (;;) {
     int n_ok = 0;
 #pragma unroll
     for (int u = 0; u < kSweepUnroll; u++) {
-      const bool ok = x[u] < hl;
-      if (ok) {
-        const uint32_t asym = (x[u] ^ s1) & 1u;
-        const uint32_t k = (x[u] - lo2) >> 1;
-        if (PACK16) {
-          const uint32_t sh = asym << 4;
-          const uint32_t old = atomicAdd(&c16[k], 1u << sh);
-          const uint32_t v = __funnelshift_l(old, old, sh);  // (other class << 16) | own class
-          acc_same += v & 0xFFFFu;
-          acc_other += v >> 16;
-        } else {
-          const unsigned long long inc = asym ? (1ull << 32) : 1ull;
-          wedge_contrib(atomicAdd(&c32[k], inc), inc, bal, unb);
-        }
+      const bool ok = active && x[u] < hl;
+      const uint32_t asym = (x[u] ^ s1) & 1u;
+      const uint32_t k = (x[u] - lo2) >> 1;
+      if (PACK16) {
+        const uint32_t sh = asym << 4;
+        uint32_t old = 0;
+        if (ok) old = atomicAdd(&c16[k], 1u << sh);
+        const uint32_t v = __funnelshift_l(old, old, sh);  // (other class << 16) | own class
+        acc_same += v & 0xFFFFu;
+        acc_other += v >> 16;
+      } else {
+        const unsigned long long inc = asym ? (1ull << 32) : 1ull;
+        unsigned long long old = 0;
+        if (ok) old = atomicAdd(&c32[k], inc);
+        wedge_contrib(old, inc, bal, unb);  // adds nothing when old == 0
       }
-      n_ok += __popc(__ballot_sync(gmask, ok));
+      n_ok += __popc((__ballot_sync(kFullMask, ok) >> gshift) & gbits);
     }
     c += (uint32_t)n_ok;
-    if (n_ok < G * kSweepUnroll) break;
-    load_chunk<G>(col, c, en, gl, x);
+    active = active && n_ok == G * kSweepUnroll;
+    if (!__any_sync(kFullMask, active)) break;
+    if (active) load_chunk<G>(col, c, en, gl, x);
   }
   bal += acc_same;
   unb += acc_other;
@@ -277,7 +293,7 @@ __device__ __forceinline__ uint32_t walk_segment(const uint32_t* col, uint32_t c
 // an entry leaves the window. A group takes kSweepBatch neighbours at a time
 // and issues all their cursor loads, then all their first-chunk loads, before
 // walking any of them, so that kSweepBatch dependent load chains are in flight
-// per group instead of one.
+// per group instead of one. Warps loop in lockstep (see walk_segment).
 template <int G, bool PACK16>
 __device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& q, uint32_t* cur, uint32_t lo,
                                              uint32_t hl, uint32_t* c16, unsigned long long* c32, uint64_t& bal,
@@ -285,10 +301,9 @@ __device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& 
   const int gl = threadIdx.x & (G - 1);
   const uint32_t gid = threadIdx.x / G;
   constexpr uint32_t groups = kSweepThreads / G;
-  const unsigned gmask = group_mask<G>();
   const uint32_t lo2 = lo << 1;
   const uint32_t* col = g.col;
-  for (uint32_t i0 = gid; i0 < q.L; i0 += groups * kSweepBatch) {
+  for (uint32_t i0 = gid; __any_sync(kFullMask, i0 < q.L); i0 += groups * kSweepBatch) {
     uint32_t c[kSweepBatch], en[kSweepBatch], s1[kSweepBatch], x[kSweepBatch][kSweepUnroll];
 #pragma unroll
     for (int k = 0; k < kSweepBatch; k++) {
@@ -305,11 +320,10 @@ __device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& 
 #pragma unroll
     for (int k = 0; k < kSweepBatch; k++) {
       const uint32_t i = i0 + k * groups;
-      if (i < q.L) {
-        const uint32_t cn = walk_segment<G, PACK16>(col, c[k], en[k], s1[k], x[k], lo2, hl, gl, gmask, c16, c32,
-                                                    bal, unb);
-        if (gl == 0 && cn != c[k]) cur[2 * i] = cn;
-      }
+      const bool active = i < q.L;
+      const uint32_t cn =
+          walk_segment<G, PACK16>(col, c[k], en[k], s1[k], x[k], lo2, hl, gl, active, c16, c32, bal, unb);
+      if (active && gl == 0 && cn != c[k]) cur[2 * i] = cn;
     }
   }
 }
@@ -390,7 +404,6 @@ __device__ __forceinline__ void list_window(const CsrView& g, const PivotGeom& q
   const int gl = threadIdx.x & (G - 1);
   const uint32_t gid = threadIdx.x / G;
   constexpr uint32_t groups = kSweepThreads / G;
-  const unsigned gmask = group_mask<G>();
   const uint32_t lo2 = lo << 1;
   const uint32_t* col = g.col;
   uint32_t i_nx = 0, c_nx = 0, en_nx = 0, s1_nx = 0;
@@ -400,7 +413,8 @@ __device__ __forceinline__ void list_window(const CsrView& g, const PivotGeom& q
     en_nx = cur[2 * i_nx + 1];
     s1_nx = col[q.rb + i_nx] & 1u;
   }
-  for (uint32_t j = gid; j < n; j += groups) {
+  for (uint32_t j = gid; __any_sync(kFullMask, j < n); j += groups) {
+    const bool active = j < n;
     const uint32_t i = i_nx, c0 = c_nx, en = en_nx, s1 = s1_nx;
     if (j + groups < n) {
       i_nx = list[j + groups];
@@ -409,9 +423,9 @@ __device__ __forceinline__ void list_window(const CsrView& g, const PivotGeom& q
       s1_nx = col[q.rb + i_nx] & 1u;
     }
     uint32_t x[kSweepUnroll];
-    load_chunk<G>(col, c0, en, gl, x);
-    const uint32_t c = walk_segment<G, PACK16>(col, c0, en, s1, x, lo2, hl, gl, gmask, c16, c32, bal, unb);
-    if (gl == 0) {
+    load_chunk<G>(col, c0, active ? en : c0, gl, x);
+    const uint32_t c = walk_segment<G, PACK16>(col, c0, en, s1, x, lo2, hl, gl, active, c16, c32, bal, unb);
+    if (active && gl == 0) {
       cur[2 * i] = c;
       if (c < en) list_append(li, col[c], i);
     }

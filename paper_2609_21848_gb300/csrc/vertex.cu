@@ -287,7 +287,7 @@ __device__ void tips_window(const CsrView& g, const PivotGeom& q, int64_t* cur, 
   }
   __syncthreads();
   const uint32_t words = PACK16 ? (hi - lo) : 2 * (hi - lo);
-  for (uint32_t j = threadIdx.x; j < words; j += kSweepThreads) c16[j] = 0u;
+  zero_words(c16, words);
   __syncthreads();
 }
 
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kSweepThreads) tips_sweep_kernel(CsrView g, co
   __shared__ int item_sh;
   __shared__ unsigned long long red[2][kSweepThreads / 32];
   const int tid = threadIdx.x;
-  for (int i = tid; i < (int)kSweepWindow16; i += kSweepThreads) c16[i] = 0u;
+  zero_words(c16, kSweepWindow16);
   int64_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 3;
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
