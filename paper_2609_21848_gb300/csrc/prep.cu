@@ -665,7 +665,9 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
     if (n > 0) {
       vertex_keys_kernel<<<grid_for(n), 256, 0, s>>>(deg, n, n_u, bits_comp, bits_deg, bits_lid, uv, vk0);
       DBBC_LAUNCH_CHECK();
-      const bool alt = radix_sort<uint64_t, uint32_t, false>(vk0, vk1, nullptr, nullptr, n, 0,
+      // keys are generated in (side, component, local id) order, so a stable
+      // sort on (side, component, degree) alone leaves equal degrees by id
+      const bool alt = radix_sort<uint64_t, uint32_t, false>(vk0, vk1, nullptr, nullptr, n, bits_lid,
                                                              1 + bits_comp + bits_deg + bits_lid, s, sc);
       ranks_kernel<<<grid_for(n), 256, 0, s>>>(alt ? vk1 : vk0, n, n_u, bits_comp, bits_deg, bits_lid, uv,
                                                g->vertex, side_rank, rowdeg);

@@ -113,8 +113,8 @@ void exclusive_scan(const TI* in, TO* out, int64_t n, cudaStream_t s, Scratch& s
 // ------------------------------------------------------------------ radix sort
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 4096 keys per tile
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 keys per tile
 
 template <typename K>
 __device__ __forceinline__ uint32_t rs_digit(K key, int shift) {
