@@ -236,23 +236,33 @@ __device__ __forceinline__ unsigned long long window_value(const uint32_t* c16, 
   return c32[k];
 }
 
-template <bool PACK16, bool VERT, bool EDGE>
-__device__ void tips_window(const CsrView& g, const PivotGeom& q, int64_t* cur, uint32_t lo, uint32_t hi,
-                            uint32_t* c16, unsigned long long* c32, const TipOut& o, uint64_t& pb, uint64_t& pu) {
+// One window of a hub item, in three passes over the item's lower
+// neighbours (lane groups of G as in the counting sweep, moving in warp
+// lockstep): count the window's wedges (each neighbour's cursor moves past
+// the window, its old value kept in `prev`), credit endpoints and the pivot
+// from the complete window, then walk every neighbour's segment
+// [prev, cursor) again for the middles and edges.
+template <int G, bool PACK16, bool VERT, bool EDGE>
+__device__ __forceinline__ void tips_window(const CsrView& g, const PivotGeom& q, uint32_t* cur, uint32_t* prev, uint32_t lo,
+                            uint32_t hi, uint32_t* c16, unsigned long long* c32, const TipOut& o, uint64_t& pb,
+                            uint64_t& pu) {
   const uint32_t hl = hi << 1, lo2 = lo << 1;
-  for (uint32_t i = threadIdx.x; i < q.L; i += kSweepThreads) {
-    int64_t c = cur[3 * i];
-    const int64_t en = cur[3 * i + 1];
-    const uint32_t s1 = g.col[q.rb + i] & 1u;
-    for (; c < en; c++) {
-      const uint32_t x = g.col[c];
-      if (x >= hl) break;
-      const bool sym = ((x ^ s1) & 1u) == 0;
-      const uint32_t k = (x - lo2) >> 1;
-      if (PACK16) atomicAdd(&c16[k], sym ? 1u : 0x10000u);
-      else atomicAdd(&c32[k], sym ? 1ull : (1ull << 32));
+  const int gl = threadIdx.x & (G - 1);
+  const uint32_t gid = threadIdx.x / G;
+  constexpr uint32_t groups = kSweepThreads / G;
+  const uint32_t* col = g.col;
+  uint64_t unused_b = 0, unused_u = 0;
+  for (uint32_t i = gid; __any_sync(kFullMask, i < q.L); i += groups) {
+    const bool active = i < q.L;
+    const uint32_t c = active ? cur[2 * i] : 0u, en = active ? cur[2 * i + 1] : 0u;
+    const uint32_t s1 = active ? col[q.rb + i] & 1u : 0u;
+    uint32_t x[kSweepUnroll];
+    load_chunk<G>(col, c, en, gl, x);
+    const uint32_t cn = walk_segment<G, PACK16>(col, c, en, s1, x, lo2, hl, gl, active, c16, c32, unused_b, unused_u);
+    if (active && gl == 0) {
+      prev[i] = c;
+      cur[2 * i] = cn;
     }
-    cur[3 * i + 2] = c;
   }
   __syncthreads();
   if (VERT) {
@@ -268,33 +278,57 @@ __device__ void tips_window(const CsrView& g, const PivotGeom& q, int64_t* cur, 
       }
     }
   }
-  for (uint32_t i = threadIdx.x; i < q.L; i += kSweepThreads) {
-    const int64_t c0 = cur[3 * i], c1 = cur[3 * i + 2];
-    const uint32_t e = g.col[q.rb + i];
+  for (uint32_t i = gid; __any_sync(kFullMask, i < q.L); i += groups) {
+    const bool active = i < q.L;
+    const uint32_t c0 = active ? prev[i] : 0u, c1 = active ? cur[2 * i] : 0u;
+    const uint32_t e = active ? col[q.rb + i] : 0u;
     const uint32_t s1 = e & 1u;
+    const uint32_t trips = __reduce_max_sync(kFullMask, (c1 - c0 + G - 1) / G);
     uint64_t sb = 0, su = 0;
-    for (int64_t c = c0; c < c1; c++) {
-      const uint32_t x = g.col[c];
-      uint64_t cb, cu;
-      wedge_pairs(window_value<PACK16>(c16, c32, (x - lo2) >> 1), ((x ^ s1) & 1u) == 0, cb, cu);
-      if (EDGE) add_pair(o.eb, o.eu, c, cb, cu);
-      sb += cb;
-      su += cu;
+    for (uint32_t t = 0; t < trips; t++) {
+      const uint32_t pos = c0 + t * G + gl;
+      if (pos < c1) {
+        const uint32_t xx = col[pos];
+        uint64_t cb, cu;
+        wedge_pairs(window_value<PACK16>(c16, c32, (xx - lo2) >> 1), ((xx ^ s1) & 1u) == 0, cb, cu);
+        if (EDGE) add_pair(o.eb, o.eu, pos, cb, cu);
+        sb += cb;
+        su += cu;
+      }
     }
-    if (VERT) add_pair(o.vb, o.vu, q.base + (e >> 1), sb, su);
-    if (EDGE) add_pair(o.eb, o.eu, q.rb + i, sb, su);
-    cur[3 * i] = c1;
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {  // sum over the group's lanes
+      sb += __shfl_xor_sync(kFullMask, sb, off);
+      su += __shfl_xor_sync(kFullMask, su, off);
+    }
+    if (active && gl == 0) {
+      if (VERT) add_pair(o.vb, o.vu, q.base + (e >> 1), sb, su);
+      if (EDGE) add_pair(o.eb, o.eu, q.rb + i, sb, su);
+    }
   }
   __syncthreads();
-  const uint32_t words = PACK16 ? (hi - lo) : 2 * (hi - lo);
-  zero_words(c16, words);
+  zero_words(c16, PACK16 ? (hi - lo) : 2 * (hi - lo));
   __syncthreads();
 }
 
+template <bool PACK16, bool VERT, bool EDGE>
+__device__ __forceinline__ void tips_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
+                                                     uint32_t* cur, uint32_t* prev, uint32_t lo, uint32_t hi,
+                                                     uint32_t* c16, unsigned long long* c32, const TipOut& o,
+                                                     uint64_t& pb, uint64_t& pu) {
+  switch (group_log) {
+    case 0: tips_window<1, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+    case 2: tips_window<4, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+    case 3: tips_window<8, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+    case 4: tips_window<16, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+    default: tips_window<32, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+  }
+}
+
 template <bool VERT, bool EDGE>
-__global__ void __launch_bounds__(kSweepThreads) tips_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
+__global__ void __launch_bounds__(kSweepThreads, 1) tips_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
                                                                    int64_t n_items, int* next_item,
-                                                                   int64_t* __restrict__ cursors, int64_t cur_cap,
+                                                                   uint32_t* __restrict__ cursors, int64_t cur_cap,
                                                                    TipOut o) {
   extern __shared__ __align__(16) unsigned char sweep_smem[];
   uint32_t* c16 = reinterpret_cast<uint32_t*>(sweep_smem);
@@ -303,7 +337,8 @@ __global__ void __launch_bounds__(kSweepThreads) tips_sweep_kernel(CsrView g, co
   __shared__ unsigned long long red[2][kSweepThreads / 32];
   const int tid = threadIdx.x;
   zero_words(c16, kSweepWindow16);
-  int64_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 3;
+  uint32_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 3;  // [cur_cap][2] cursor and row end
+  uint32_t* prev = cur + 2 * cur_cap;                              // [cur_cap] cursor before the window
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
     __syncthreads();
@@ -314,29 +349,16 @@ __global__ void __launch_bounds__(kSweepThreads) tips_sweep_kernel(CsrView g, co
     const PivotGeom q = pivot_geom(g, item.row);
     const bool wide = (item.flags & kItemWide) != 0;
     const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
-    const uint32_t first = item.lo << 1;
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
-      const uint32_t e = g.col[q.rb + i];
-      const int64_t vrow = q.base + (e >> 1);
-      int64_t b = g.row_ptr[vrow];
-      const int64_t en = g.row_ptr[vrow + 1];
-      if (first) {  // lower_bound of `first` in the row
-        int64_t lo = b, hi = en;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (g.col[mid] < first) lo = mid + 1; else hi = mid;
-        }
-        b = lo;
-      }
-      cur[3 * i] = b;
-      cur[3 * i + 1] = en;
+      uint32_t b, en;
+      init_cursor(g, q, i, item.lo, cur, b, en);
     }
     __syncthreads();
     uint64_t pb = 0, pu = 0;
     for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
       const uint32_t hi = min(lo + H, item.hi);
-      if (wide) tips_window<false, VERT, EDGE>(g, q, cur, lo, hi, c16, c32, o, pb, pu);
-      else tips_window<true, VERT, EDGE>(g, q, cur, lo, hi, c16, c32, o, pb, pu);
+      if (wide) tips_window_dispatch<false, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
+      else tips_window_dispatch<true, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
     }
     if (VERT) {  // the pivot's share of this item
       pb = warp_sum_u64(pb);
@@ -436,7 +458,7 @@ void enqueue_tips(const dbbc_graph* g, cudaStream_t s, const TipOut& o, unsigned
     const size_t smem = (size_t)kSweepWindow16 * 4;
     DBBC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = sms * blocks_per_sm((const void*)fn, kSweepThreads, smem);
-    int64_t* cursors = sc.get<int64_t>((size_t)grid * (size_t)g->sweep_max_lower * 3);
+    uint32_t* cursors = sc.get<uint32_t>((size_t)grid * (size_t)g->sweep_max_lower * 3);
     int* next = sc.get<int>(1);
     DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
     fn<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, next, cursors, g->sweep_max_lower,
