@@ -37,14 +37,15 @@ UNIT = "G wedges/s"
 L2_BYTES = 129 * 2**20
 
 # Algorithmic bytes per unit of work of the hub window-sweep kernel (the
-# dominant kernel; its counters live in shared memory):
+# dominant kernel; its counters live in shared memory; cursors are two uint32):
 #   per accepted wedge               : 4 B CSR entry
-#   per (item, lower neighbour) init : 4 B pivot-row entry + 16 B row offsets + 16 B cursor write
-#   per (window, lower neighbour)    : 4 B pivot-row entry (edge sign) + 16 B cursor read
-#                                      + 8 B cursor write + 4 B first entry past the window
+#   per (item, lower neighbour) init : 4 B pivot-row entry + 16 B row offsets + 8 B cursor write
+#   per (window, lower neighbour)    : 4 B pivot-row entry (edge sign) + 8 B cursor read
+#   visited by cursor                  + 4 B cursor write + 4 B first entry past the window
+#   per list-mode visit              : the same 20 B + 4 B list entry read + 4 B list append
 # Light / medium tiers: 4 B per wedge + 28 B per lower neighbour (entry,
 # row offsets, end-of-row probe).
-B_WEDGE, B_CUR_INIT, B_CUR_STEP, B_LOWER = 4, 36, 32, 28
+B_WEDGE, B_CUR_INIT, B_CUR_STEP, B_LIST_VISIT, B_LOWER = 4, 28, 20, 28, 28
 
 
 def parse():
@@ -708,8 +709,9 @@ def main():
     peaks, peak_kind = measured_peaks()
     n_agg = max(1, int(prof.get("launches_hub_aggregate", 0)))
     agg_s = prof.get("ms_hub_aggregate", 0.0) / 1e3
+    list_visits = prof.get("hub_list_visits", 0) / max(1, a.steps)
     bytes_hub_step = (B_WEDGE * info["wedges_hub"] + B_CUR_INIT * info["hub_cursor_inits"]
-                      + B_CUR_STEP * info["hub_cursor_steps"])
+                      + B_CUR_STEP * info["hub_cursor_steps"] + B_LIST_VISIT * list_visits)
     per_launch_bytes = bytes_hub_step * a.steps / n_agg
     per_launch_s = agg_s / n_agg
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
