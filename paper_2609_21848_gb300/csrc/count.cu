@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
 __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
                                                                       int64_t n_items, int* next_item,
                                                                       uint32_t* __restrict__ cursors, int64_t cur_cap,
-                                                                      uint32_t* __restrict__ lists, int64_t list_cap,
+                                                                      uint2* __restrict__ lists, int64_t list_cap,
                                                                       unsigned long long* out,
                                                                       unsigned long long* visits) {
   extern __shared__ __align__(16) unsigned char sweep_smem[];
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
   const int tid = threadIdx.x;
   zero_words(c16, kSweepWindow16);
   uint32_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
-  uint32_t* my_lists = lists ? lists + (int64_t)blockIdx.x * list_cap : nullptr;
+  uint2* my_lists = lists ? lists + (int64_t)blockIdx.x * list_cap : nullptr;
   uint64_t bal = 0, unb = 0, n_visits = 0;
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en;
       init_cursor(g, q, i, item.lo, cur, b, en);
-      if (listed && b < en) list_append(li, g.col[b], i);
+      if (listed && b < en) list_append(li, g.col[b], b, en, g.col[q.rb + i] & 1u);
     }
     __syncthreads();
     for (uint32_t r = 0; r < R; r++) {
@@ -135,9 +135,9 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
       const uint32_t hi = min(lo + H, item.hi);
       if (listed) {
         const uint32_t n = (uint32_t)cnt[r];
-        const uint32_t* list = my_lists + (size_t)r * q.L;
-        if (wide) list_window_dispatch<false>(item.group_log, g, q, cur, li, list, n, lo, hi << 1, c16, c32, bal, unb);
-        else list_window_dispatch<true>(item.group_log, g, q, cur, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+        const uint2* list = my_lists + (size_t)r * q.L;
+        if (wide) list_window_dispatch<false>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+        else list_window_dispatch<true>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
         n_visits += tid == 0 ? n : 0;
       } else {
         if (wide) sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
@@ -235,7 +235,7 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
     DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = sms * blocks_per_sm((const void*)hub_sweep_kernel, kSweepThreads, smem);
     uint32_t* cursors = sc.get<uint32_t>((size_t)grid * (size_t)g->sweep_max_lower * 2);
-    uint32_t* lists = g->sweep_list_cap > 0 ? sc.get<uint32_t>((size_t)grid * (size_t)g->sweep_list_cap) : nullptr;
+    uint2* lists = g->sweep_list_cap > 0 ? sc.get<uint2>((size_t)grid * (size_t)g->sweep_list_cap) : nullptr;
     int* next = sc.get<int>(1);
     DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
     if (prof) {

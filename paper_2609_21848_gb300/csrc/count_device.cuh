@@ -370,12 +370,14 @@ __device__ __forceinline__ void init_cursor(const CsrView& g, const PivotGeom& q
 // still reads its cursor there. In list mode a neighbour is visited only in the
 // windows that hold its entries. Window r of an item keeps a list (global
 // memory, L slots per window) of the neighbours whose next entry falls in it;
-// after walking its entries in window r, a neighbour is appended to the list of
-// the window of its next entry (always a later window), or drops out at the end
-// of its row or of the item. Each neighbour is in at most one list at a time
-// and in each list at most once, so L slots per window never overflow.
+// a slot carries the neighbour's whole state (cursor, entries left in its row,
+// edge sign), so a visit reads its slot and then the row. After walking its
+// entries in window r, a neighbour is appended to the list of the window of
+// its next entry (always a later window), or drops out at the end of its row
+// or of the item. Each neighbour is in at most one list at a time and in each
+// list at most once, so L slots per window never overflow.
 struct ListItem {
-  uint32_t* lists;   // [windows][L] neighbour indices
+  uint2* lists;      // [windows][L] {cursor, entries left | sign << 31}
   int* cnt;          // [windows] list lengths (shared memory)
   uint32_t L;
   uint32_t lo;       // first rank of the item
@@ -383,66 +385,53 @@ struct ListItem {
   uint32_t hl;       // (last rank of the item + 1) << 1
 };
 
-__device__ __forceinline__ void list_append(const ListItem& li, uint32_t x, uint32_t i) {
+// Queue a neighbour whose cursor c (row end en, edge sign s1) stopped at entry
+// x, unless x lies past the item.
+__device__ __forceinline__ void list_append(const ListItem& li, uint32_t x, uint32_t c, uint32_t en, uint32_t s1) {
   if (x < li.hl) {
     const uint32_t r = ((x >> 1) - li.lo) / li.H;
     const int pos = atomicAdd(&li.cnt[r], 1);
-    li.lists[(size_t)r * li.L + (uint32_t)pos] = i;
+    li.lists[(size_t)r * li.L + (uint32_t)pos] = make_uint2(c, (en - c) | (s1 << 31));
   }
 }
 
 // One window of a list-mode item: groups of G lanes take the listed
 // neighbours j = gid, gid + groups, ... of `list` (n of them), walk each from
 // its cursor like sweep_window, then requeue it by its first entry past the
-// window. The next listed neighbour and its cursor are loaded while the
-// current one is walked (the list, cursor, entry loads form a chain, so one
-// stage ahead beats loading several neighbours at once here).
+// window. The next listed slot is loaded while the current one is walked.
 template <int G, bool PACK16>
-__device__ __forceinline__ void list_window(const CsrView& g, const PivotGeom& q, uint32_t* cur, const ListItem& li,
-                                            const uint32_t* list, uint32_t n, uint32_t lo, uint32_t hl,
-                                            uint32_t* c16, unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
+__device__ __forceinline__ void list_window(const CsrView& g, const ListItem& li, const uint2* list, uint32_t n,
+                                            uint32_t lo, uint32_t hl, uint32_t* c16, unsigned long long* c32,
+                                            uint64_t& bal, uint64_t& unb) {
   const int gl = threadIdx.x & (G - 1);
   const uint32_t gid = threadIdx.x / G;
   constexpr uint32_t groups = kSweepThreads / G;
   const uint32_t lo2 = lo << 1;
   const uint32_t* col = g.col;
-  uint32_t i_nx = 0, c_nx = 0, en_nx = 0, s1_nx = 0;
-  if (gid < n) {
-    i_nx = list[gid];
-    c_nx = cur[2 * i_nx];
-    en_nx = cur[2 * i_nx + 1];
-    s1_nx = col[q.rb + i_nx] & 1u;
-  }
+  uint2 e_nx = make_uint2(0u, 0u);
+  if (gid < n) e_nx = list[gid];
   for (uint32_t j = gid; __any_sync(kFullMask, j < n); j += groups) {
     const bool active = j < n;
-    const uint32_t i = i_nx, c0 = c_nx, en = en_nx, s1 = s1_nx;
-    if (j + groups < n) {
-      i_nx = list[j + groups];
-      c_nx = cur[2 * i_nx];
-      en_nx = cur[2 * i_nx + 1];
-      s1_nx = col[q.rb + i_nx] & 1u;
-    }
+    const uint32_t c0 = e_nx.x, en = e_nx.x + (e_nx.y & 0x7FFFFFFFu), s1 = e_nx.y >> 31;
+    if (j + groups < n) e_nx = list[j + groups];
     uint32_t x[kSweepUnroll];
     load_chunk<G>(col, c0, active ? en : c0, gl, x);
     const uint32_t c = walk_segment<G, PACK16>(col, c0, en, s1, x, lo2, hl, gl, active, c16, c32, bal, unb);
-    if (active && gl == 0) {
-      cur[2 * i] = c;
-      if (c < en) list_append(li, col[c], i);
-    }
+    if (active && gl == 0 && c < en) list_append(li, col[c], c, en, s1);
   }
 }
 
 template <bool PACK16>
-__device__ __forceinline__ void list_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
-                                                     uint32_t* cur, const ListItem& li, const uint32_t* list,
-                                                     uint32_t n, uint32_t lo, uint32_t hl, uint32_t* c16,
-                                                     unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
+__device__ __forceinline__ void list_window_dispatch(int group_log, const CsrView& g, const ListItem& li,
+                                                     const uint2* list, uint32_t n, uint32_t lo, uint32_t hl,
+                                                     uint32_t* c16, unsigned long long* c32, uint64_t& bal,
+                                                     uint64_t& unb) {
   switch (group_log) {
-    case 0: list_window<1, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    case 2: list_window<4, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    case 3: list_window<8, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    case 4: list_window<16, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    default: list_window<32, PACK16>(g, q, cur, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 0: list_window<1, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 2: list_window<4, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 3: list_window<8, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 4: list_window<16, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    default: list_window<32, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
   }
 }
 
