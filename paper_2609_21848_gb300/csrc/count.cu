@@ -89,8 +89,9 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
 // ------------------------------------------------------------------ hub tier
 // Items are pulled dynamically in descending estimated work (LPT). An item in
 // list mode (count_device.cuh) uses per-window neighbour lists in `lists`
-// (list_cap slots per CTA); with no room for them (list_cap too small) it is
-// swept by cursors like every other item, which gives the same counts.
+// (list_cap slots per CTA); with no room for them (list_cap below three slots
+// per lower neighbour) it is swept by cursors like every other item, which
+// gives the same counts.
 __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
                                                                       int64_t n_items, int* next_item,
                                                                       uint32_t* __restrict__ cursors, int64_t cur_cap,
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
   unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
   __shared__ int item_sh;
   __shared__ int cnt[kListMaxWindows];
+  __shared__ int ocnt[2];
   const int tid = threadIdx.x;
   zero_words(c16, kSweepWindow16);
   uint32_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
@@ -109,7 +111,6 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
   uint64_t bal = 0, unb = 0, n_visits = 0;
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
-    if (tid < kListMaxWindows) cnt[tid] = 0;
     __syncthreads();  // also orders the zeroing above / below before reuse
     const int64_t it = item_sh;
     __syncthreads();
@@ -119,31 +120,64 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     const bool wide = (item.flags & kItemWide) != 0;
     const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
     const uint32_t R = (item.hi - item.lo + H - 1) / H;
-    const bool listed = (item.flags & kItemList) != 0 && my_lists != nullptr && R <= (uint32_t)kListMaxWindows &&
-                        (int64_t)R * q.L <= list_cap;
-    const ListItem li{my_lists, cnt, q.L, item.lo, H, item.hi << 1};
-    // cursors; in list mode each neighbour also joins the list of the window
-    // of its first entry
+    // list scratch per item: Rsub window lists + two overflow lists of L slots
+    const int64_t per_nb = q.L ? list_cap / (int64_t)q.L : 0;
+    const bool listed = (item.flags & kItemList) != 0 && my_lists != nullptr && per_nb >= 3;
+    if (listed) {
+      const uint32_t Rsub = (uint32_t)(per_nb - 2 < kListMaxWindows ? per_nb - 2 : kListMaxWindows);
+      int in_buf = 0;  // overflow list feeding the next span
+      for (uint32_t s0 = 0; s0 < R; s0 += Rsub) {
+        const uint32_t nwin = min(Rsub, R - s0);
+        const uint32_t span_lo = item.lo + s0 * H;
+        const uint32_t span_hi = min(item.hi, span_lo + nwin * H);
+        if (tid < kListMaxWindows) cnt[tid] = 0;
+        if (tid == 0) ocnt[in_buf ^ 1] = 0;
+        __syncthreads();
+        const ListItem li{my_lists, cnt, my_lists + (size_t)(Rsub + (in_buf ^ 1)) * q.L, &ocnt[in_buf ^ 1], q.L,
+                          span_lo, H, span_hi << 1, item.hi << 1};
+        if (s0 == 0) {  // each neighbour joins the list of the window of its first entry
+          for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
+            uint32_t b, en;
+            init_cursor(g, q, i, item.lo, cur, b, en);
+            if (b < en) list_append(li, g.col[b], b, en, g.col[q.rb + i] & 1u);
+          }
+        } else {  // the neighbours that waited for this span
+          const uint32_t n_in = (uint32_t)ocnt[in_buf];
+          const uint2* in = my_lists + (size_t)(Rsub + in_buf) * q.L;
+          for (uint32_t j = tid; j < n_in; j += kSweepThreads) {
+            const uint2 e = in[j];
+            const uint32_t c = e.x, en = e.x + (e.y & 0x7FFFFFFFu);
+            list_append(li, g.col[c], c, en, e.y >> 31);
+          }
+        }
+        __syncthreads();
+        for (uint32_t r = 0; r < nwin; r++) {
+          const uint32_t lo = span_lo + r * H;
+          const uint32_t hi = min(lo + H, span_hi);
+          const uint32_t n = (uint32_t)cnt[r];
+          const uint2* list = my_lists + (size_t)r * q.L;
+          if (wide) list_window_dispatch<false>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+          else list_window_dispatch<true>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+          n_visits += tid == 0 ? n : 0;
+          __syncthreads();  // also publishes the appends made to later windows' lists
+          zero_words(c16, wide ? 2 * (hi - lo) : (hi - lo));
+          __syncthreads();
+        }
+        in_buf ^= 1;
+      }
+      continue;
+    }
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en;
       init_cursor(g, q, i, item.lo, cur, b, en);
-      if (listed && b < en) list_append(li, g.col[b], b, en, g.col[q.rb + i] & 1u);
     }
     __syncthreads();
     for (uint32_t r = 0; r < R; r++) {
       const uint32_t lo = item.lo + r * H;
       const uint32_t hi = min(lo + H, item.hi);
-      if (listed) {
-        const uint32_t n = (uint32_t)cnt[r];
-        const uint2* list = my_lists + (size_t)r * q.L;
-        if (wide) list_window_dispatch<false>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
-        else list_window_dispatch<true>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
-        n_visits += tid == 0 ? n : 0;
-      } else {
-        if (wide) sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-        else sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      }
-      __syncthreads();  // also publishes the appends made to later windows' lists
+      if (wide) sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      else sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      __syncthreads();
       const uint32_t words = wide ? 2 * (hi - lo) : (hi - lo);  // 32-bit words to clear
       zero_words(c16, words);
       __syncthreads();

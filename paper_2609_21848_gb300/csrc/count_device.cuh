@@ -376,22 +376,35 @@ __device__ __forceinline__ void init_cursor(const CsrView& g, const PivotGeom& q
 // its next entry (always a later window), or drops out at the end of its row
 // or of the item. Each neighbour is in at most one list at a time and in each
 // list at most once, so L slots per window never overflow.
+// An item in list mode runs as consecutive spans of at most `Rsub` windows
+// (so that the lists of a span fit the CTA's list scratch). A neighbour whose
+// next entry lies past the current span but inside the item waits in an
+// overflow list and is queued into the next span's windows when that span
+// starts, so each neighbour's row is searched only once per item.
 struct ListItem {
   uint2* lists;      // [windows][L] {cursor, entries left | sign << 31}
   int* cnt;          // [windows] list lengths (shared memory)
+  uint2* over;       // [L] neighbours waiting for a later span
+  int* ocnt;         // their count (shared memory)
   uint32_t L;
-  uint32_t lo;       // first rank of the item
+  uint32_t lo;       // first rank of the span
   uint32_t H;        // ranks per window
-  uint32_t hl;       // (last rank of the item + 1) << 1
+  uint32_t hl;       // (last rank of the span + 1) << 1
+  uint32_t item_hl;  // (last rank of the item + 1) << 1
 };
 
 // Queue a neighbour whose cursor c (row end en, edge sign s1) stopped at entry
-// x, unless x lies past the item.
+// x: into the list of x's window in this span, into the overflow list if x
+// lies in a later span of the item, else nowhere (the neighbour is done).
 __device__ __forceinline__ void list_append(const ListItem& li, uint32_t x, uint32_t c, uint32_t en, uint32_t s1) {
+  const uint2 slot = make_uint2(c, (en - c) | (s1 << 31));
   if (x < li.hl) {
     const uint32_t r = ((x >> 1) - li.lo) / li.H;
     const int pos = atomicAdd(&li.cnt[r], 1);
-    li.lists[(size_t)r * li.L + (uint32_t)pos] = make_uint2(c, (en - c) | (s1 << 31));
+    li.lists[(size_t)r * li.L + (uint32_t)pos] = slot;
+  } else if (x < li.item_hl) {
+    const int pos = atomicAdd(li.ocnt, 1);
+    li.over[pos] = slot;
   }
 }
 

@@ -50,8 +50,9 @@ constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per wor
 #define DBBC_GROUP_T4 2
 #endif
 constexpr double kGroupThreshold[4] = {DBBC_GROUP_T32, DBBC_GROUP_T16, DBBC_GROUP_T8, DBBC_GROUP_T4};
-// Hub items in list mode (see count_device.cuh): at most this many windows per
-// item, and at most kListCapEntries (window, neighbour) list slots per CTA.
+// Hub items in list mode (see count_device.cuh) run in spans of at most
+// kListMaxWindows windows, with at most kListCapEntries list slots (8 bytes
+// each) per CTA.
 constexpr int kListMaxWindows = 64;
 constexpr int64_t kListCapEntries = int64_t{1} << 22;
 

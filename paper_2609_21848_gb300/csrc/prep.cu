@@ -453,10 +453,12 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
     const double density = (double)W / ((double)L * (double)std::max<uint64_t>(1, Rn + Rw));
     const double* gd = g->tune.group_density;
     const int16_t dense_log = density >= gd[0] ? 5 : density >= gd[1] ? 4 : density >= gd[2] ? 3 : density >= gd[3] ? 2 : 0;
-    // sparse hubs sweep in list mode, with items of at most Rcap windows so
-    // that their lists (windows x L slots) fit the per-CTA list scratch
-    const uint64_t Rcap = std::min<uint64_t>(kListMaxWindows, (uint64_t)kListCapEntries / std::max<uint32_t>(L, 1));
-    const bool listed = density < g->tune.list_density && Rcap >= 2 && Rn + Rw >= 2;
+    // sparse hubs sweep in list mode: one item per counter width, run in
+    // spans of at most Rsub windows whose lists (plus two overflow lists of
+    // L slots) fit the per-CTA list scratch
+    const uint64_t per_nb = (uint64_t)kListCapEntries / std::max<uint32_t>(L, 1);
+    const uint64_t Rsub = per_nb >= 3 ? std::min<uint64_t>(kListMaxWindows, per_nb - 2) : 0;
+    const bool listed = density < g->tune.list_density && Rsub >= 1 && Rn + Rw >= 2;
     const int16_t group_log = listed ? (int16_t)g->tune.list_group_log : dense_log;
     const int16_t list_flag = listed ? kItemList : 0;
     auto add = [&](uint64_t lo, uint64_t hi, uint64_t H, int16_t flags, uint64_t est) {
@@ -470,24 +472,18 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
       plan.push_back(p);
       const int64_t R = (int64_t)((hi - lo + H - 1) / H);
       g->hub_cursor_inits += L;
-      if (listed) g->sweep_list_cap = std::max<int64_t>(g->sweep_list_cap, R * (int64_t)L);
+      if (listed)
+        g->sweep_list_cap = std::max<int64_t>(g->sweep_list_cap, (std::min<int64_t>(R, (int64_t)Rsub) + 2) * (int64_t)L);
       else g->hub_cursor_steps += (int64_t)L * R;
     };
-    uint64_t spans = std::max<uint64_t>(1, std::min<uint64_t>(Rn, W / target));
-    if (listed) spans = std::max<uint64_t>(spans, (Rn + Rcap - 1) / Rcap);
+    const uint64_t spans = listed ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(Rn, W / target));
     for (uint64_t k = 0; k < spans && Rn > 0; k++) {
       const uint64_t w0 = Rn * k / spans, w1 = Rn * (k + 1) / spans;
       if (w1 > w0)
         add(start + w0 * kSweepWindow16, std::min<uint64_t>(narrow_end, start + w1 * kSweepWindow16),
             kSweepWindow16, 0, W / spans);
     }
-    const uint64_t wspans = listed ? (Rw + Rcap - 1) / Rcap : 1;
-    for (uint64_t k = 0; k < wspans && sp > narrow_end; k++) {
-      const uint64_t w0 = Rw * k / wspans, w1 = Rw * (k + 1) / wspans;
-      if (w1 > w0)
-        add(narrow_end + w0 * kSweepWindow32, std::min<uint64_t>(sp, narrow_end + w1 * kSweepWindow32),
-            kSweepWindow32, kItemWide, W / (spans + 1) / wspans);
-    }
+    if (sp > narrow_end) add(narrow_end, sp, kSweepWindow32, kItemWide, W / (spans + 1));
   }
   std::stable_sort(plan.begin(), plan.end(), [](const Planned& a, const Planned& b) { return a.est > b.est; });
   std::vector<SweepItem> items(plan.size());
