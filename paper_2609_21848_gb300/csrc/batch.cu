@@ -196,8 +196,8 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     const SweepItem item = bi.it;
     const CsrView g = view_of(desc[bi.graph]);
     const PivotGeom q = pivot_geom(g, item.row);
-    const bool wide = (item.flags & kItemWide) != 0;
-    const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
+    const int cw = item_width(item.flags);
+    const uint32_t H = item_window(cw);
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en;
       init_cursor(g, q, i, item.lo, cur, b, en);
@@ -206,11 +206,11 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     uint64_t bal = 0, unb = 0;
     for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
       const uint32_t hi = min(lo + H, item.hi);
-      if (wide) sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      else sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      if (cw == 8) sweep_window_dispatch<8>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      else if (cw == 16) sweep_window_dispatch<16>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      else sweep_window_dispatch<32>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
       __syncthreads();
-      const uint32_t words = wide ? 2 * (hi - lo) : (hi - lo);
-      zero_words(c16, words);
+      zero_words(c16, item_words(cw, hi - lo));
       __syncthreads();
     }
     block_add_pair<kSweepThreads>(bal, unb, out + 2 * bi.graph);

@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     if (it >= n_items) break;
     const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    const bool wide = (item.flags & kItemWide) != 0;
-    const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
+    const int cw = item_width(item.flags);
+    const uint32_t H = item_window(cw);
     const uint32_t R = (item.hi - item.lo + H - 1) / H;
     // list scratch per item: Rsub window lists + two overflow lists of L slots
     const int64_t per_nb = q.L ? list_cap / (int64_t)q.L : 0;
@@ -156,11 +156,12 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
           const uint32_t hi = min(lo + H, span_hi);
           const uint32_t n = (uint32_t)cnt[r];
           const uint2* list = my_lists + (size_t)r * q.L;
-          if (wide) list_window_dispatch<false>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
-          else list_window_dispatch<true>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+          if (cw == 8) list_window_dispatch<8>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+          else if (cw == 16) list_window_dispatch<16>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+          else list_window_dispatch<32>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
           n_visits += tid == 0 ? n : 0;
           __syncthreads();  // also publishes the appends made to later windows' lists
-          zero_words(c16, wide ? 2 * (hi - lo) : (hi - lo));
+          zero_words(c16, item_words(cw, hi - lo));
           __syncthreads();
         }
         in_buf ^= 1;
@@ -175,11 +176,11 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     for (uint32_t r = 0; r < R; r++) {
       const uint32_t lo = item.lo + r * H;
       const uint32_t hi = min(lo + H, item.hi);
-      if (wide) sweep_window_dispatch<false>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      else sweep_window_dispatch<true>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      if (cw == 8) sweep_window_dispatch<8>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      else if (cw == 16) sweep_window_dispatch<16>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
+      else sweep_window_dispatch<32>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
       __syncthreads();
-      const uint32_t words = wide ? 2 * (hi - lo) : (hi - lo);  // 32-bit words to clear
-      zero_words(c16, words);
+      zero_words(c16, item_words(cw, hi - lo));
       __syncthreads();
     }
   }

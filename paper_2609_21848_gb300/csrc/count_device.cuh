@@ -235,20 +235,76 @@ __device__ __forceinline__ void load_chunk(const uint32_t* col, uint32_t c, uint
   }
 }
 
+// Counter widths of a window. CW = 16: one 32-bit word per endpoint packing
+// (asym << 16) | sym, kSweepWindow16 ranks per window. CW = 8: two endpoints
+// per 32-bit word, each (asym << 8) | sym, twice the ranks per window; used
+// where every endpoint has degree < 256 or the hub has fewer than 256 lower
+// neighbours (a count never exceeds either). CW = 32: one 64-bit word per
+// endpoint, half the ranks.
+template <int CW>
+__host__ __device__ constexpr uint32_t window_ranks() {
+  return CW == 8 ? 2 * kSweepWindow16 : CW == 16 ? kSweepWindow16 : kSweepWindow32;
+}
+
+template <int CW>
+__device__ __forceinline__ uint32_t window_words(uint32_t ranks) {  // 32-bit words holding `ranks` counters
+  return CW == 8 ? (ranks + 1) >> 1 : CW == 16 ? ranks : 2 * ranks;
+}
+
+// Counter width of a work item, its ranks per window, and the 32-bit words
+// holding `ranks` of its counters.
+__device__ __forceinline__ int item_width(int16_t flags) {
+  return (flags & kItemTiny) ? 8 : (flags & kItemWide) ? 32 : 16;
+}
+__device__ __forceinline__ uint32_t item_window(int cw) {
+  return cw == 8 ? window_ranks<8>() : cw == 16 ? window_ranks<16>() : window_ranks<32>();
+}
+__device__ __forceinline__ uint32_t item_words(int cw, uint32_t ranks) {
+  return cw == 8 ? window_words<8>(ranks) : cw == 16 ? window_words<16>(ranks) : window_words<32>(ranks);
+}
+
+// Add one wedge (endpoint counter k, asym = the two edge signs differ) when
+// `ok`, and accumulate its Lemma 1 contribution from the counter's old value:
+// the old count of the wedge's own class (B1 for a symmetric wedge, B2 for an
+// asymmetric one) closes balanced butterflies and the other class unbalanced
+// ones. Packed counters are rotated for an asymmetric wedge so that its own
+// class sits in the low half. Narrow widths sum into 32-bit accumulators (a
+// segment adds fewer than 2^32 to each); the 64-bit width adds directly.
+template <int CW>
+__device__ __forceinline__ void add_wedge(bool ok, uint32_t k, uint32_t asym, uint32_t* c16, unsigned long long* c32,
+                                          uint32_t& acc_same, uint32_t& acc_other, uint64_t& bal, uint64_t& unb) {
+  if (CW == 8) {
+    const uint32_t wsh = (k & 1u) << 4;  // which half of the word
+    uint32_t old = 0;
+    if (ok) old = atomicAdd(&c16[k >> 1], (asym ? 0x100u : 1u) << wsh);
+    const uint32_t v = (old >> wsh) & 0xFFFFu;            // (asym << 8) | sym
+    const uint32_t r = ((v << 16) | v) >> (asym << 3);  // own class in the low byte
+    acc_same += r & 0xFFu;
+    acc_other += (r >> 8) & 0xFFu;
+  } else if (CW == 16) {
+    const uint32_t sh = asym << 4;
+    uint32_t old = 0;
+    if (ok) old = atomicAdd(&c16[k], 1u << sh);
+    const uint32_t v = __funnelshift_l(old, old, sh);  // (other class << 16) | own class
+    acc_same += v & 0xFFFFu;
+    acc_other += v >> 16;
+  } else {
+    const unsigned long long inc = asym ? (1ull << 32) : 1ull;
+    unsigned long long old = 0;
+    if (ok) old = atomicAdd(&c32[k], inc);
+    wedge_contrib(old, inc, bal, unb);  // adds nothing when old == 0
+  }
+}
+
 // A group of G lanes walks one neighbour's entries inside the window [lo,
 // hl >> 1) from cursor c (the first chunk already in x) and returns the cursor
 // past the window. Entries of the window are a prefix of what is left of the
 // row, so the group stops at the first chunk that is not full. All groups of a
 // warp run the loop in lockstep until the last of them is done (warp-wide
 // votes, the atomic the only predicated step), which keeps the warp converged;
-// a group that is not `active` (no neighbour) only votes.
-// Narrow counters: the old value of the wedge's own class (B1 for a symmetric
-// wedge, B2 for an asymmetric one) closes balanced butterflies and the other
-// class unbalanced ones (Lemma 1, incremental); rotating the packed counter by
-// 16 bits for an asymmetric wedge puts its own class in the low half. One
-// segment adds fewer than 2^32 to each (< 57344 wedges, each < 2^16), so the
-// sums run in 32 bits and are added once per segment.
-template <int G, bool PACK16>
+// a group that is not `active` (no neighbour) only votes. Contributions of
+// the narrow widths are summed per segment in 32 bits (add_wedge).
+template <int G, int CW>
 __device__ __forceinline__ uint32_t walk_segment(const uint32_t* col, uint32_t c, uint32_t en, uint32_t s1,
                                                  uint32_t (&x)[kSweepUnroll], uint32_t lo2, uint32_t hl, int gl,
                                                  bool active, uint32_t* c16, unsigned long long* c32,
@@ -263,19 +319,7 @@ __device__ __forceinline__ uint32_t walk_segment(const uint32_t* col, uint32_t c
       const bool ok = active && x[u] < hl;
       const uint32_t asym = (x[u] ^ s1) & 1u;
       const uint32_t k = (x[u] - lo2) >> 1;
-      if (PACK16) {
-        const uint32_t sh = asym << 4;
-        uint32_t old = 0;
-        if (ok) old = atomicAdd(&c16[k], 1u << sh);
-        const uint32_t v = __funnelshift_l(old, old, sh);  // (other class << 16) | own class
-        acc_same += v & 0xFFFFu;
-        acc_other += v >> 16;
-      } else {
-        const unsigned long long inc = asym ? (1ull << 32) : 1ull;
-        unsigned long long old = 0;
-        if (ok) old = atomicAdd(&c32[k], inc);
-        wedge_contrib(old, inc, bal, unb);  // adds nothing when old == 0
-      }
+      add_wedge<CW>(ok, k, asym, c16, c32, acc_same, acc_other, bal, unb);
       n_ok += __popc((__ballot_sync(kFullMask, ok) >> gshift) & gbits);
     }
     c += (uint32_t)n_ok;
@@ -294,7 +338,7 @@ __device__ __forceinline__ uint32_t walk_segment(const uint32_t* col, uint32_t c
 // and issues all their cursor loads, then all their first-chunk loads, before
 // walking any of them, so that kSweepBatch dependent load chains are in flight
 // per group instead of one. Warps loop in lockstep (see walk_segment).
-template <int G, bool PACK16>
+template <int G, int CW>
 __device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& q, uint32_t* cur, uint32_t lo,
                                              uint32_t hl, uint32_t* c16, unsigned long long* c32, uint64_t& bal,
                                              uint64_t& unb) {
@@ -322,22 +366,22 @@ __device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& 
       const uint32_t i = i0 + k * groups;
       const bool active = i < q.L;
       const uint32_t cn =
-          walk_segment<G, PACK16>(col, c[k], en[k], s1[k], x[k], lo2, hl, gl, active, c16, c32, bal, unb);
+          walk_segment<G, CW>(col, c[k], en[k], s1[k], x[k], lo2, hl, gl, active, c16, c32, bal, unb);
       if (active && gl == 0 && cn != c[k]) cur[2 * i] = cn;
     }
   }
 }
 
-template <bool PACK16>
+template <int CW>
 __device__ __forceinline__ void sweep_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
                                                       uint32_t* cur, uint32_t lo, uint32_t hl, uint32_t* c16,
                                                       unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
   switch (group_log) {
-    case 0: sweep_window<1, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
-    case 2: sweep_window<4, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
-    case 3: sweep_window<8, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
-    case 4: sweep_window<16, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
-    default: sweep_window<32, PACK16>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 0: sweep_window<1, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 2: sweep_window<4, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 3: sweep_window<8, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    case 4: sweep_window<16, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
+    default: sweep_window<32, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
   }
 }
 
@@ -412,7 +456,7 @@ __device__ __forceinline__ void list_append(const ListItem& li, uint32_t x, uint
 // neighbours j = gid, gid + groups, ... of `list` (n of them), walk each from
 // its cursor like sweep_window, then requeue it by its first entry past the
 // window. The next listed slot is loaded while the current one is walked.
-template <int G, bool PACK16>
+template <int G, int CW>
 __device__ __forceinline__ void list_window(const CsrView& g, const ListItem& li, const uint2* list, uint32_t n,
                                             uint32_t lo, uint32_t hl, uint32_t* c16, unsigned long long* c32,
                                             uint64_t& bal, uint64_t& unb) {
@@ -429,22 +473,22 @@ __device__ __forceinline__ void list_window(const CsrView& g, const ListItem& li
     if (j + groups < n) e_nx = list[j + groups];
     uint32_t x[kSweepUnroll];
     load_chunk<G>(col, c0, active ? en : c0, gl, x);
-    const uint32_t c = walk_segment<G, PACK16>(col, c0, en, s1, x, lo2, hl, gl, active, c16, c32, bal, unb);
+    const uint32_t c = walk_segment<G, CW>(col, c0, en, s1, x, lo2, hl, gl, active, c16, c32, bal, unb);
     if (active && gl == 0 && c < en) list_append(li, col[c], c, en, s1);
   }
 }
 
-template <bool PACK16>
+template <int CW>
 __device__ __forceinline__ void list_window_dispatch(int group_log, const CsrView& g, const ListItem& li,
                                                      const uint2* list, uint32_t n, uint32_t lo, uint32_t hl,
                                                      uint32_t* c16, unsigned long long* c32, uint64_t& bal,
                                                      uint64_t& unb) {
   switch (group_log) {
-    case 0: list_window<1, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    case 2: list_window<4, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    case 3: list_window<8, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    case 4: list_window<16, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    default: list_window<32, PACK16>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 0: list_window<1, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 2: list_window<4, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 3: list_window<8, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    case 4: list_window<16, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
+    default: list_window<32, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
   }
 }
 

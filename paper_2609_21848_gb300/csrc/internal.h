@@ -85,6 +85,9 @@ struct SweepItem {
 };
 constexpr int16_t kItemWide = 1;  // 32-bit counter halves (kSweepWindow32 ranks per window)
 constexpr int16_t kItemList = 2;  // list mode: visit a neighbour only in windows holding its entries
+constexpr int16_t kItemTiny = 4;  // 8-bit counter halves (2 * kSweepWindow16 ranks per window)
+// Counts below this fit the 8-bit halves of a tiny counter.
+constexpr int32_t kTinyCountLimit = 256;
 
 // Read-only view of the device CSR passed to kernels by value.
 // Rows [0, n_u) are U vertices in ascending Def. 3 priority, rows [n_u, n)
@@ -133,6 +136,7 @@ struct dbbc_graph {
   int64_t sweep_max_lower = 0;  // largest lower-neighbour count of a hub (cursor scratch per CTA)
   int64_t sweep_list_cap = 0;   // largest windows x lower neighbours of a list-mode item (list slots per CTA)
   int64_t narrow_ranks_u = 0, narrow_ranks_v = 0;  // per side: vertices of degree < 2^16 (a rank prefix)
+  int64_t tiny_ranks_u = 0, tiny_ranks_v = 0;      // per side: vertices of degree < 2^8 (a rank prefix)
   // disjoint union of several graphs (dbbc_graph_from_coo_multi): component
   // of every row, 0 for a plain handle (n_components == 1)
   int32_t n_components = 1;

@@ -310,10 +310,14 @@ __global__ void pivot_keys_kernel(const uint64_t* __restrict__ work, const uint3
   }
 }
 
-__global__ void narrow_ranks_kernel(const int32_t* __restrict__ rowdeg, int64_t n, int32_t n_u, int32_t limit,
-                                    int64_t* out) {
-  if (threadIdx.x == 0) out[0] = lower_bound_dev<int32_t>(rowdeg, n_u, limit);
-  if (threadIdx.x == 1) out[1] = lower_bound_dev<int32_t>(rowdeg + n_u, n - n_u, limit);
+// Per side, how many vertices have degree below `narrow` and below `tiny`
+// (ranks ascend by degree within a side).
+__global__ void narrow_ranks_kernel(const int32_t* __restrict__ rowdeg, int64_t n, int32_t n_u, int32_t narrow,
+                                    int32_t tiny, int64_t* out) {
+  if (threadIdx.x == 0) out[0] = lower_bound_dev<int32_t>(rowdeg, n_u, narrow);
+  if (threadIdx.x == 1) out[1] = lower_bound_dev<int32_t>(rowdeg + n_u, n - n_u, narrow);
+  if (threadIdx.x == 2) out[2] = lower_bound_dev<int32_t>(rowdeg, n_u, tiny);
+  if (threadIdx.x == 3) out[3] = lower_bound_dev<int32_t>(rowdeg + n_u, n - n_u, tiny);
 }
 
 // Union of several graphs: graph i's local ids are validated against its own
@@ -438,19 +442,31 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
     const std::vector<int64_t>& off = is_u ? un.uoff : un.voff;
     const uint64_t start =
         (uint64_t)off[(size_t)(std::upper_bound(off.begin(), off.end(), (int64_t)sp) - off.begin() - 1)];
-    // narrow counters below the side's first endpoint of degree >= 2^16 (for
-    // a union, whose ranks are component-major, only when every count fits)
+    // counter widths by the counts they must hold: a count never exceeds the
+    // endpoint's degree nor the hub's lower-neighbour count L. Ranks ascend by
+    // degree, so tiny (8-bit halves) counters serve the ranks below the side's
+    // first endpoint of degree >= 2^8 and narrow (16-bit) ones those below
+    // degree 2^16; for a union, whose ranks are component-major, only L bounds
+    // the counts.
+    auto clamp_rank = [&](int64_t x) {
+      return std::max<uint64_t>(start, std::min<uint64_t>(sp, (uint64_t)std::max<int64_t>(x, 0)));
+    };
+    const uint64_t tiny_end = L < (uint32_t)kTinyCountLimit ? sp
+                              : un.n_graphs > 1            ? start
+                                                           : clamp_rank(is_u ? g->tiny_ranks_u : g->tiny_ranks_v);
     const uint64_t narrow_end =
         L < (uint32_t)kNarrowCountLimit ? sp
-        : un.n_graphs > 1               ? start
-                                        : std::max<uint64_t>(start, std::min<uint64_t>(
-                                              sp, (uint64_t)(is_u ? g->narrow_ranks_u : g->narrow_ranks_v)));
-    const uint64_t Rn = (narrow_end - start + kSweepWindow16 - 1) / kSweepWindow16;
+        : un.n_graphs > 1               ? tiny_end
+                                        : std::max<uint64_t>(tiny_end,
+                                                             clamp_rank(is_u ? g->narrow_ranks_u : g->narrow_ranks_v));
+    const uint64_t H8 = 2ull * kSweepWindow16;
+    const uint64_t Rt = (tiny_end - start + H8 - 1) / H8;
+    const uint64_t Rn = (narrow_end - tiny_end + kSweepWindow16 - 1) / kSweepWindow16;
     const uint64_t Rw = (sp - narrow_end + kSweepWindow32 - 1) / kSweepWindow32;
     const uint64_t target = std::max<uint64_t>(g->tune.hub_item_work, 64ull * L);
     max_lower = std::max<int64_t>(max_lower, L);
     // lanes per (neighbour, window) segment from the hub's mean segment length
-    const double density = (double)W / ((double)L * (double)std::max<uint64_t>(1, Rn + Rw));
+    const double density = (double)W / ((double)L * (double)std::max<uint64_t>(1, Rt + Rn + Rw));
     const double* gd = g->tune.group_density;
     const int16_t dense_log = density >= gd[0] ? 5 : density >= gd[1] ? 4 : density >= gd[2] ? 3 : density >= gd[3] ? 2 : 0;
     // sparse hubs sweep in list mode: one item per counter width, run in
@@ -458,7 +474,7 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
     // L slots) fit the per-CTA list scratch
     const uint64_t per_nb = (uint64_t)kListCapEntries / std::max<uint32_t>(L, 1);
     const uint64_t Rsub = per_nb >= 3 ? std::min<uint64_t>(kListMaxWindows, per_nb - 2) : 0;
-    const bool listed = density < g->tune.list_density && Rsub >= 1 && Rn + Rw >= 2;
+    const bool listed = density < g->tune.list_density && Rsub >= 1 && Rt + Rn + Rw >= 2;
     const int16_t group_log = listed ? (int16_t)g->tune.list_group_log : dense_log;
     const int16_t list_flag = listed ? kItemList : 0;
     auto add = [&](uint64_t lo, uint64_t hi, uint64_t H, int16_t flags, uint64_t est) {
@@ -476,14 +492,21 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
         g->sweep_list_cap = std::max<int64_t>(g->sweep_list_cap, (std::min<int64_t>(R, (int64_t)Rsub) + 2) * (int64_t)L);
       else g->hub_cursor_steps += (int64_t)L * R;
     };
-    const uint64_t spans = listed ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(Rn, W / target));
-    for (uint64_t k = 0; k < spans && Rn > 0; k++) {
-      const uint64_t w0 = Rn * k / spans, w1 = Rn * (k + 1) / spans;
-      if (w1 > w0)
-        add(start + w0 * kSweepWindow16, std::min<uint64_t>(narrow_end, start + w1 * kSweepWindow16),
-            kSweepWindow16, 0, W / spans);
-    }
-    if (sp > narrow_end) add(narrow_end, sp, kSweepWindow32, kItemWide, W / (spans + 1));
+    // each width's part in items of roughly `target` wedges (one item in list
+    // mode), the work estimated in proportion to the part's windows
+    const uint64_t R_all = std::max<uint64_t>(1, Rt + Rn + Rw);
+    auto add_part = [&](uint64_t lo, uint64_t hi, uint64_t H, uint64_t R, int16_t flags) {
+      if (R == 0) return;
+      const uint64_t Wp = W * R / R_all;
+      const uint64_t spans = listed ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(R, Wp / target));
+      for (uint64_t k = 0; k < spans; k++) {
+        const uint64_t w0 = R * k / spans, w1 = R * (k + 1) / spans;
+        if (w1 > w0) add(lo + w0 * H, std::min<uint64_t>(hi, lo + w1 * H), H, flags, std::max<uint64_t>(1, Wp / spans));
+      }
+    };
+    add_part(start, tiny_end, H8, Rt, kItemTiny);
+    add_part(tiny_end, narrow_end, kSweepWindow16, Rn, 0);
+    add_part(narrow_end, sp, kSweepWindow32, Rw, kItemWide);
   }
   std::stable_sort(plan.begin(), plan.end(), [](const Planned& a, const Planned& b) { return a.est > b.est; });
   std::vector<SweepItem> items(plan.size());
@@ -772,16 +795,18 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
     if (alt)
       DBBC_CUDA(cudaMemcpyAsync(pr0, pr1, (size_t)g->n_piv * 4, cudaMemcpyDeviceToDevice, s));
   }
-  // per side: how many vertices have degree < 2^16 (ranks ascend by degree)
+  // per side: how many vertices have degree < 2^16 and < 2^8 (ranks ascend by degree)
   {
-    int64_t* d_t = sc.get<int64_t>(2);
-    narrow_ranks_kernel<<<1, 32, 0, s>>>(rowdeg, n, n_u, kNarrowCountLimit, d_t);
+    int64_t* d_t = sc.get<int64_t>(4);
+    narrow_ranks_kernel<<<1, 32, 0, s>>>(rowdeg, n, n_u, kNarrowCountLimit, kTinyCountLimit, d_t);
     DBBC_LAUNCH_CHECK();
-    int64_t ht[2];
+    int64_t ht[4];
     DBBC_CUDA(cudaMemcpyAsync(ht, d_t, sizeof(ht), cudaMemcpyDeviceToHost, s));
     DBBC_CUDA(cudaStreamSynchronize(s));
     g->narrow_ranks_u = ht[0];
     g->narrow_ranks_v = ht[1];
+    g->tiny_ranks_u = ht[2];
+    g->tiny_ranks_v = ht[3];
   }
   plan_hubs(g, s, *un);
   DBBC_CUDA(cudaStreamSynchronize(s));

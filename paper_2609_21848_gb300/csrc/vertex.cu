@@ -221,15 +221,15 @@ __global__ void __launch_bounds__(kMediumThreads) tips_medium_kernel(CsrView g, 
 }
 
 // ------------------------------------------------------------------ hub windows
-// Per window of a hub item: count (each lower neighbour's cursor stops at
-// `next`), credit the endpoints and the pivot from the dense window, then walk
-// [pos, next) of every lower neighbour again for the middles and edges and
-// move pos to next. One thread per neighbour segment; cursor state per
-// neighbour: pos, end, next.
-template <bool PACK16>
+// Counter k of a window of width CW (see add_wedge) as (asym << 32) | sym.
+template <int CW>
 __device__ __forceinline__ unsigned long long window_value(const uint32_t* c16, const unsigned long long* c32,
                                                            uint32_t k) {
-  if (PACK16) {
+  if (CW == 8) {
+    const uint32_t v = (c16[k >> 1] >> ((k & 1u) << 4)) & 0xFFFFu;
+    return ((unsigned long long)(v >> 8) << 32) | (v & 0xFFu);
+  }
+  if (CW == 16) {
     const uint32_t v = c16[k];
     return ((unsigned long long)(v >> 16) << 32) | (v & 0xFFFFu);
   }
@@ -242,7 +242,7 @@ __device__ __forceinline__ unsigned long long window_value(const uint32_t* c16, 
 // the window, its old value kept in `prev`), credit endpoints and the pivot
 // from the complete window, then walk every neighbour's segment
 // [prev, cursor) again for the middles and edges.
-template <int G, bool PACK16, bool VERT, bool EDGE>
+template <int G, int CW, bool VERT, bool EDGE>
 __device__ __forceinline__ void tips_window(const CsrView& g, const PivotGeom& q, uint32_t* cur, uint32_t* prev, uint32_t lo,
                             uint32_t hi, uint32_t* c16, unsigned long long* c32, const TipOut& o, uint64_t& pb,
                             uint64_t& pu) {
@@ -258,7 +258,7 @@ __device__ __forceinline__ void tips_window(const CsrView& g, const PivotGeom& q
     const uint32_t s1 = active ? col[q.rb + i] & 1u : 0u;
     uint32_t x[kSweepUnroll];
     load_chunk<G>(col, c, en, gl, x);
-    const uint32_t cn = walk_segment<G, PACK16>(col, c, en, s1, x, lo2, hl, gl, active, c16, c32, unused_b, unused_u);
+    const uint32_t cn = walk_segment<G, CW>(col, c, en, s1, x, lo2, hl, gl, active, c16, c32, unused_b, unused_u);
     if (active && gl == 0) {
       prev[i] = c;
       cur[2 * i] = cn;
@@ -268,7 +268,7 @@ __device__ __forceinline__ void tips_window(const CsrView& g, const PivotGeom& q
   if (VERT) {
     const int64_t end_base = q.base == 0 ? (int64_t)g.n_u : 0;  // endpoints share the pivot's side
     for (uint32_t k = threadIdx.x; k < hi - lo; k += kSweepThreads) {
-      const unsigned long long v = window_value<PACK16>(c16, c32, k);
+      const unsigned long long v = window_value<CW>(c16, c32, k);
       if (v) {
         uint64_t eb = 0, eu = 0;
         endpoint_contrib(v, eb, eu);
@@ -290,7 +290,7 @@ __device__ __forceinline__ void tips_window(const CsrView& g, const PivotGeom& q
       if (pos < c1) {
         const uint32_t xx = col[pos];
         uint64_t cb, cu;
-        wedge_pairs(window_value<PACK16>(c16, c32, (xx - lo2) >> 1), ((xx ^ s1) & 1u) == 0, cb, cu);
+        wedge_pairs(window_value<CW>(c16, c32, (xx - lo2) >> 1), ((xx ^ s1) & 1u) == 0, cb, cu);
         if (EDGE) add_pair(o.eb, o.eu, pos, cb, cu);
         sb += cb;
         su += cu;
@@ -307,21 +307,21 @@ __device__ __forceinline__ void tips_window(const CsrView& g, const PivotGeom& q
     }
   }
   __syncthreads();
-  zero_words(c16, PACK16 ? (hi - lo) : 2 * (hi - lo));
+  zero_words(c16, window_words<CW>(hi - lo));
   __syncthreads();
 }
 
-template <bool PACK16, bool VERT, bool EDGE>
+template <int CW, bool VERT, bool EDGE>
 __device__ __forceinline__ void tips_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
                                                      uint32_t* cur, uint32_t* prev, uint32_t lo, uint32_t hi,
                                                      uint32_t* c16, unsigned long long* c32, const TipOut& o,
                                                      uint64_t& pb, uint64_t& pu) {
   switch (group_log) {
-    case 0: tips_window<1, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
-    case 2: tips_window<4, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
-    case 3: tips_window<8, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
-    case 4: tips_window<16, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
-    default: tips_window<32, PACK16, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+    case 0: tips_window<1, CW, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+    case 2: tips_window<4, CW, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+    case 3: tips_window<8, CW, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+    case 4: tips_window<16, CW, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
+    default: tips_window<32, CW, VERT, EDGE>(g, q, cur, prev, lo, hi, c16, c32, o, pb, pu); break;
   }
 }
 
@@ -347,8 +347,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1) tips_sweep_kernel(CsrView g,
     if (it >= n_items) break;
     const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    const bool wide = (item.flags & kItemWide) != 0;
-    const uint32_t H = wide ? kSweepWindow32 : kSweepWindow16;
+    const int cw = item_width(item.flags);
+    const uint32_t H = item_window(cw);
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en;
       init_cursor(g, q, i, item.lo, cur, b, en);
@@ -357,8 +357,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) tips_sweep_kernel(CsrView g,
     uint64_t pb = 0, pu = 0;
     for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
       const uint32_t hi = min(lo + H, item.hi);
-      if (wide) tips_window_dispatch<false, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
-      else tips_window_dispatch<true, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
+      if (cw == 8) tips_window_dispatch<8, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
+      else if (cw == 16) tips_window_dispatch<16, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
+      else tips_window_dispatch<32, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
     }
     if (VERT) {  // the pivot's share of this item
       pb = warp_sum_u64(pb);
