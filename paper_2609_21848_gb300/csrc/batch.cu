@@ -196,16 +196,17 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     const SweepItem item = bi.it;
     const CsrView g = view_of(desc[bi.graph]);
     const PivotGeom q = pivot_geom(g, item.row);
-    const int cw = item_width(item.flags);
-    const uint32_t H = item_window(cw);
+    const ItemWindows iw(item);
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en;
       init_cursor(g, q, i, item.lo, cur, b, en);
     }
     __syncthreads();
     uint64_t bal = 0, unb = 0;
-    for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
-      const uint32_t hi = min(lo + H, item.hi);
+    for (uint32_t r = 0; r < iw.count(); r++) {
+      uint32_t lo, hi;
+      int cw;
+      iw.window(r, lo, hi, cw);
       if (cw == 8) sweep_window_dispatch<8>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
       else if (cw == 16) sweep_window_dispatch<16>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
       else sweep_window_dispatch<32>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);

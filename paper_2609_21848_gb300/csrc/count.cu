@@ -117,9 +117,8 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     if (it >= n_items) break;
     const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    const int cw = item_width(item.flags);
-    const uint32_t H = item_window(cw);
-    const uint32_t R = (item.hi - item.lo + H - 1) / H;
+    const ItemWindows iw(item);
+    const uint32_t R = iw.count();
     // list scratch per item: Rsub window lists + two overflow lists of L slots
     const int64_t per_nb = q.L ? list_cap / (int64_t)q.L : 0;
     const bool listed = (item.flags & kItemList) != 0 && my_lists != nullptr && per_nb >= 3;
@@ -128,13 +127,15 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
       int in_buf = 0;  // overflow list feeding the next span
       for (uint32_t s0 = 0; s0 < R; s0 += Rsub) {
         const uint32_t nwin = min(Rsub, R - s0);
-        const uint32_t span_lo = item.lo + s0 * H;
-        const uint32_t span_hi = min(item.hi, span_lo + nwin * H);
+        uint32_t span_lo, span_hi, wlo, whi;
+        int cw;
+        iw.window(s0, span_lo, whi, cw);
+        iw.window(s0 + nwin - 1, wlo, span_hi, cw);
         if (tid < kListMaxWindows) cnt[tid] = 0;
         if (tid == 0) ocnt[in_buf ^ 1] = 0;
         __syncthreads();
         const ListItem li{my_lists, cnt, my_lists + (size_t)(Rsub + (in_buf ^ 1)) * q.L, &ocnt[in_buf ^ 1], q.L,
-                          span_lo, H, span_hi << 1, item.hi << 1};
+                          iw, s0, span_hi << 1, item.hi << 1};
         if (s0 == 0) {  // each neighbour joins the list of the window of its first entry
           for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
             uint32_t b, en;
@@ -152,16 +153,15 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
         }
         __syncthreads();
         for (uint32_t r = 0; r < nwin; r++) {
-          const uint32_t lo = span_lo + r * H;
-          const uint32_t hi = min(lo + H, span_hi);
+          iw.window(s0 + r, wlo, whi, cw);
           const uint32_t n = (uint32_t)cnt[r];
           const uint2* list = my_lists + (size_t)r * q.L;
-          if (cw == 8) list_window_dispatch<8>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
-          else if (cw == 16) list_window_dispatch<16>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
-          else list_window_dispatch<32>(item.group_log, g, li, list, n, lo, hi << 1, c16, c32, bal, unb);
+          if (cw == 8) list_window_dispatch<8>(item.group_log, g, li, list, n, wlo, whi << 1, c16, c32, bal, unb);
+          else if (cw == 16) list_window_dispatch<16>(item.group_log, g, li, list, n, wlo, whi << 1, c16, c32, bal, unb);
+          else list_window_dispatch<32>(item.group_log, g, li, list, n, wlo, whi << 1, c16, c32, bal, unb);
           n_visits += tid == 0 ? n : 0;
           __syncthreads();  // also publishes the appends made to later windows' lists
-          zero_words(c16, item_words(cw, hi - lo));
+          zero_words(c16, item_words(cw, whi - wlo));
           __syncthreads();
         }
         in_buf ^= 1;
@@ -174,8 +174,9 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     }
     __syncthreads();
     for (uint32_t r = 0; r < R; r++) {
-      const uint32_t lo = item.lo + r * H;
-      const uint32_t hi = min(lo + H, item.hi);
+      uint32_t lo, hi;
+      int cw;
+      iw.window(r, lo, hi, cw);
       if (cw == 8) sweep_window_dispatch<8>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
       else if (cw == 16) sweep_window_dispatch<16>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
       else sweep_window_dispatch<32>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);

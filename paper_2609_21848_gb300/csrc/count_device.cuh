@@ -251,17 +251,48 @@ __device__ __forceinline__ uint32_t window_words(uint32_t ranks) {  // 32-bit wo
   return CW == 8 ? (ranks + 1) >> 1 : CW == 16 ? ranks : 2 * ranks;
 }
 
-// Counter width of a work item, its ranks per window, and the 32-bit words
-// holding `ranks` of its counters.
-__device__ __forceinline__ int item_width(int16_t flags) {
-  return (flags & kItemTiny) ? 8 : (flags & kItemWide) ? 32 : 16;
-}
-__device__ __forceinline__ uint32_t item_window(int cw) {
-  return cw == 8 ? window_ranks<8>() : cw == 16 ? window_ranks<16>() : window_ranks<32>();
-}
 __device__ __forceinline__ uint32_t item_words(int cw, uint32_t ranks) {
   return cw == 8 ? window_words<8>(ranks) : cw == 16 ? window_words<16>(ranks) : window_words<32>(ranks);
 }
+
+// The windows of a work item: tiny ones over [lo, te), narrow ones over
+// [te, ne), wide ones over [ne, hi), numbered in rank order.
+struct ItemWindows {
+  uint32_t lo, te, ne, hi;
+  uint32_t rt, rn, rw;
+  __device__ __forceinline__ explicit ItemWindows(const SweepItem& it) {
+    lo = it.lo;
+    hi = it.hi;
+    te = min(max(it.t_end, lo), hi);
+    ne = min(max(it.n_end, te), hi);
+    rt = (te - lo + window_ranks<8>() - 1) / window_ranks<8>();
+    rn = (ne - te + window_ranks<16>() - 1) / window_ranks<16>();
+    rw = (hi - ne + window_ranks<32>() - 1) / window_ranks<32>();
+  }
+  __device__ __forceinline__ uint32_t count() const { return rt + rn + rw; }
+  // window r: its ranks [wlo, whi) and counter width
+  __device__ __forceinline__ void window(uint32_t r, uint32_t& wlo, uint32_t& whi, int& cw) const {
+    if (r < rt) {
+      wlo = lo + r * window_ranks<8>();
+      whi = min(wlo + window_ranks<8>(), te);
+      cw = 8;
+    } else if (r < rt + rn) {
+      wlo = te + (r - rt) * window_ranks<16>();
+      whi = min(wlo + window_ranks<16>(), ne);
+      cw = 16;
+    } else {
+      wlo = ne + (r - rt - rn) * window_ranks<32>();
+      whi = min(wlo + window_ranks<32>(), hi);
+      cw = 32;
+    }
+  }
+  // the window holding rank x (lo <= x < hi)
+  __device__ __forceinline__ uint32_t index_of(uint32_t x) const {
+    if (x < te) return (x - lo) / window_ranks<8>();
+    if (x < ne) return rt + (x - te) / window_ranks<16>();
+    return rt + rn + (x - ne) / window_ranks<32>();
+  }
+};
 
 // Add one wedge (endpoint counter k, asym = the two edge signs differ) when
 // `ok`, and accumulate its Lemma 1 contribution from the counter's old value:
@@ -431,8 +462,8 @@ struct ListItem {
   uint2* over;       // [L] neighbours waiting for a later span
   int* ocnt;         // their count (shared memory)
   uint32_t L;
-  uint32_t lo;       // first rank of the span
-  uint32_t H;        // ranks per window
+  ItemWindows iw;    // the item's windows
+  uint32_t s0;       // first window of the span
   uint32_t hl;       // (last rank of the span + 1) << 1
   uint32_t item_hl;  // (last rank of the item + 1) << 1
 };
@@ -443,7 +474,7 @@ struct ListItem {
 __device__ __forceinline__ void list_append(const ListItem& li, uint32_t x, uint32_t c, uint32_t en, uint32_t s1) {
   const uint2 slot = make_uint2(c, (en - c) | (s1 << 31));
   if (x < li.hl) {
-    const uint32_t r = ((x >> 1) - li.lo) / li.H;
+    const uint32_t r = li.iw.index_of(x >> 1) - li.s0;
     const int pos = atomicAdd(&li.cnt[r], 1);
     li.lists[(size_t)r * li.L + (uint32_t)pos] = slot;
   } else if (x < li.item_hl) {

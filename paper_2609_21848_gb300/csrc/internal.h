@@ -72,20 +72,23 @@ const Tuning& current_tuning();
 constexpr int32_t kNarrowCountLimit = 65536;
 
 // One unit of hub work: endpoints with side ranks [lo, hi) of hub row `row`,
-// swept in windows of kSweepWindow16 (narrow: 16-bit halves) or
-// kSweepWindow32 (wide: 32-bit halves) ranks, each lower neighbour's segment
-// walked by 2^group_log lanes. A count never exceeds the endpoint's degree,
-// so only ranges holding endpoints of degree >= 2^16 need wide counters.
+// swept in windows whose counters are as narrow as the counts allow: ranks
+// below t_end in tiny windows (8-bit halves, 2 * kSweepWindow16 ranks), below
+// n_end in narrow ones (16-bit halves, kSweepWindow16 ranks), the rest in wide
+// ones (32-bit halves, kSweepWindow32 ranks); t_end and n_end are the hub's
+// boundaries (clamped to the item). Each lower neighbour's segment is walked
+// by 2^group_log lanes. A count never exceeds the endpoint's degree nor the
+// hub's lower-neighbour count.
 struct SweepItem {
   int32_t row;
   uint32_t lo;
   uint32_t hi;
+  uint32_t t_end;
+  uint32_t n_end;
   int16_t group_log;
-  int16_t flags;  // kItemWide | kItemList
+  int16_t flags;  // kItemList
 };
-constexpr int16_t kItemWide = 1;  // 32-bit counter halves (kSweepWindow32 ranks per window)
 constexpr int16_t kItemList = 2;  // list mode: visit a neighbour only in windows holding its entries
-constexpr int16_t kItemTiny = 4;  // 8-bit counter halves (2 * kSweepWindow16 ranks per window)
 // Counts below this fit the 8-bit halves of a tiny counter.
 constexpr int32_t kTinyCountLimit = 256;
 

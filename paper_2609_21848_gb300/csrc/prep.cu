@@ -469,44 +469,42 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
     const double density = (double)W / ((double)L * (double)std::max<uint64_t>(1, Rt + Rn + Rw));
     const double* gd = g->tune.group_density;
     const int16_t dense_log = density >= gd[0] ? 5 : density >= gd[1] ? 4 : density >= gd[2] ? 3 : density >= gd[3] ? 2 : 0;
-    // sparse hubs sweep in list mode: one item per counter width, run in
-    // spans of at most Rsub windows whose lists (plus two overflow lists of
-    // L slots) fit the per-CTA list scratch
+    // sparse hubs sweep in list mode: one item per hub, run in spans of at
+    // most Rsub windows whose lists (plus two overflow lists of L slots) fit
+    // the per-CTA list scratch
     const uint64_t per_nb = (uint64_t)kListCapEntries / std::max<uint32_t>(L, 1);
     const uint64_t Rsub = per_nb >= 3 ? std::min<uint64_t>(kListMaxWindows, per_nb - 2) : 0;
-    const bool listed = density < g->tune.list_density && Rsub >= 1 && Rt + Rn + Rw >= 2;
-    const int16_t group_log = listed ? (int16_t)g->tune.list_group_log : dense_log;
-    const int16_t list_flag = listed ? kItemList : 0;
-    auto add = [&](uint64_t lo, uint64_t hi, uint64_t H, int16_t flags, uint64_t est) {
+    const uint64_t R_all = Rt + Rn + Rw;
+    const bool listed = density < g->tune.list_density && Rsub >= 1 && R_all >= 2;
+    // the first rank of window w of the hub (windows numbered in rank order
+    // over the tiny, narrow and wide parts)
+    auto window_start = [&](uint64_t w) -> uint64_t {
+      if (w < Rt) return start + w * H8;
+      if (w < Rt + Rn) return tiny_end + (w - Rt) * kSweepWindow16;
+      return std::min<uint64_t>(sp, narrow_end + (w - Rt - Rn) * kSweepWindow32);
+    };
+    // items of roughly `target` wedges over consecutive windows (one item in
+    // list mode); an item crosses width boundaries freely
+    const uint64_t spans = listed ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(R_all, W / target));
+    for (uint64_t k = 0; k < spans && R_all > 0; k++) {
+      const uint64_t w0 = R_all * k / spans, w1 = R_all * (k + 1) / spans;
+      if (w1 <= w0) continue;
       Planned p;
       p.it.row = row;
-      p.it.lo = (uint32_t)lo;
-      p.it.hi = (uint32_t)hi;
-      p.it.group_log = group_log;
-      p.it.flags = (int16_t)(flags | list_flag);
-      p.est = est;
+      p.it.lo = (uint32_t)window_start(w0);
+      p.it.hi = (uint32_t)(w1 == R_all ? sp : window_start(w1));
+      p.it.t_end = (uint32_t)tiny_end;
+      p.it.n_end = (uint32_t)narrow_end;
+      p.it.group_log = listed ? (int16_t)g->tune.list_group_log : dense_log;
+      p.it.flags = listed ? kItemList : 0;
+      p.est = std::max<uint64_t>(1, W / spans);
       plan.push_back(p);
-      const int64_t R = (int64_t)((hi - lo + H - 1) / H);
+      const int64_t R = (int64_t)(w1 - w0);
       g->hub_cursor_inits += L;
       if (listed)
         g->sweep_list_cap = std::max<int64_t>(g->sweep_list_cap, (std::min<int64_t>(R, (int64_t)Rsub) + 2) * (int64_t)L);
       else g->hub_cursor_steps += (int64_t)L * R;
-    };
-    // each width's part in items of roughly `target` wedges (one item in list
-    // mode), the work estimated in proportion to the part's windows
-    const uint64_t R_all = std::max<uint64_t>(1, Rt + Rn + Rw);
-    auto add_part = [&](uint64_t lo, uint64_t hi, uint64_t H, uint64_t R, int16_t flags) {
-      if (R == 0) return;
-      const uint64_t Wp = W * R / R_all;
-      const uint64_t spans = listed ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(R, Wp / target));
-      for (uint64_t k = 0; k < spans; k++) {
-        const uint64_t w0 = R * k / spans, w1 = R * (k + 1) / spans;
-        if (w1 > w0) add(lo + w0 * H, std::min<uint64_t>(hi, lo + w1 * H), H, flags, std::max<uint64_t>(1, Wp / spans));
-      }
-    };
-    add_part(start, tiny_end, H8, Rt, kItemTiny);
-    add_part(tiny_end, narrow_end, kSweepWindow16, Rn, 0);
-    add_part(narrow_end, sp, kSweepWindow32, Rw, kItemWide);
+    }
   }
   std::stable_sort(plan.begin(), plan.end(), [](const Planned& a, const Planned& b) { return a.est > b.est; });
   std::vector<SweepItem> items(plan.size());

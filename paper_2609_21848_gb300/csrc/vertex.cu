@@ -347,16 +347,17 @@ __global__ void __launch_bounds__(kSweepThreads, 1) tips_sweep_kernel(CsrView g,
     if (it >= n_items) break;
     const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    const int cw = item_width(item.flags);
-    const uint32_t H = item_window(cw);
+    const ItemWindows iw(item);
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en;
       init_cursor(g, q, i, item.lo, cur, b, en);
     }
     __syncthreads();
     uint64_t pb = 0, pu = 0;
-    for (uint32_t lo = item.lo; lo < item.hi; lo += H) {
-      const uint32_t hi = min(lo + H, item.hi);
+    for (uint32_t r = 0; r < iw.count(); r++) {
+      uint32_t lo, hi;
+      int cw;
+      iw.window(r, lo, hi, cw);
       if (cw == 8) tips_window_dispatch<8, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
       else if (cw == 16) tips_window_dispatch<16, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
       else tips_window_dispatch<32, VERT, EDGE>(item.group_log, g, q, cur, prev, lo, hi, c16, c32, o, pb, pu);
