@@ -164,7 +164,7 @@ class Server:
 
     def __init__(self, backend, memory_budget: int | None = None, reserve_bytes: int = 2 << 30,
                  large_edges: int = 1_000_000, max_batch: int = 4096, max_group_edges: int = 1 << 26,
-                 builders: int = 2, large_lanes: int = 2):
+                 builders: int = 3, large_lanes: int = 2):
         self.backend = backend
         free = backend.free_memory()
         self.budget = int(memory_budget if memory_budget is not None else max(0, free - reserve_bytes))
