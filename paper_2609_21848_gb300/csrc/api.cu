@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "internal.h"
 #include "common.cuh"
@@ -24,10 +26,47 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+// Device memory comes from one stream-ordered pool per device owned by the
+// library. The pool keeps up to kPoolKeepBytes of freed memory mapped across
+// synchronizations (the default pool would unmap all of it at every
+// synchronize, and the next build or count would map it again); what it holds
+// beyond that goes back to the device.
+constexpr uint64_t kPoolKeepBytes = uint64_t{8} << 30;
+
+static cudaMemPool_t library_pool(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    (void)cudaGetLastError();
+    pool = nullptr;  // fall back to the device's default pool
+  } else {
+    uint64_t keep = kPoolKeepBytes;
+    (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  pools[dev] = pool;
+  return pool;
+}
+
 void* dev_alloc(size_t bytes, cudaStream_t s) {
   if (g_alloc_fn) return g_alloc_fn(bytes, (void*)s, g_alloc_ctx);
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  const cudaMemPool_t pool = library_pool(dev);
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return nullptr;
   }
