@@ -28,7 +28,8 @@
  *   - On error, output parameters are left untouched and a status other than
  *     DBBC_OK is returned. No C++ exception crosses this interface.
  *   - Device memory is taken from the allocator set with dbbc_set_allocator,
- *     else from cudaMallocAsync on the call's stream.
+ *     else stream-ordered on the call's stream from the library's own memory
+ *     pool (see dbbc_set_allocator).
  *   - A handle may be read by several counts at once (each count allocates its
  *     own scratch); it must not be freed while a count on it is in flight.
  */
@@ -252,7 +253,10 @@ DBBC_API dbbc_status dbbc_graph_export(const dbbc_graph* g, void* cuda_stream, i
                               uint32_t* lower, int32_t* vertex, uint64_t* work);
 
 /* Device allocator hook (e.g. a framework's caching allocator). alloc returns
- * NULL on failure. Passing NULL for both restores cudaMallocAsync/cudaFreeAsync.
+ * NULL on failure. Passing NULL for both restores the default: stream-ordered
+ * allocations (cudaMallocFromPoolAsync) from one memory pool per device owned
+ * by the library, which keeps up to 8 GiB of freed memory mapped between
+ * calls instead of returning it to the device at every synchronization.
  * Not thread-safe against concurrent library calls. */
 DBBC_API void dbbc_set_allocator(void* (*alloc_fn)(size_t bytes, void* cuda_stream, void* ctx),
                         void (*free_fn)(void* ptr, void* cuda_stream, void* ctx), void* ctx);
