@@ -112,13 +112,4 @@ __device__ __forceinline__ void block_add_pair(uint64_t a, uint64_t b, unsigned 
   }
 }
 
-// Contribution of one endpoint counter packed as (asym << 32) | sym
-// (Algorithm 1 buckets B1 = sym, B2 = asym; Lemma 1 for the unbalanced term).
-__device__ __forceinline__ void pair_contrib(uint64_t packed, uint64_t& bal, uint64_t& unb) {
-  const uint64_t p = packed & 0xFFFFFFFFull;
-  const uint64_t q = packed >> 32;
-  bal += (p * (p - (p > 0)) >> 1) + (q * (q - (q > 0)) >> 1);
-  unb += p * q;
-}
-
 }  // namespace dbbc

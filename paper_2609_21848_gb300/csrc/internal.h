@@ -49,7 +49,6 @@ constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per wor
 #ifndef DBBC_GROUP_T4
 #define DBBC_GROUP_T4 2
 #endif
-constexpr double kGroupThreshold[4] = {DBBC_GROUP_T32, DBBC_GROUP_T16, DBBC_GROUP_T8, DBBC_GROUP_T4};
 // Hub items in list mode (see count_device.cuh) run in spans of at most
 // kListMaxWindows windows, with at most kListCapEntries list slots (8 bytes
 // each) per CTA.
