@@ -279,6 +279,12 @@ def test_union_build_validates_each_component():
          hash_mult_log=3),   # 32-lane groups everywhere, sparse hash tables
     dict(light_max_work=16, medium_max_work=64, hub_item_work=4096, group_density=[1e9, 1e9, 1e9, 1e9],
          hash_mult_log=2),   # one lane per segment
+    dict(light_max_work=1, medium_max_work=1, hub_item_work=1024, group_density=[40.0, 16.0, 6.0, 2.0],
+         hash_mult_log=1, list_density=1e9, list_group_log=0),   # every pivot a list-mode hub, one lane
+    dict(light_max_work=64, medium_max_work=512, hub_item_work=1 << 20, group_density=[40.0, 16.0, 6.0, 2.0],
+         hash_mult_log=2, list_density=1e9, list_group_log=5),   # list mode with whole-warp groups
+    dict(light_max_work=512, medium_max_work=4096, hub_item_work=1 << 22, group_density=[40.0, 16.0, 6.0, 2.0],
+         hash_mult_log=2, list_density=0.0, list_group_log=2),   # no list mode
 ])
 def test_counts_do_not_depend_on_tuning(tuning):
     base = dbbc.dbbc_get_tuning()
