@@ -231,7 +231,7 @@ __device__ __forceinline__ void load_chunk(const uint32_t* col, uint32_t c, uint
 #pragma unroll
   for (int u = 0; u < kSweepUnroll; u++) {
     const uint32_t off = (uint32_t)(u * G + gl);
-    x[u] = en - c > off ? col[c + off] : 0xFFFFFFFFu;
+    x[u] = en - c > off ? __ldg(col + c + off) : 0xFFFFFFFFu;
   }
 }
 
@@ -385,9 +385,10 @@ __device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& 
       const uint32_t i = i0 + k * groups;
       c[k] = en[k] = s1[k] = 0;
       if (i < q.L) {
-        c[k] = cur[2 * i];
-        en[k] = cur[2 * i + 1];
-        s1[k] = col[q.rb + i] & 1u;
+        const uint2 ce = *reinterpret_cast<const uint2*>(cur + 2 * i);  // cursor and row end
+        c[k] = ce.x;
+        en[k] = ce.y;
+        s1[k] = __ldg(col + q.rb + i) & 1u;
       }
     }
 #pragma unroll
