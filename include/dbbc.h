@@ -294,7 +294,9 @@ DBBC_API dbbc_status dbbc_count_partition(const dbbc_graph* g, void* cuda_stream
  *                     shorter than this (>= 0; 0 turns it off) sweep in list
  *                     mode, visiting a neighbour only in the windows that
  *                     hold its entries;
- *   list_group_log  : lanes per neighbour segment in list mode, log2 (0..5). */
+ *   list_group_log  : lanes per neighbour segment in list mode, log2 (0 or
+ *                     2..5: one lane, or lane groups of 4 to 32).
+ * Setting and reading the tuning is safe against builds on other threads. */
 typedef struct {
   uint64_t light_max_work;
   uint64_t medium_max_work;

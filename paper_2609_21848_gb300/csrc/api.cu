@@ -19,8 +19,16 @@ void (*g_free_fn)(void*, void*, void*) = nullptr;
 void* g_alloc_ctx = nullptr;
 }  // namespace
 
+// The tuning new builds take; builder threads read it while another thread
+// may set it, so both sides hold the lock.
+namespace {
+std::mutex g_tuning_mu;
 Tuning g_tuning;
-const Tuning& current_tuning() { return g_tuning; }
+}  // namespace
+Tuning current_tuning() {
+  std::lock_guard<std::mutex> lock(g_tuning_mu);
+  return g_tuning;
+}
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -127,6 +135,7 @@ const char* dbbc_status_string(dbbc_status s) {
 
 dbbc_status dbbc_set_tuning(const dbbc_tuning* t) {
   if (!t) {
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
     g_tuning = Tuning();
     return DBBC_OK;
   }
@@ -145,19 +154,21 @@ dbbc_status dbbc_set_tuning(const dbbc_tuning* t) {
   n.hash_mult_log = t->hash_mult_log;
   n.list_density = t->list_density;
   n.list_group_log = t->list_group_log;
+  std::lock_guard<std::mutex> lock(g_tuning_mu);
   g_tuning = n;
   return DBBC_OK;
 }
 
 void dbbc_get_tuning(dbbc_tuning* t) {
   if (!t) return;
-  t->light_max_work = g_tuning.light_max_work;
-  t->medium_max_work = g_tuning.medium_max_work;
-  t->hub_item_work = g_tuning.hub_item_work;
-  for (int i = 0; i < 4; i++) t->group_density[i] = g_tuning.group_density[i];
-  t->hash_mult_log = g_tuning.hash_mult_log;
-  t->list_density = g_tuning.list_density;
-  t->list_group_log = g_tuning.list_group_log;
+  const Tuning c = current_tuning();
+  t->light_max_work = c.light_max_work;
+  t->medium_max_work = c.medium_max_work;
+  t->hub_item_work = c.hub_item_work;
+  for (int i = 0; i < 4; i++) t->group_density[i] = c.group_density[i];
+  t->hash_mult_log = c.hash_mult_log;
+  t->list_density = c.list_density;
+  t->list_group_log = c.list_group_log;
 }
 
 void dbbc_set_allocator(void* (*alloc_fn)(size_t, void*, void*), void (*free_fn)(void*, void*, void*), void* ctx) {

@@ -65,7 +65,7 @@ struct Tuning {
   double list_density = 8.0;  // hubs with a mean (neighbour, window) segment shorter than this use list mode
   int32_t list_group_log = 2; // lanes per neighbour segment in list mode (log2)
 };
-const Tuning& current_tuning();
+Tuning current_tuning();  // a copy, taken under the tuning lock
 
 // Counts below this fit the 16-bit halves of a narrow counter.
 constexpr int32_t kNarrowCountLimit = 65536;

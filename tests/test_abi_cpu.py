@@ -98,3 +98,37 @@ def test_tuning_round_trip_and_validation(lib):
         assert dbbc.dbbc_get_tuning() == autotune.DEFAULT
     finally:
         dbbc.dbbc_set_tuning(base)
+
+
+def test_tuning_reads_are_whole_under_concurrent_sets(lib):
+    """Threads that set and read the tuning at once (as the serving loop's
+    builder threads may) only ever read one of the settings some thread set."""
+    import threading
+    base = dbbc.dbbc_get_tuning()
+    a = dict(light_max_work=128, medium_max_work=1024, hub_item_work=1 << 19,
+             group_density=[40.0, 16.0, 6.0, 2.0], hash_mult_log=1, list_density=4.0, list_group_log=2)
+    b = dict(light_max_work=512, medium_max_work=4096, hub_item_work=1 << 22,
+             group_density=[128.0, 48.0, 12.0, 4.0], hash_mult_log=3, list_density=32.0, list_group_log=5)
+    seen, errors = [], []
+
+    def writer(t):
+        try:
+            for _ in range(2000):
+                dbbc.dbbc_set_tuning(t)  # every key given: nothing merged from the current values
+        except Exception as e:  # pragma: no cover - reported below
+            errors.append(e)
+
+    def reader():
+        for _ in range(2000):
+            seen.append(dbbc.dbbc_get_tuning())
+
+    try:
+        threads = [threading.Thread(target=writer, args=(t,)) for t in (a, b)] + [threading.Thread(target=reader)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        assert not errors
+        assert all(r in (a, b, base) for r in seen)
+    finally:
+        dbbc.dbbc_set_tuning(base)
