@@ -44,3 +44,32 @@ def test_default_arguments_keep_the_contract(monkeypatch):
     a = b.parse()
     assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1 and a.impl == "dbbc"
     assert a.workload == "chunglu-1m-200k-20m" and a.scale == 1.0
+
+
+def run_reference_arm(extra_env=None):
+    import json
+    import subprocess
+    env = dict(os.environ, **(extra_env or {}))
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "uniform-2k-3k-20k", "--steps", "2", "--warmup", "1", "--reference-seconds", "3"],
+                       capture_output=True, text=True, env=env, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [line for line in r.stdout.splitlines() if line.startswith("{")]
+    return [json.loads(line) for line in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """The reference arm times the oracle on the host cores and prints one
+    JSON line with the keys the benchmark contract asks of it."""
+    (line,) = run_reference_arm()
+    assert line["impl"] == "reference" and line["unit"] == "G wedges/s" and line["value"] > 0
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    assert line["config"]["workload"] == "uniform-2k-3k-20k"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    assert run_reference_arm({"RANK": "1", "WORLD_SIZE": "2"}) == []
