@@ -6,12 +6,22 @@ pointers, streams to ``cudaStream_t``) and calls ``_build/libdbbc.so``; every
 step of the computation runs in the library's CUDA kernels. There is no CPU
 fallback: if the library has not been built, :func:`lib` raises.
 
-Functions carry the C names: :func:`dbbc_graph_from_coo`, :func:`dbbc_count`,
-:func:`dbbc_count_async`, :func:`dbbc_count_batch`,
-:func:`dbbc_count_batch_async`, :func:`dbbc_graph_get_info`,
-:func:`dbbc_graph_device_bytes`, :func:`dbbc_estimate_bytes`,
-:func:`dbbc_graph_export`, :func:`dbbc_graph_free`, :func:`dbbc_set_allocator`,
-:func:`dbbc_status_string`, :func:`dbbc_version`.
+Functions carry the C names (``EXPORTED`` lists them all):
+
+- graphs: :func:`dbbc_graph_from_coo`, :func:`dbbc_graph_from_coo_multi`,
+  :func:`dbbc_graph_get_info`, :func:`dbbc_graph_device_bytes`,
+  :func:`dbbc_estimate_bytes`, :func:`dbbc_graph_export`, :func:`dbbc_graph_free`;
+- counts: :func:`dbbc_count`, :func:`dbbc_count_async`,
+  :func:`dbbc_count_profiled`, :func:`dbbc_count_noalloc`,
+  :func:`dbbc_count_components`, :func:`dbbc_count_vertices`,
+  :func:`dbbc_count_edges`;
+- many graphs: :func:`dbbc_count_batch`, :func:`dbbc_count_batch_async`,
+  :func:`dbbc_batch_create`, :func:`dbbc_batch_count`,
+  :func:`dbbc_batch_count_async`, :func:`dbbc_batch_free`;
+- several GPUs: :func:`dbbc_lpt_partition`, :func:`dbbc_count_partition`;
+- housekeeping: :func:`dbbc_set_tuning`, :func:`dbbc_get_tuning`,
+  :func:`dbbc_set_allocator`, :func:`dbbc_kernel_launches`,
+  :func:`dbbc_status_string`, :func:`dbbc_version`.
 """
 from __future__ import annotations
 
