@@ -5,7 +5,12 @@ One step = one pass of the whole path over one synthetic graph already
 resident in HBM: build (validate, keep-latest dedup, degrees, Def. 3 ranks,
 sign-packed CSR, accepted-wedge work and tiers) + count (light / medium / hub
 wedge aggregation, Lemma 1 finalisation, reduction) + free. The metric is
-accepted wedges of Algorithm 1 per second (G wedges/s), whole job.
+accepted wedges of Algorithm 1 per second (G wedges/s), whole job. The
+default workload is the largest single graph (polarized, 20M x 2M vertices,
+300M edges); its line also carries the batched form (4,096 resident graphs
+counted by one replayed plan, against one count per graph) and the served form
+(a Poisson stream of 100,000 requests at 2,000/s) as "batch" and "serve"
+records, in graphs/s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl dbbc|reference]
 
@@ -33,6 +38,9 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "G wedges/s and graphs/s, batched vs per-graph launches, bit-exact counts"
+# the largest single graph: the headline line, which also carries the batched
+# (4,096 graphs) and served (Poisson stream) records
+DEFAULT_WORKLOAD = "polarized-20m-2m-300m"
 UNIT = "G wedges/s"
 L2_BYTES = 129 * 2**20
 
@@ -54,10 +62,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dbbc", "reference"], default="dbbc")
-    ap.add_argument("--workload", default="chunglu-1m-200k-20m", choices=sorted(synth.WORKLOADS) + ["batch-4096", "serve", "sign-sweep", "tips"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(synth.WORKLOADS) + ["batch-4096", "serve", "sign-sweep", "tips"])
     ap.add_argument("--n-graphs", type=int, default=4096, help="graphs in the batch-4096 workload")
-    ap.add_argument("--requests", type=int, default=4000, help="requests of the served workload")
-    ap.add_argument("--large-pool", type=int, default=4, help="distinct large graphs cycled by the served stream")
+    ap.add_argument("--requests", type=int, default=synth.SERVE["n_requests"],
+                    help="requests of the served workload (and of the default line's serve record)")
+    ap.add_argument("--large-pool", type=int, default=16,
+                    help="distinct large graphs (5M-20M edges) the served stream's large requests are drawn from")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave the batch and serve records out of the default single-graph line")
     ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the host-buffer end-to-end timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -256,14 +268,16 @@ def cpu_baseline(g, target_s: float) -> dict:
                       f"{nc} threads; oracle graph build {build_s:.1f} s untimed)"}
 
 
-def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
+def batch_record(a, torch, dbbc, world, rank, local, dist, barrier, graphs=None, with_cpu=True) -> dict:
     """The batched form: thousands of uneven resident graphs counted by one
     replayed CUDA graph (three kernels for all graphs), against the plain path
-    of one synchronous count (one launch sequence) per graph. Metric: graphs/s."""
+    of one synchronous count (one launch sequence) per graph. Metric: graphs/s.
+    Returns the line (printed by run_batch, or attached to the default line)."""
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
-    graphs = synth.batch(a.n_graphs)
+    if graphs is None:
+        graphs = synth.batch(a.n_graphs)
     gen_s = time.perf_counter() - t0
     sizes = [g.m for g in graphs]
     offs = np.concatenate([[0], np.cumsum(sizes)])
@@ -350,8 +364,7 @@ def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
             "config": {"workload": "batch-4096", "n_graphs": len(handles), "edges_total": int(offs[-1]),
                        "tuning": dbbc.dbbc_get_tuning(),
                        "wedges_per_step": wedges,
-                       "parallelism": (f"LPT pivot partition x{world}" if partition else f"replicas x{world}")
-                       if world > 1 else "1 GPU",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (all graphs' CSR %.0f MB > 129 MB)" % (
                            sum(8 * i["m"] + 24 * (i["n_u"] + i["n_v"]) for i in infos) / 1e6)},
             "plain_graphs_per_s": plain_gps, "batched_over_plain": value / world / plain_gps,
@@ -368,7 +381,7 @@ def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
                          "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "bytes_per_launch": nbytes, "ms_per_launch": 1e3 * per_replay_s},
             "gpu_launches": int(launches), "clocks": clocks}
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+    if with_cpu and rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle
         nc = cores()
         t0 = time.perf_counter()
@@ -385,23 +398,30 @@ def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
     plan.free()
     for h in handles:
         h.free()
+    return line
+
+
+def run_batch(a, torch, dbbc, world, rank, local, dist, barrier):
+    line = batch_record(a, torch, dbbc, world, rank, local, dist, barrier)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_serve(a, torch, dbbc, world, rank, local, dist, barrier):
+def serve_record(a, torch, dbbc, world, rank, local, dist, barrier, small=None) -> dict:
     """The served form: a Poisson stream at 2,000 requests/s, 99% graphs of the
-    batch distribution and 1% large polarized graphs (5M-20M edges), served
-    with continuous batching (paper_2609_21848_gb300.serve). Reports latency
-    percentiles at that rate, the saturated throughput (every request arrives
-    at once), and the plain path (one request at a time: build, count, free)."""
+    batch distribution and 1% large polarized graphs (5M-20M edges, drawn from
+    a pool of --large-pool distinct graphs), served with continuous batching
+    (paper_2609_21848_gb300.serve). Reports latency percentiles at that rate,
+    the saturated throughput (every request arrives at once), and the plain
+    path (one request at a time: build, count, free). Returns the line."""
     from paper_2609_21848_gb300.serve import DbbcBackend, Request, Server, poisson_arrivals
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     rate = synth.SERVE["rate"]
     n = a.requests
     t0 = time.perf_counter()
-    small = synth.batch(min(n, 4096))
+    if small is None:
+        small = synth.batch(min(n, 4096))
     is_large = [synth.serve_is_large(i) for i in range(n)]
     n_large = sum(is_large)
     large = [synth.serve_large_graph(i) for i in range(min(a.large_pool, max(1, n_large)))] if n_large else []
@@ -482,6 +502,11 @@ def run_serve(a, torch, dbbc, world, rank, local, dist, barrier):
             "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 9 * edges,
                     "d2h_bytes_per_step": 16 * n, "steps": 1, "bit_exact": exact},
             "roofline": None, "gpu_launches": int(launches), "clocks": clocks}
+    return line
+
+
+def run_serve(a, torch, dbbc, world, rank, local, dist, barrier):
+    line = serve_record(a, torch, dbbc, world, rank, local, dist, barrier)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -688,7 +713,7 @@ def main():
     value = (1 if partition else world) * wedges * a.steps / (t_ms / 1e3) / 1e9
 
     # end to end through the public API with host buffers (pinned), H2D + D2H inside
-    e2e_steps = a.steps if a.e2e_steps is None else a.e2e_steps
+    e2e_steps = min(a.steps, 5) if a.e2e_steps is None else a.e2e_steps
     e2e = None
     if e2e_steps > 0:
         hu, hv, hs = (torch.from_numpy(x).pin_memory() for x in (g.u, g.v, g.s))
@@ -750,6 +775,30 @@ def main():
             "count_only_gwedges_per_s": wedges / (tiers_ms["ms_total"] / 1e3) / 1e9 if tiers_ms["ms_total"] else None,
             "e2e": e2e,
             "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
+    # the other half of the metric, on the same GPU after the timed region:
+    # graphs/s of the batched (one replayed plan over 4,096 graphs) and served
+    # (Poisson stream, continuous batching) forms against one launch per graph
+    if a.workload == DEFAULT_WORKLOAD and a.scale == 1.0 and not a.no_extras:
+        if world == 1:
+            del du, dv, ds
+            torch.cuda.synchronize(dev)
+            autotune.apply_saved("batch-4096")
+            small = synth.batch(a.n_graphs)
+            b = batch_record(a, torch, dbbc, world, rank, local, dist, barrier, graphs=small, with_cpu=False)
+            line["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "plain_graphs_per_s",
+                                               "batched_over_plain", "bit_exact_vs_plain", "batched_gwedges_per_s",
+                                               "union_build_and_count_graphs_per_s", "union_bit_exact", "e2e",
+                                               "gpu_launches", "clocks")}
+            line["batch"]["config"] = b["config"]
+            s = serve_record(a, torch, dbbc, world, rank, local, dist, barrier, small=small)
+            line["serve"] = {k: s[k] for k in ("value", "unit", "served_at_rate", "saturated", "plain_graphs_per_s",
+                                               "served_over_plain", "bit_exact_vs_alone", "e2e", "gpu_launches",
+                                               "clocks")}
+            line["serve"]["config"] = s["config"]
+            autotune.apply_saved(a.workload)
+        else:
+            line["batch"] = line["serve"] = {"skipped": "with N > 1 every rank counts a replica of the single "
+                                                        "graph only; the batched and served forms run at N = 1"}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, a.cpu_seconds)
     if rank == 0:

@@ -43,7 +43,9 @@ def test_default_arguments_keep_the_contract(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = b.parse()
     assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1 and a.impl == "dbbc"
-    assert a.workload == "chunglu-1m-200k-20m" and a.scale == 1.0
+    # the headline is the largest single graph, with the batched and served records attached
+    assert a.workload == "polarized-20m-2m-300m" and a.scale == 1.0 and not a.no_extras
+    assert a.requests == 100_000 and a.large_pool >= 16
 
 
 def run_reference_arm(extra_env=None):
