@@ -295,7 +295,13 @@ DBBC_API dbbc_status dbbc_count_partition(const dbbc_graph* g, void* cuda_stream
  *                     mode, visiting a neighbour only in the windows that
  *                     hold its entries;
  *   list_group_log  : lanes per neighbour segment in list mode, log2 (0 or
- *                     2..5: one lane, or lane groups of 4 to 32).
+ *                     2..5: one lane, or lane groups of 4 to 32);
+ *   finalize_window_wedges : hub work items with at least this many accepted
+ *                     wedges per window (estimated) finalise each window by
+ *                     one scan of its counters (C(p,2) + C(q,2) and p*q per
+ *                     endpoint, Lemma 1) when clearing it; sparser items add
+ *                     every wedge's Lemma 1 contribution as it is counted
+ *                     (0: every item scans; UINT64_MAX: none does).
  * Setting and reading the tuning is safe against builds on other threads. */
 typedef struct {
   uint64_t light_max_work;
@@ -305,6 +311,7 @@ typedef struct {
   int32_t hash_mult_log;
   double list_density;
   int32_t list_group_log;
+  uint64_t finalize_window_wedges;
 } dbbc_tuning;
 DBBC_API dbbc_status dbbc_set_tuning(const dbbc_tuning* t); /* NULL restores the defaults; DBBC_EINVAL if out of range */
 DBBC_API void dbbc_get_tuning(dbbc_tuning* t);

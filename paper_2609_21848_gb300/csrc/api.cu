@@ -154,6 +154,7 @@ dbbc_status dbbc_set_tuning(const dbbc_tuning* t) {
   n.hash_mult_log = t->hash_mult_log;
   n.list_density = t->list_density;
   n.list_group_log = t->list_group_log;
+  n.finalize_window_wedges = t->finalize_window_wedges;
   std::lock_guard<std::mutex> lock(g_tuning_mu);
   g_tuning = n;
   return DBBC_OK;
@@ -169,6 +170,7 @@ void dbbc_get_tuning(dbbc_tuning* t) {
   t->hash_mult_log = c.hash_mult_log;
   t->list_density = c.list_density;
   t->list_group_log = c.list_group_log;
+  t->finalize_window_wedges = c.finalize_window_wedges;
 }
 
 void dbbc_set_allocator(void* (*alloc_fn)(size_t, void*, void*), void (*free_fn)(void*, void*, void*), void* ctx) {

@@ -8,7 +8,7 @@
 #include <algorithm>
 #include <numeric>
 
-#include "count_device.cuh"
+#include "sweep_device.cuh"
 
 namespace dbbc {
 
@@ -177,15 +177,17 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_batch_kernel(cons
 __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const GraphDesc* __restrict__ desc,
                                                                         const BatchHubItem* __restrict__ items,
                                                                         int64_t n_items, int* next_item,
-                                                                        uint32_t* __restrict__ cursors, int64_t cur_cap,
+                                                                        uint2* __restrict__ cursors, int64_t cur_cap,
                                                                         unsigned long long* out) {
   extern __shared__ __align__(16) unsigned char sweep_smem[];
-  uint32_t* c16 = reinterpret_cast<uint32_t*>(sweep_smem);
-  unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
+  uint32_t* cnt_words = reinterpret_cast<uint32_t*>(sweep_smem);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sweep_smem);
   __shared__ int item_sh;
+  __shared__ uint32_t nb_next;
   const int tid = threadIdx.x;
-  zero_words(c16, kSweepWindow16);
-  uint32_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
+  zero_words(cnt_words, kSweepWords);
+  if (tid == 0) nb_next = 0u;
+  uint2* cur = cursors + (int64_t)blockIdx.x * cur_cap;
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
     __syncthreads();
@@ -197,9 +199,11 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     const CsrView g = view_of(desc[bi.graph]);
     const PivotGeom q = pivot_geom(g, item.row);
     const ItemWindows iw(item);
+    const bool fin = (item.flags & kItemFinalize) != 0;
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
-      uint32_t b, en;
-      init_cursor(g, q, i, item.lo, cur, b, en);
+      uint32_t b, en, s1;
+      lean_cursor_start(g, q, i, item.lo, b, en, s1);
+      cur[i] = lean_slot(b, en, s1);
     }
     __syncthreads();
     uint64_t bal = 0, unb = 0;
@@ -207,12 +211,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
       uint32_t lo, hi;
       int cw;
       iw.window(r, lo, hi, cw);
-      if (cw == 8) sweep_window_dispatch<8>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      else if (cw == 16) sweep_window_dispatch<16>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      else sweep_window_dispatch<32>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      __syncthreads();
-      zero_words(c16, item_words(cw, hi - lo));
-      __syncthreads();
+      lean_sweep_cursor(cw, fin, item.group_log, g.col, q.L, cur, lo, hi, sbase, cnt_words, &nb_next, bal, unb);
     }
     block_add_pair<kSweepThreads>(bal, unb, out + 2 * bi.graph);
   }
@@ -231,7 +230,7 @@ struct dbbc_batch {
   dbbc::BatchHubItem* hub = nullptr;
   int64_t n_light = 0, n_medium = 0, n_hub_items = 0, max_lower = 1;
   unsigned long long* out = nullptr;  // [n_graphs][2]
-  uint32_t* cursors = nullptr;
+  uint2* cursors = nullptr;
   int* counters = nullptr;  // [0] light chunks, [1] hub items
   unsigned* status = nullptr;
   int hub_grid = 0, light_grid = 0, medium_grid = 0;
@@ -341,10 +340,9 @@ static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector
   b->out = static_cast<unsigned long long*>(batch_alloc(b, (size_t)n * 2 * sizeof(unsigned long long)));
   b->counters = static_cast<int*>(batch_alloc(b, 2 * sizeof(int)));
   b->status = static_cast<unsigned*>(batch_alloc(b, sizeof(unsigned)));
-  const size_t smem = (size_t)kSweepWindow16 * 4;
-  b->hub_grid = num_sms() * blocks_per_sm((const void*)hub_sweep_batch_kernel, kSweepThreads, smem);
+  b->hub_grid = num_sms() * blocks_per_sm((const void*)hub_sweep_batch_kernel, kSweepThreads, kSweepSmem);
   if (b->n_hub_items > 0)
-    b->cursors = static_cast<uint32_t*>(batch_alloc(b, (size_t)b->hub_grid * (size_t)b->max_lower * 8));
+    b->cursors = static_cast<uint2*>(batch_alloc(b, (size_t)b->hub_grid * (size_t)b->max_lower * sizeof(uint2)));
   {
     const int sms = num_sms();
     const int64_t want = ceil_div<int64_t>(ceil_div<int64_t>(b->n_light, 32), kLightWarps);
@@ -379,9 +377,8 @@ static void enqueue_batch(dbbc_batch* b, cudaStream_t s) {
     DBBC_LAUNCH_CHECK();
   }
   if (b->n_hub_items > 0) {
-    const size_t smem = (size_t)kSweepWindow16 * 4;
     const int grid = (int)std::min<int64_t>(b->hub_grid, b->n_hub_items);
-    hub_sweep_batch_kernel<<<grid, kSweepThreads, smem, s>>>(b->desc, b->hub, b->n_hub_items, b->counters + 1,
+    hub_sweep_batch_kernel<<<grid, kSweepThreads, kSweepSmem, s>>>(b->desc, b->hub, b->n_hub_items, b->counters + 1,
                                                              b->cursors, b->max_lower, b->out);
     DBBC_LAUNCH_CHECK();
   }
@@ -393,7 +390,7 @@ static void set_batch_attributes() {
   DBBC_CUDA(cudaFuncSetAttribute(count_medium_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)((size_t)kMediumSlots * 12)));
   DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)kSweepWindow16 * 4)));
+                                 (int)kSweepSmem));
 }
 
 static void check_batch_status(const dbbc_batch* b, cudaStream_t s) {

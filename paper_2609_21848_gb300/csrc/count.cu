@@ -12,7 +12,7 @@
 // Each pivot p walks its lower neighbours v (a prefix of its CSR row) and,
 // for each, the prefix of v's row whose entries rank below p, so every wedge
 // it reads is accepted.
-#include "count_device.cuh"
+#include "sweep_device.cuh"
 
 namespace dbbc {
 
@@ -87,31 +87,113 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
 }
 
 // ------------------------------------------------------------------ hub tier
+// One list-mode item (see ListItem in count_device.cuh): spans of at most
+// Rsub windows whose lists, plus two overflow lists of L slots, fit the CTA's
+// list_cap slots. A separate function (one call per item), so that the list
+// bookkeeping costs the cursor-mode walk no registers. Returns the visits
+// (listed neighbours, counted by thread 0).
+__device__ __noinline__ uint64_t sweep_list_item(const CsrView& g, const SweepItem& item, const PivotGeom& q,
+                                                 uint2* my_lists, int64_t list_cap, int* cnt, int* ocnt,
+                                                 uint32_t sbase, uint32_t* cnt_words, uint32_t* nb_next_p,
+                                                 uint64_t& bal, uint64_t& unb) {
+  const int tid = threadIdx.x;
+  const ItemWindows iw(item);
+  const uint32_t R = iw.count();
+  const bool fin = (item.flags & kItemFinalize) != 0;
+  const int64_t per_nb = list_cap / (int64_t)q.L;
+  uint32_t& nb_next = *nb_next_p;
+  uint64_t n_visits = 0;
+  const uint32_t Rsub = (uint32_t)(per_nb - 2 < kListMaxWindows ? per_nb - 2 : kListMaxWindows);
+  int in_buf = 0;  // overflow list feeding the next span
+  for (uint32_t s0 = 0; s0 < R; s0 += Rsub) {
+    const uint32_t nwin = min(Rsub, R - s0);
+    uint32_t span_lo, span_hi, wlo, whi;
+    int cw;
+    iw.window(s0, span_lo, whi, cw);
+    iw.window(s0 + nwin - 1, wlo, span_hi, cw);
+    if (tid < kListMaxWindows) cnt[tid] = 0;
+    if (tid == 0) ocnt[in_buf ^ 1] = 0;
+    __syncthreads();
+    const ListItem li{my_lists, cnt, my_lists + (size_t)(Rsub + (in_buf ^ 1)) * q.L, &ocnt[in_buf ^ 1], q.L,
+                      iw, s0, span_hi << 1, item.hi << 1};
+    if (s0 == 0) {  // each neighbour joins the list of the window of its first entry
+      for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
+        uint32_t b, en, s1;
+        lean_cursor_start(g, q, i, item.lo, b, en, s1);
+        if (b < en) list_append(li, g.col[b], b, en, s1);
+      }
+    } else {  // the neighbours that waited for this span
+      const uint32_t n_in = (uint32_t)ocnt[in_buf];
+      const uint2* in = my_lists + (size_t)(Rsub + in_buf) * q.L;
+      for (uint32_t j = tid; j < n_in; j += kSweepThreads) {
+        const uint2 e = in[j];
+        const uint32_t c = e.x, en = e.x + (e.y & 0x7FFFFFFFu);
+        list_append(li, g.col[c], c, en, e.y >> 31);
+      }
+    }
+    __syncthreads();
+    for (uint32_t r = 0; r < nwin; r++) {
+      iw.window(s0 + r, wlo, whi, cw);
+      const uint32_t n = (uint32_t)cnt[r];
+      const uint2* list = my_lists + (size_t)r * q.L;
+      const Win w = make_win(cw, wlo, whi, sbase);
+      if (cw == 8) {
+        if (fin) lean_list_window_dispatch<8, false>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
+        else lean_list_window_dispatch<8, true>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
+      } else if (cw == 16) {
+        if (fin) lean_list_window_dispatch<16, false>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
+        else lean_list_window_dispatch<16, true>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
+      } else {
+        if (fin) lean_list_window_dispatch<32, false>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
+        else lean_list_window_dispatch<32, true>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
+      }
+      n_visits += tid == 0 ? n : 0;
+      __syncthreads();  // also publishes the appends made to later windows' lists
+      if (cw == 8) {
+        if (fin) lean_clear<8, true>(cnt_words, w.words, bal, unb);
+        else lean_clear<8, false>(cnt_words, w.words, bal, unb);
+      } else if (cw == 16) {
+        if (fin) lean_clear<16, true>(cnt_words, w.words, bal, unb);
+        else lean_clear<16, false>(cnt_words, w.words, bal, unb);
+      } else {
+        if (fin) lean_clear<32, true>(cnt_words, w.words, bal, unb);
+        else lean_clear<32, false>(cnt_words, w.words, bal, unb);
+      }
+      if (tid == 0) nb_next = 0u;
+      __syncthreads();
+    }
+    in_buf ^= 1;
+  }
+  return n_visits;
+}
+
 // Items are pulled dynamically in descending estimated work (LPT). An item in
 // list mode (count_device.cuh) uses per-window neighbour lists in `lists`
 // (list_cap slots per CTA); with no room for them (list_cap below three slots
 // per lower neighbour) it is swept by cursors like every other item, which
-// gives the same counts.
+// gives the same counts. The walk itself is in sweep_device.cuh.
 __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
                                                                       int64_t n_items, int* next_item,
-                                                                      uint32_t* __restrict__ cursors, int64_t cur_cap,
+                                                                      uint2* __restrict__ cursors, int64_t cur_cap,
                                                                       uint2* __restrict__ lists, int64_t list_cap,
                                                                       unsigned long long* out,
                                                                       unsigned long long* visits) {
   extern __shared__ __align__(16) unsigned char sweep_smem[];
-  uint32_t* c16 = reinterpret_cast<uint32_t*>(sweep_smem);
-  unsigned long long* c32 = reinterpret_cast<unsigned long long*>(sweep_smem);
+  uint32_t* cnt_words = reinterpret_cast<uint32_t*>(sweep_smem);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sweep_smem);
   __shared__ int item_sh;
   __shared__ int cnt[kListMaxWindows];
   __shared__ int ocnt[2];
+  __shared__ uint32_t nb_next;
   const int tid = threadIdx.x;
-  zero_words(c16, kSweepWindow16);
-  uint32_t* cur = cursors + (int64_t)blockIdx.x * cur_cap * 2;
+  zero_words(cnt_words, kSweepWords);
+  if (tid == 0) nb_next = 0u;
+  uint2* cur = cursors + (int64_t)blockIdx.x * cur_cap;
   uint2* my_lists = lists ? lists + (int64_t)blockIdx.x * list_cap : nullptr;
   uint64_t bal = 0, unb = 0, n_visits = 0;
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
-    __syncthreads();  // also orders the zeroing above / below before reuse
+    __syncthreads();  // also orders the clearing above / below before reuse
     const int64_t it = item_sh;
     __syncthreads();
     if (it >= n_items) break;
@@ -119,70 +201,25 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     const PivotGeom q = pivot_geom(g, item.row);
     const ItemWindows iw(item);
     const uint32_t R = iw.count();
+    const bool fin = (item.flags & kItemFinalize) != 0;
     // list scratch per item: Rsub window lists + two overflow lists of L slots
     const int64_t per_nb = q.L ? list_cap / (int64_t)q.L : 0;
     const bool listed = (item.flags & kItemList) != 0 && my_lists != nullptr && per_nb >= 3;
     if (listed) {
-      const uint32_t Rsub = (uint32_t)(per_nb - 2 < kListMaxWindows ? per_nb - 2 : kListMaxWindows);
-      int in_buf = 0;  // overflow list feeding the next span
-      for (uint32_t s0 = 0; s0 < R; s0 += Rsub) {
-        const uint32_t nwin = min(Rsub, R - s0);
-        uint32_t span_lo, span_hi, wlo, whi;
-        int cw;
-        iw.window(s0, span_lo, whi, cw);
-        iw.window(s0 + nwin - 1, wlo, span_hi, cw);
-        if (tid < kListMaxWindows) cnt[tid] = 0;
-        if (tid == 0) ocnt[in_buf ^ 1] = 0;
-        __syncthreads();
-        const ListItem li{my_lists, cnt, my_lists + (size_t)(Rsub + (in_buf ^ 1)) * q.L, &ocnt[in_buf ^ 1], q.L,
-                          iw, s0, span_hi << 1, item.hi << 1};
-        if (s0 == 0) {  // each neighbour joins the list of the window of its first entry
-          for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
-            uint32_t b, en;
-            init_cursor(g, q, i, item.lo, cur, b, en);
-            if (b < en) list_append(li, g.col[b], b, en, g.col[q.rb + i] & 1u);
-          }
-        } else {  // the neighbours that waited for this span
-          const uint32_t n_in = (uint32_t)ocnt[in_buf];
-          const uint2* in = my_lists + (size_t)(Rsub + in_buf) * q.L;
-          for (uint32_t j = tid; j < n_in; j += kSweepThreads) {
-            const uint2 e = in[j];
-            const uint32_t c = e.x, en = e.x + (e.y & 0x7FFFFFFFu);
-            list_append(li, g.col[c], c, en, e.y >> 31);
-          }
-        }
-        __syncthreads();
-        for (uint32_t r = 0; r < nwin; r++) {
-          iw.window(s0 + r, wlo, whi, cw);
-          const uint32_t n = (uint32_t)cnt[r];
-          const uint2* list = my_lists + (size_t)r * q.L;
-          if (cw == 8) list_window_dispatch<8>(item.group_log, g, li, list, n, wlo, whi << 1, c16, c32, bal, unb);
-          else if (cw == 16) list_window_dispatch<16>(item.group_log, g, li, list, n, wlo, whi << 1, c16, c32, bal, unb);
-          else list_window_dispatch<32>(item.group_log, g, li, list, n, wlo, whi << 1, c16, c32, bal, unb);
-          n_visits += tid == 0 ? n : 0;
-          __syncthreads();  // also publishes the appends made to later windows' lists
-          zero_words(c16, item_words(cw, whi - wlo));
-          __syncthreads();
-        }
-        in_buf ^= 1;
-      }
+      n_visits += sweep_list_item(g, item, q, my_lists, list_cap, cnt, ocnt, sbase, cnt_words, &nb_next, bal, unb);
       continue;
     }
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
-      uint32_t b, en;
-      init_cursor(g, q, i, item.lo, cur, b, en);
+      uint32_t b, en, s1;
+      lean_cursor_start(g, q, i, item.lo, b, en, s1);
+      cur[i] = lean_slot(b, en, s1);
     }
     __syncthreads();
     for (uint32_t r = 0; r < R; r++) {
       uint32_t lo, hi;
       int cw;
       iw.window(r, lo, hi, cw);
-      if (cw == 8) sweep_window_dispatch<8>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      else if (cw == 16) sweep_window_dispatch<16>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      else sweep_window_dispatch<32>(item.group_log, g, q, cur, lo, hi << 1, c16, c32, bal, unb);
-      __syncthreads();
-      zero_words(c16, item_words(cw, hi - lo));
-      __syncthreads();
+      lean_sweep_cursor(cw, fin, item.group_log, g.col, q.L, cur, lo, hi, sbase, cnt_words, &nb_next, bal, unb);
     }
   }
   block_add_pair<kSweepThreads>(bal, unb, out);
@@ -231,23 +268,57 @@ CountProfiler::~CountProfiler() {
   }
 }
 
+// Launches of the three tiers, shared by enqueue_count and
+// enqueue_count_prealloc.
+static void launch_light(const dbbc_graph* g, const CsrView& view, cudaStream_t s, unsigned long long* d_out,
+                         unsigned* d_status) {
+  const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
+  DBBC_CUDA(cudaFuncSetAttribute(count_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
+  const int64_t cap = (int64_t)num_sms() * blocks_per_sm((const void*)count_light_kernel, kLightWarps * 32, smem);
+  count_light_kernel<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
+      view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, d_out, d_status);
+  DBBC_LAUNCH_CHECK();
+}
+
+static void launch_medium(const dbbc_graph* g, const CsrView& view, cudaStream_t s, unsigned long long* d_out,
+                          unsigned* d_status) {
+  const size_t smem = (size_t)kMediumSlots * 12;
+  DBBC_CUDA(cudaFuncSetAttribute(count_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t cap = (int64_t)num_sms() * blocks_per_sm((const void*)count_medium_kernel, kMediumThreads, smem);
+  count_medium_kernel<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
+      view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, d_out, d_status);
+  DBBC_LAUNCH_CHECK();
+}
+
+// CTAs the hub sweep can keep resident (one per SM: its counters fill the
+// SM's shared memory).
+static int64_t hub_full_grid() {
+  DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem));
+  return (int64_t)num_sms() * blocks_per_sm((const void*)hub_sweep_kernel, kSweepThreads, kSweepSmem);
+}
+
+// The hub sweep on `grid` CTAs with per-CTA cursors (sweep_max_lower each)
+// and, if `lists` is given, per-CTA list scratch (sweep_list_cap slots each);
+// `next` is the item counter, cleared here.
+static void launch_hub(const dbbc_graph* g, const CsrView& view, cudaStream_t s, int grid, int* next,
+                       uint2* cursors, uint2* lists, unsigned long long* d_out, unsigned long long* visits) {
+  DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
+  hub_sweep_kernel<<<grid, kSweepThreads, kSweepSmem, s>>>(view, g->sweep_items, g->n_sweep_items, next, cursors,
+                                                           g->sweep_max_lower, lists,
+                                                           lists ? g->sweep_list_cap : 0, d_out, visits);
+  DBBC_LAUNCH_CHECK();
+}
+
 void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_out, unsigned* d_status,
                    Scratch& sc, CountProfiler* prof) {
   if (g->n_piv == 0) return;
   const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
-  const int sms = num_sms();
   cudaEvent_t t_all = prof ? prof->begin(s) : nullptr;
   cudaEvent_t t0 = nullptr;
-
   if (g->n_light > 0) {
     if (prof) t0 = prof->begin(s);
-    const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
-    DBBC_CUDA(cudaFuncSetAttribute(count_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
-    const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_light_kernel, kLightWarps * 32, smem);
-    count_light_kernel<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
-        view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, d_out, d_status);
-    DBBC_LAUNCH_CHECK();
+    launch_light(g, view, s, d_out, d_status);
     if (prof) {
       prof->end(CountProfiler::LIGHT, t0, s);
       prof->launches[CountProfiler::LIGHT]++;
@@ -255,34 +326,23 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
   }
   if (g->n_medium > 0) {
     if (prof) t0 = prof->begin(s);
-    const size_t smem = (size_t)kMediumSlots * 12;
-    DBBC_CUDA(cudaFuncSetAttribute(count_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_medium_kernel, kMediumThreads, smem);
-    count_medium_kernel<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
-        view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, d_out, d_status);
-    DBBC_LAUNCH_CHECK();
+    launch_medium(g, view, s, d_out, d_status);
     if (prof) {
       prof->end(CountProfiler::MEDIUM, t0, s);
       prof->launches[CountProfiler::MEDIUM]++;
     }
   }
   if (g->n_hub > 0) {
-    const size_t smem = (size_t)kSweepWindow16 * 4;
-    DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = sms * blocks_per_sm((const void*)hub_sweep_kernel, kSweepThreads, smem);
-    uint32_t* cursors = sc.get<uint32_t>((size_t)grid * (size_t)g->sweep_max_lower * 2);
+    const int grid = (int)hub_full_grid();
+    uint2* cursors = sc.get<uint2>((size_t)grid * (size_t)g->sweep_max_lower);
     uint2* lists = g->sweep_list_cap > 0 ? sc.get<uint2>((size_t)grid * (size_t)g->sweep_list_cap) : nullptr;
     int* next = sc.get<int>(1);
-    DBBC_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
     if (prof) {
       prof->d_visits = sc.get<unsigned long long>(1);
       DBBC_CUDA(cudaMemsetAsync(prof->d_visits, 0, sizeof(unsigned long long), s));
       t0 = prof->begin(s);
     }
-    hub_sweep_kernel<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, next, cursors,
-                                                       g->sweep_max_lower, lists, g->sweep_list_cap, d_out,
-                                                       prof ? prof->d_visits : nullptr);
-    DBBC_LAUNCH_CHECK();
+    launch_hub(g, view, s, grid, next, cursors, lists, d_out, prof ? prof->d_visits : nullptr);
     if (prof) {
       prof->end(CountProfiler::HUB_AGG, t0, s);
       prof->launches[CountProfiler::HUB_AGG]++;
@@ -291,54 +351,29 @@ void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_ou
   if (prof) prof->end(CountProfiler::TOTAL, t_all, s);
 }
 
-}  // namespace dbbc
-
-namespace dbbc {
-
 // The kernels of enqueue_count with all device scratch supplied by the caller:
 // d_status (one word) and d_next (one int) are cleared here, and the hub
-// sweep keeps its per-CTA cursors in `cursors` (cursor_bytes long), which
-// bounds how many CTAs it can run. Throws DBBC_EOVERFLOW when not even one
-// CTA's cursors fit.
+// sweep keeps its per-CTA cursors (8 bytes per lower neighbour of the largest
+// hub) in `cursors` (cursor_bytes long, 8-byte aligned), which bounds how many
+// CTAs it can run; it runs without list scratch (cursor mode for every item,
+// same counts). Throws DBBC_EOVERFLOW when not even one CTA's cursors fit.
 void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_out, unsigned* d_status,
                             int* d_next, uint32_t* cursors, size_t cursor_bytes) {
   DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
   DBBC_CUDA(cudaMemsetAsync(d_out, 0, 2 * sizeof(unsigned long long), s));
   if (g->n_piv == 0) return;
   const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
-  const int sms = num_sms();
   int64_t hub_grid = 0;
   if (g->n_hub > 0) {
-    const size_t per_cta = (size_t)g->sweep_max_lower * 2 * sizeof(uint32_t);
+    const size_t per_cta = (size_t)g->sweep_max_lower * sizeof(uint2);
     hub_grid = (int64_t)(cursor_bytes / per_cta);
     if (hub_grid < 1) throw Error{DBBC_EOVERFLOW, "hub cursors exceed the fixed scratch"};
   }
-  if (g->n_light > 0) {
-    const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
-    DBBC_CUDA(cudaFuncSetAttribute(count_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
-    const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_light_kernel, kLightWarps * 32, smem);
-    count_light_kernel<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
-        view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, d_out, d_status);
-    DBBC_LAUNCH_CHECK();
-  }
-  if (g->n_medium > 0) {
-    const size_t smem = (size_t)kMediumSlots * 12;
-    DBBC_CUDA(cudaFuncSetAttribute(count_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_medium_kernel, kMediumThreads, smem);
-    count_medium_kernel<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
-        view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, d_out, d_status);
-    DBBC_LAUNCH_CHECK();
-  }
+  if (g->n_light > 0) launch_light(g, view, s, d_out, d_status);
+  if (g->n_medium > 0) launch_medium(g, view, s, d_out, d_status);
   if (g->n_hub > 0) {
-    const size_t smem = (size_t)kSweepWindow16 * 4;
-    DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t full = (int64_t)sms * blocks_per_sm((const void*)hub_sweep_kernel, kSweepThreads, smem);
-    const int grid = (int)std::min<int64_t>(full, hub_grid);
-    DBBC_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
-    hub_sweep_kernel<<<grid, kSweepThreads, smem, s>>>(view, g->sweep_items, g->n_sweep_items, d_next, cursors,
-                                                       g->sweep_max_lower, nullptr, 0, d_out, nullptr);
-    DBBC_LAUNCH_CHECK();
+    const int grid = (int)std::min<int64_t>(hub_full_grid(), hub_grid);
+    launch_hub(g, view, s, grid, d_next, reinterpret_cast<uint2*>(cursors), nullptr, d_out, nullptr);
   }
 }
 

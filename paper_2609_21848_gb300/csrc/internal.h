@@ -55,6 +55,11 @@ constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per wor
 constexpr int kListMaxWindows = 64;
 constexpr int64_t kListCapEntries = int64_t{1} << 22;
 
+// Hub items with at least this many estimated wedges per window finalise each
+// window by a scan of its counters (kItemFinalize); sparser ones take the
+// Lemma 1 contribution of every wedge from its atomic's old value.
+constexpr uint64_t kFinalizeWindowWedges = 65536;
+
 // Runtime tuning (dbbc_set_tuning), snapshotted into every graph at build.
 struct Tuning {
   uint64_t light_max_work = kLightMaxWork;
@@ -64,6 +69,7 @@ struct Tuning {
   int32_t hash_mult_log = 1;
   double list_density = 8.0;  // hubs with a mean (neighbour, window) segment shorter than this use list mode
   int32_t list_group_log = 2; // lanes per neighbour segment in list mode (log2)
+  uint64_t finalize_window_wedges = kFinalizeWindowWedges;  // see kItemFinalize
 };
 Tuning current_tuning();  // a copy, taken under the tuning lock
 
@@ -85,9 +91,12 @@ struct SweepItem {
   uint32_t t_end;
   uint32_t n_end;
   int16_t group_log;
-  int16_t flags;  // kItemList
+  int16_t flags;  // kItemList | kItemFinalize
 };
 constexpr int16_t kItemList = 2;  // list mode: visit a neighbour only in windows holding its entries
+// counters of a window are finalised when it is cleared (C(p,2) + C(q,2) and
+// p*q per endpoint) instead of wedge by wedge
+constexpr int16_t kItemFinalize = 4;
 // Counts below this fit the 8-bit halves of a tiny counter.
 constexpr int32_t kTinyCountLimit = 256;
 

@@ -1,0 +1,438 @@
+// The hub tier's window sweep (Algorithm 1, Phase 5, for pivots with many
+// accepted wedges): the inner loop shared by the single-graph and batched
+// sweep kernels.
+//
+// A work item is one hub pivot and a span of its endpoint ranks, owned by one
+// CTA; the span is cut into windows whose counters fill the CTA's shared
+// memory (see ItemWindows in count_device.cuh for the 8/16/32-bit counter
+// widths). Every lower neighbour v of the hub keeps a cursor into its row;
+// rows ascend by rank, so the entries of v inside a window are the next run of
+// its row and the cursor only moves forward across windows.
+//
+// Per entry the walk does one compare, the counter's shared address, the
+// packed increment and one predicated shared-memory atomic; the segment end is
+// detected once per chunk (the group's last entry), and the next chunk is
+// loaded before the current one is counted. Lemma 1 is applied in one of two
+// ways, chosen per item by its wedges per window:
+//
+//   * per wedge (RET): the atomic returns the endpoint's counter before the
+//     increment, and a symmetric wedge that raises (p, q) to (p + 1, q) closes
+//     p balanced and q unbalanced butterflies (an asymmetric one q and p);
+//   * per window (FIN): the atomics return nothing, and when the window is
+//     cleared every endpoint adds C(p,2) + C(q,2) balanced and p * q unbalanced
+//     butterflies from its final counter. This is the paper's finalisation over
+//     the touched endpoints, done for the whole window at once.
+#pragma once
+
+#include "count_device.cuh"
+
+namespace dbbc {
+
+// entries per lane per chunk, and neighbours a lane group starts together
+#ifndef DBBC_LEAN_UNROLL
+#define DBBC_LEAN_UNROLL 4
+#endif
+#ifndef DBBC_LEAN_BATCH
+#define DBBC_LEAN_BATCH 1
+#endif
+constexpr int kLU = DBBC_LEAN_UNROLL;
+constexpr int kLB = DBBC_LEAN_BATCH;
+
+// Shared counters of the sweep: one window, plus one word so that a window of
+// 8-bit counters may start at the even rank below its first rank.
+constexpr uint32_t kSweepWords = kSweepWindow16 + 4;
+constexpr size_t kSweepSmem = (size_t)kSweepWords * 4;
+
+// A window of side ranks [wlo, whi): entries below h lie in it (cursors start
+// at its first rank), and the counter word of rank r is at shared byte address
+// wb + (r >> 1) * 4 (8-bit counters, two ranks per word, rank pairs aligned to
+// an even rank), wb + r * 4 (16-bit) or wb + r * 8 (32-bit).
+struct Win {
+  uint32_t h;
+  uint32_t wb;
+  uint32_t words;  // 32-bit words in use
+};
+
+__device__ __forceinline__ Win make_win(int cw, uint32_t wlo, uint32_t whi, uint32_t sbase) {
+  Win w;
+  w.h = whi << 1;
+  if (cw == 8) {
+    const uint32_t l2 = wlo & ~1u;
+    w.wb = sbase - l2 * 2u;
+    w.words = (whi - l2 + 1u) >> 1;
+  } else if (cw == 16) {
+    w.wb = sbase - wlo * 4u;
+    w.words = whi - wlo;
+  } else {
+    w.wb = sbase - wlo * 8u;
+    w.words = 2u * (whi - wlo);
+  }
+  return w;
+}
+
+// Shared-memory atomics on 32-bit shared addresses, taken only when x < h.
+__device__ __forceinline__ void red_if_u32(uint32_t x, uint32_t h, uint32_t addr, uint32_t v) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %0, %1;\n\t@p red.shared.add.u32 [%2], %3;\n\t}"
+               :: "r"(x), "r"(h), "r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_if_u32(uint32_t x, uint32_t h, uint32_t addr, uint32_t v) {
+  uint32_t old;
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\tmov.u32 %0, 0;\n\t@p atom.shared.add.u32 %0, [%3], %4;\n\t}"
+               : "=r"(old) : "r"(x), "r"(h), "r"(addr), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_if_u64(uint32_t x, uint32_t h, uint32_t addr, uint64_t v) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %0, %1;\n\t@p red.shared.add.u64 [%2], %3;\n\t}"
+               :: "r"(x), "r"(h), "r"(addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t atom_if_u64(uint32_t x, uint32_t h, uint32_t addr, uint64_t v) {
+  uint64_t old;
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\tmov.u64 %0, 0;\n\t@p atom.shared.add.u64 %0, [%3], %4;\n\t}"
+               : "=l"(old) : "r"(x), "r"(h), "r"(addr), "l"(v) : "memory");
+  return old;
+}
+
+// Count one entry x (a CSR entry (side_rank << 1) | negative) of a neighbour
+// whose edge to the hub has sign bit s1, if x < h. The wedge is symmetric when
+// the two sign bits agree (bucket B1 of Algorithm 1, the low half of the
+// packed counter) and asymmetric otherwise (B2, the high half). With RET the
+// counter's old value gives the Lemma 1 contribution: rotated so that the
+// wedge's own class is in the low half, it is summed into a_lo (own + other
+// << 16, mod 2^32) and a_hi (other); the 64-bit width adds to bal / unb.
+template <int CW, bool RET>
+__device__ __forceinline__ void lean_add(uint32_t x, uint32_t h, uint32_t s1, uint32_t wb, uint32_t& a_lo,
+                                         uint32_t& a_hi, uint64_t& bal, uint64_t& unb) {
+  if constexpr (CW == 8) {
+    // byte (2 * (rank & 1) + asym) of the word: (asym1, sym1, asym0, sym0)
+    const uint32_t sel = (x ^ s1) & 3u;
+    const uint32_t addr = wb + (x & ~3u);
+    const uint32_t inc = 1u << (sel << 3);
+    if constexpr (!RET) {
+      red_if_u32(x, h, addr, inc);
+    } else {
+      const uint32_t old = atom_if_u32(x, h, addr, inc);
+      // own class byte to byte 0, the other class to byte 2
+      const uint32_t v = __byte_perm(old, 0u, (sel * 0x101u) ^ 0x4140u);
+      a_lo += v;
+      a_hi += v >> 16;
+    }
+  } else if constexpr (CW == 16) {
+    const uint32_t asym = (x ^ s1) & 1u;
+    const uint32_t addr = wb + ((x >> 1) << 2);
+    const uint32_t inc = 1u + asym * 0xFFFFu;
+    if constexpr (!RET) {
+      red_if_u32(x, h, addr, inc);
+    } else {
+      const uint32_t old = atom_if_u32(x, h, addr, inc);
+      const uint32_t v = __funnelshift_l(old, old, asym << 4);
+      a_lo += v;
+      a_hi += v >> 16;
+    }
+  } else {
+    const uint32_t asym = (x ^ s1) & 1u;
+    const uint32_t addr = wb + ((x >> 1) << 3);
+    const uint64_t inc = asym ? (1ull << 32) : 1ull;
+    if constexpr (!RET) {
+      red_if_u64(x, h, addr, inc);
+    } else {
+      const uint64_t old = atom_if_u64(x, h, addr, inc);
+      const uint64_t p = old & 0xFFFFFFFFull, q = old >> 32;
+      bal += asym ? q : p;
+      unb += asym ? p : q;
+    }
+  }
+}
+
+// x[u] = the entry at position c + u*G + gl of a row ending at en, or ~0 past
+// the end (en >= c).
+template <int G>
+__device__ __forceinline__ void lean_load(const uint32_t* __restrict__ col, uint32_t c, uint32_t en, int gl,
+                                          uint32_t (&x)[kLU]) {
+  const uint32_t rem = en - c;
+  const uint32_t* p = col + c + (uint32_t)gl;
+#pragma unroll
+  for (int u = 0; u < kLU; u++) x[u] = (uint32_t)(u * G + gl) < rem ? __ldg(p + u * G) : 0xFFFFFFFFu;
+}
+
+// A group of G lanes walks one neighbour's entries inside window w from
+// cursor c (row end en, first chunk already in x) and returns the cursor past
+// the window; x_next gets the neighbour's first entry past the window (~0 at
+// the end of its row). All groups of the warp run the loop in lockstep until
+// the last of them is done: the loop's only exit follows a warp-wide vote, so
+// every shuffle and vote in it is reached by the whole warp. A group that is
+// not `active` (no neighbour) only votes.
+template <int G, int CW, bool RET>
+__device__ __forceinline__ uint32_t lean_walk(const uint32_t* __restrict__ col, uint32_t c, uint32_t en, uint32_t s1,
+                                              uint32_t (&x)[kLU], const Win& w, int gl, bool active, uint64_t& bal,
+                                              uint64_t& unb, uint32_t& x_next) {
+  const unsigned lane = lane_id();
+  const unsigned gbase = lane & ~(unsigned)(G - 1);
+  uint32_t h = active ? w.h : 0u;
+  uint32_t a_lo = 0, a_hi = 0;
+  for (;;) {
+    // the chunk lies wholly inside the window iff its last entry does
+    uint32_t xl = x[kLU - 1];
+    if constexpr (G > 1) xl = __shfl_sync(kFullMask, xl, gbase + (G - 1));
+    const bool cont = xl < h;
+    uint32_t y[kLU];
+    const uint32_t cn = c + (uint32_t)(G * kLU);
+    lean_load<G>(col, cn, cont ? en : cn, gl, y);  // the next chunk, while this one is counted
+#pragma unroll
+    for (int u = 0; u < kLU; u++) lean_add<CW, RET>(x[u], h, s1, w.wb, a_lo, a_hi, bal, unb);
+    if (!__any_sync(kFullMask, cont)) break;
+    if (cont) {
+      c = cn;
+#pragma unroll
+      for (int u = 0; u < kLU; u++) x[u] = y[u];
+    } else {
+      h = 0u;  // done: keep its last chunk in x, count nothing more
+    }
+  }
+  // the accepted entries of the group's last chunk are a prefix of it
+  uint32_t n_ok = 0;
+#pragma unroll
+  for (int u = 0; u < kLU; u++) {
+    const unsigned b = __ballot_sync(kFullMask, x[u] < w.h);
+    n_ok += G == 32 ? __popc(b) : __popc((b >> gbase) & ((1u << G) - 1u));
+  }
+  const uint32_t ui = n_ok / G;
+  uint32_t t = x[0];
+#pragma unroll
+  for (int u = 1; u < kLU; u++) t = ui == (uint32_t)u ? x[u] : t;
+  x_next = G == 1 ? t : __shfl_sync(kFullMask, t, gbase + (n_ok & (G - 1)));
+  if constexpr (RET && CW != 32) {
+    // a_lo = own + (other << 16) mod 2^32; the own-class sum of one segment
+    // stays below 2^32 (at most 57,344 entries of counts < 2^16, or 114,688
+    // of counts < 2^8)
+    bal += a_lo - (a_hi << 16);
+    unb += a_hi;
+  }
+  return c + n_ok;
+}
+
+// Neighbour cursors of an item, one uint2 per lower neighbour i:
+// {position, (entries left in its row) | (sign bit of the hub's edge to it) << 31}.
+__device__ __forceinline__ void lean_cursor_start(const CsrView& g, const PivotGeom& q, uint32_t i, uint32_t lo_rank,
+                                                  uint32_t& b_out, uint32_t& en_out, uint32_t& s1_out) {
+  const uint32_t e = g.col[q.rb + i];
+  const int64_t vrow = q.base + (e >> 1);
+  int64_t b = g.row_ptr[vrow];
+  const int64_t en = g.row_ptr[vrow + 1];
+  const uint32_t first = lo_rank << 1;
+  if (first) {  // lower_bound of `first` in the row
+    int64_t lo = b, hi = en;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (g.col[mid] < first) lo = mid + 1; else hi = mid;
+    }
+    b = lo;
+  }
+  b_out = (uint32_t)b;
+  en_out = (uint32_t)en;
+  s1_out = e & 1u;
+}
+
+__device__ __forceinline__ uint2 lean_slot(uint32_t c, uint32_t en, uint32_t s1) {
+  return make_uint2(c, (en - c) | (s1 << 31));
+}
+
+// The next batch of neighbour indices for this warp: groups of the warp take
+// base + group, base + group + groups_per_warp, ... (kLB each), handed out
+// through a shared counter so that warps that finish early take more.
+template <int G>
+__device__ __forceinline__ uint32_t lean_grab(uint32_t* nb_next) {
+  uint32_t base = 0;
+  if (lane_id() == 0) base = atomicAdd(nb_next, (uint32_t)(32 / G) * kLB);
+  return __shfl_sync(kFullMask, base, 0);
+}
+
+// One window, cursor mode: every lower neighbour (L of them) is walked from its
+// cursor.
+template <int G, int CW, bool RET>
+__device__ __forceinline__ void lean_cursor_window(const uint32_t* __restrict__ col, uint32_t L, uint2* cur,
+                                                   const Win& w, uint32_t* nb_next, uint64_t& bal, uint64_t& unb) {
+  const int gl = threadIdx.x & (G - 1);
+  const uint32_t gw = lane_id() / G;
+  constexpr uint32_t gpw = 32 / G;
+  for (;;) {
+    const uint32_t base = lean_grab<G>(nb_next);
+    if (base >= L) break;
+    uint32_t c[kLB], en[kLB], s1[kLB], x[kLB][kLU];
+#pragma unroll
+    for (int k = 0; k < kLB; k++) {
+      const uint32_t i = base + gw + k * gpw;
+      c[k] = en[k] = s1[k] = 0;
+      if (i < L) {
+        const uint2 e = cur[i];
+        c[k] = e.x;
+        en[k] = e.x + (e.y & 0x7FFFFFFFu);
+        s1[k] = e.y >> 31;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kLB; k++) lean_load<G>(col, c[k], en[k], gl, x[k]);
+#pragma unroll
+    for (int k = 0; k < kLB; k++) {
+      const uint32_t i = base + gw + k * gpw;
+      const bool active = i < L;
+      uint32_t xn;
+      const uint32_t cn = lean_walk<G, CW, RET>(col, c[k], en[k], s1[k], x[k], w, gl, active, bal, unb, xn);
+      if (active && gl == 0 && cn != c[k]) cur[i] = lean_slot(cn, en[k], s1[k]);
+    }
+  }
+}
+
+// One window of a list-mode item (see ListItem in count_device.cuh): the n
+// neighbours listed for it are walked from their slots, then queued by their
+// first entry past the window.
+template <int G, int CW, bool RET>
+__device__ __forceinline__ void lean_list_window(const uint32_t* __restrict__ col, const ListItem& li,
+                                                 const uint2* list, uint32_t n, const Win& w, uint32_t* nb_next,
+                                                 uint64_t& bal, uint64_t& unb) {
+  const int gl = threadIdx.x & (G - 1);
+  const uint32_t gw = lane_id() / G;
+  constexpr uint32_t gpw = 32 / G;
+  for (;;) {
+    const uint32_t base = lean_grab<G>(nb_next);
+    if (base >= n) break;
+    uint32_t c[kLB], en[kLB], s1[kLB], x[kLB][kLU];
+#pragma unroll
+    for (int k = 0; k < kLB; k++) {
+      const uint32_t j = base + gw + k * gpw;
+      c[k] = en[k] = s1[k] = 0;
+      if (j < n) {
+        const uint2 e = list[j];
+        c[k] = e.x;
+        en[k] = e.x + (e.y & 0x7FFFFFFFu);
+        s1[k] = e.y >> 31;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kLB; k++) lean_load<G>(col, c[k], en[k], gl, x[k]);
+#pragma unroll
+    for (int k = 0; k < kLB; k++) {
+      const uint32_t j = base + gw + k * gpw;
+      const bool active = j < n;
+      uint32_t xn;
+      const uint32_t cn = lean_walk<G, CW, RET>(col, c[k], en[k], s1[k], x[k], w, gl, active, bal, unb, xn);
+      if (active && gl == 0 && cn < en[k]) list_append(li, xn, cn, en[k], s1[k]);
+    }
+  }
+}
+
+// Clear the window's `words` counter words for the next window. With FIN,
+// first add every endpoint's Lemma 1 total from its final counter:
+// C(p,2) + C(q,2) balanced and p * q unbalanced butterflies.
+template <int CW, bool FIN>
+__device__ __forceinline__ void lean_clear(uint32_t* cnt, uint32_t words, uint64_t& bal, uint64_t& unb) {
+  uint4* q4 = reinterpret_cast<uint4*>(cnt);
+  const uint32_t quads = (words + 3u) >> 2;
+  if constexpr (!FIN) {
+    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) q4[j] = make_uint4(0u, 0u, 0u, 0u);
+  } else if constexpr (CW == 8) {
+    // bytes (q1, p1, q0, p0): sum of squares, sum, and twice the sum of
+    // p * q, by 4-way byte dot products (each per-thread sum < 2^32: at most
+    // 60 words of bytes < 256 per window)
+    uint32_t sq = 0, s = 0, pq2 = 0;
+    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) {
+      const uint4 v = q4[j];
+      if ((v.x | v.y | v.z | v.w) == 0u) continue;
+      const uint32_t a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        sq = __dp4a(a[k], a[k], sq);
+        s = __dp4a(a[k], 0x01010101u, s);
+        pq2 = __dp4a(a[k], __byte_perm(a[k], 0u, 0x2301u), pq2);
+      }
+      q4[j] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    bal += (uint64_t)((sq - s) >> 1);
+    unb += (uint64_t)(pq2 >> 1);
+  } else if constexpr (CW == 16) {
+    // C(p,2) + C(q,2) = C(p+q,2) - p*q
+    uint64_t ss = 0, pq = 0;
+    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) {
+      const uint4 v = q4[j];
+      if ((v.x | v.y | v.z | v.w) == 0u) continue;
+      const uint32_t a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const uint32_t p = a[k] & 0xFFFFu, q = a[k] >> 16, t = p + q;
+        ss += (uint64_t)t * (t - 1u);  // 0 when t = 0
+        pq += (uint64_t)p * q;
+      }
+      q4[j] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    bal += (ss >> 1) - pq;
+    unb += pq;
+  } else {
+    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) {
+      const uint4 v = q4[j];
+      if ((v.x | v.y | v.z | v.w) == 0u) continue;
+      const uint64_t p0 = v.x, q0 = v.y, p1 = v.z, q1 = v.w;
+      bal += (p0 * (p0 - 1) >> 1) + (q0 * (q0 - 1) >> 1) + (p1 * (p1 - 1) >> 1) + (q1 * (q1 - 1) >> 1);
+      unb += p0 * q0 + p1 * q1;
+      q4[j] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+}
+
+template <int CW, bool RET>
+__device__ __forceinline__ void lean_cursor_window_dispatch(int group_log, const uint32_t* __restrict__ col,
+                                                            uint32_t L, uint2* cur, const Win& w, uint32_t* nb_next,
+                                                            uint64_t& bal, uint64_t& unb) {
+  switch (group_log) {
+    case 0: lean_cursor_window<1, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
+    case 2: lean_cursor_window<4, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
+    case 3: lean_cursor_window<8, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
+    case 4: lean_cursor_window<16, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
+    default: lean_cursor_window<32, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
+  }
+}
+
+// The list-mode walker is a separate function (one call per window): the
+// list bookkeeping around it then costs the walk loop no registers.
+template <int CW, bool RET>
+__device__ __noinline__ void lean_list_window_dispatch(int group_log, const uint32_t* __restrict__ col,
+                                                          const ListItem& li, const uint2* list, uint32_t n,
+                                                          const Win& w, uint32_t* nb_next, uint64_t& bal,
+                                                          uint64_t& unb) {
+  switch (group_log) {
+    case 0: lean_list_window<1, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
+    case 2: lean_list_window<4, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
+    case 3: lean_list_window<8, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
+    case 4: lean_list_window<16, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
+    default: lean_list_window<32, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
+  }
+}
+
+// One window of a cursor-mode item: walk, then clear (finalising with FIN).
+// `nb_next` must be zero on entry and is zero again on return; the caller
+// has synchronised the block after the cursors were written.
+__device__ __forceinline__ void lean_sweep_cursor(int cw, bool fin, int group_log, const uint32_t* __restrict__ col,
+                                                  uint32_t L, uint2* cur, uint32_t wlo, uint32_t whi, uint32_t sbase,
+                                                  uint32_t* cnt, uint32_t* nb_next, uint64_t& bal, uint64_t& unb) {
+  const Win w = make_win(cw, wlo, whi, sbase);
+  if (cw == 8) {
+    if (fin) lean_cursor_window_dispatch<8, false>(group_log, col, L, cur, w, nb_next, bal, unb);
+    else lean_cursor_window_dispatch<8, true>(group_log, col, L, cur, w, nb_next, bal, unb);
+  } else if (cw == 16) {
+    if (fin) lean_cursor_window_dispatch<16, false>(group_log, col, L, cur, w, nb_next, bal, unb);
+    else lean_cursor_window_dispatch<16, true>(group_log, col, L, cur, w, nb_next, bal, unb);
+  } else {
+    if (fin) lean_cursor_window_dispatch<32, false>(group_log, col, L, cur, w, nb_next, bal, unb);
+    else lean_cursor_window_dispatch<32, true>(group_log, col, L, cur, w, nb_next, bal, unb);
+  }
+  __syncthreads();
+  if (cw == 8) {
+    if (fin) lean_clear<8, true>(cnt, w.words, bal, unb); else lean_clear<8, false>(cnt, w.words, bal, unb);
+  } else if (cw == 16) {
+    if (fin) lean_clear<16, true>(cnt, w.words, bal, unb); else lean_clear<16, false>(cnt, w.words, bal, unb);
+  } else {
+    if (fin) lean_clear<32, true>(cnt, w.words, bal, unb); else lean_clear<32, false>(cnt, w.words, bal, unb);
+  }
+  if (threadIdx.x == 0) *nb_next = 0u;
+  __syncthreads();
+}
+
+}  // namespace dbbc

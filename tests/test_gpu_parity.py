@@ -237,12 +237,24 @@ def _union_inputs(graphs):
     return u, v, s, off, [g.n_u for g in graphs], [g.n_v for g in graphs]
 
 
-@pytest.mark.parametrize("device_input", [False, True])
-def test_union_build_counts_each_component_exactly(device_input):
+@pytest.mark.parametrize("device_input,finalize", [(False, None), (True, None), (False, 0), (False, 2**64 - 1)])
+def test_union_build_counts_each_component_exactly(device_input, finalize):
     """dbbc_graph_from_coo_multi: per-component counts equal each graph counted
     alone (oracle), the plain count of the union is their sum, and duplicates
-    stay within their own component."""
+    stay within their own component. Components start at arbitrary (odd) ranks,
+    so 8-bit counter windows start at odd ranks too; `finalize` forces every hub
+    window through one Lemma 1 mode (scan on clear, or per wedge)."""
     import torch
+    base = dbbc.dbbc_get_tuning()
+    if finalize is not None:
+        dbbc.dbbc_set_tuning({"finalize_window_wedges": finalize, "light_max_work": 16, "medium_max_work": 64})
+    try:
+        _union_case(device_input, torch)
+    finally:
+        dbbc.dbbc_set_tuning(base)
+
+
+def _union_case(device_input, torch):
     rng = np.random.default_rng(21)
     graphs = [synth.batch_graph(i) for i in range(30)]
     graphs.insert(3, synth.Graph(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8), 4, 9))
@@ -285,6 +297,14 @@ def test_union_build_validates_each_component():
          hash_mult_log=2, list_density=1e9, list_group_log=5),   # list mode with whole-warp groups
     dict(light_max_work=512, medium_max_work=4096, hub_item_work=1 << 22, group_density=[40.0, 16.0, 6.0, 2.0],
          hash_mult_log=2, list_density=0.0, list_group_log=2),   # no list mode
+    dict(light_max_work=1, medium_max_work=1, hub_item_work=1024, group_density=[40.0, 16.0, 6.0, 2.0],
+         hash_mult_log=1, list_density=8.0, list_group_log=3,
+         finalize_window_wedges=0),   # every hub window finalised by a scan of its counters
+    dict(light_max_work=1, medium_max_work=1, hub_item_work=1024, group_density=[0.0, 0.0, 0.0, 0.0],
+         hash_mult_log=1, list_density=0.0, finalize_window_wedges=0),   # scan-finalised, 32-lane groups
+    dict(light_max_work=1, medium_max_work=1, hub_item_work=1024, group_density=[1e9, 1e9, 1e9, 1e9],
+         hash_mult_log=1, list_density=1e9, list_group_log=0,
+         finalize_window_wedges=2**64 - 1),   # every wedge's Lemma 1 term from its atomic, one lane
 ])
 def test_counts_do_not_depend_on_tuning(tuning):
     base = dbbc.dbbc_get_tuning()
