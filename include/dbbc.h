@@ -32,6 +32,9 @@
  *     pool (see dbbc_set_allocator).
  *   - A handle may be read by several counts at once (each count allocates its
  *     own scratch); it must not be freed while a count on it is in flight.
+ *     The one exception is dbbc_count_noalloc, which allocates nothing and
+ *     whose calls share one fixed device array: its calls must not overlap
+ *     on the GPU.
  */
 #ifndef DBBC_H
 #define DBBC_H
@@ -56,7 +59,7 @@ typedef enum {
   DBBC_EINVAL = 1,    /* bad argument or input (id out of range, sign not +-1, m < 0, duplicate under DUP_REJECT) */
   DBBC_ENOMEM = 2,    /* a device allocation failed */
   DBBC_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
-  DBBC_ETIMEOUT = 4,  /* a bounded device wait gave up (status word set by a kernel) */
+  DBBC_ETIMEOUT = 4,  /* reserved: no kernel of this library waits on another, so no call returns it */
   DBBC_EOVERFLOW = 5, /* a count or an internal capacity exceeded its type */
   DBBC_EINTERNAL = 6  /* an internal consistency check failed (a bug: please report) */
 } dbbc_status;

@@ -183,10 +183,10 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
   uint32_t* cnt_words = reinterpret_cast<uint32_t*>(sweep_smem);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sweep_smem);
   __shared__ int item_sh;
-  __shared__ uint32_t nb_next;
+  __shared__ uint32_t nbn[2];
   const int tid = threadIdx.x;
   zero_words(cnt_words, kSweepWords);
-  if (tid == 0) nb_next = 0u;
+  if (tid < 2) nbn[tid] = 0u;
   uint2* cur = cursors + (int64_t)blockIdx.x * cur_cap;
   for (;;) {
     if (tid == 0) item_sh = atomicAdd(next_item, 1);
@@ -198,8 +198,6 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     const SweepItem item = bi.it;
     const CsrView g = view_of(desc[bi.graph]);
     const PivotGeom q = pivot_geom(g, item.row);
-    const ItemWindows iw(item);
-    const bool fin = (item.flags & kItemFinalize) != 0;
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en, s1;
       lean_cursor_start(g, q, i, item.lo, b, en, s1);
@@ -207,12 +205,8 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     }
     __syncthreads();
     uint64_t bal = 0, unb = 0;
-    for (uint32_t r = 0; r < iw.count(); r++) {
-      uint32_t lo, hi;
-      int cw;
-      iw.window(r, lo, hi, cw);
-      lean_sweep_cursor(cw, fin, item.group_log, g.col, q.L, cur, lo, hi, sbase, cnt_words, &nb_next, bal, unb);
-    }
+    sweep_cursor_item_dispatch(item.group_log, g.col, q.L, cur, ItemWindows(item), (item.flags & kItemFinalize) != 0,
+                               sbase, cnt_words, nbn, bal, unb);
     block_add_pair<kSweepThreads>(bal, unb, out + 2 * bi.graph);
   }
 }

@@ -87,91 +87,11 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g,
 }
 
 // ------------------------------------------------------------------ hub tier
-// One list-mode item (see ListItem in count_device.cuh): spans of at most
-// Rsub windows whose lists, plus two overflow lists of L slots, fit the CTA's
-// list_cap slots. A separate function (one call per item), so that the list
-// bookkeeping costs the cursor-mode walk no registers. Returns the visits
-// (listed neighbours, counted by thread 0).
-__device__ __noinline__ uint64_t sweep_list_item(const CsrView& g, const SweepItem& item, const PivotGeom& q,
-                                                 uint2* my_lists, int64_t list_cap, int* cnt, int* ocnt,
-                                                 uint32_t sbase, uint32_t* cnt_words, uint32_t* nb_next_p,
-                                                 uint64_t& bal, uint64_t& unb) {
-  const int tid = threadIdx.x;
-  const ItemWindows iw(item);
-  const uint32_t R = iw.count();
-  const bool fin = (item.flags & kItemFinalize) != 0;
-  const int64_t per_nb = list_cap / (int64_t)q.L;
-  uint32_t& nb_next = *nb_next_p;
-  uint64_t n_visits = 0;
-  const uint32_t Rsub = (uint32_t)(per_nb - 2 < kListMaxWindows ? per_nb - 2 : kListMaxWindows);
-  int in_buf = 0;  // overflow list feeding the next span
-  for (uint32_t s0 = 0; s0 < R; s0 += Rsub) {
-    const uint32_t nwin = min(Rsub, R - s0);
-    uint32_t span_lo, span_hi, wlo, whi;
-    int cw;
-    iw.window(s0, span_lo, whi, cw);
-    iw.window(s0 + nwin - 1, wlo, span_hi, cw);
-    if (tid < kListMaxWindows) cnt[tid] = 0;
-    if (tid == 0) ocnt[in_buf ^ 1] = 0;
-    __syncthreads();
-    const ListItem li{my_lists, cnt, my_lists + (size_t)(Rsub + (in_buf ^ 1)) * q.L, &ocnt[in_buf ^ 1], q.L,
-                      iw, s0, span_hi << 1, item.hi << 1};
-    if (s0 == 0) {  // each neighbour joins the list of the window of its first entry
-      for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
-        uint32_t b, en, s1;
-        lean_cursor_start(g, q, i, item.lo, b, en, s1);
-        if (b < en) list_append(li, g.col[b], b, en, s1);
-      }
-    } else {  // the neighbours that waited for this span
-      const uint32_t n_in = (uint32_t)ocnt[in_buf];
-      const uint2* in = my_lists + (size_t)(Rsub + in_buf) * q.L;
-      for (uint32_t j = tid; j < n_in; j += kSweepThreads) {
-        const uint2 e = in[j];
-        const uint32_t c = e.x, en = e.x + (e.y & 0x7FFFFFFFu);
-        list_append(li, g.col[c], c, en, e.y >> 31);
-      }
-    }
-    __syncthreads();
-    for (uint32_t r = 0; r < nwin; r++) {
-      iw.window(s0 + r, wlo, whi, cw);
-      const uint32_t n = (uint32_t)cnt[r];
-      const uint2* list = my_lists + (size_t)r * q.L;
-      const Win w = make_win(cw, wlo, whi, sbase);
-      if (cw == 8) {
-        if (fin) lean_list_window_dispatch<8, false>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
-        else lean_list_window_dispatch<8, true>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
-      } else if (cw == 16) {
-        if (fin) lean_list_window_dispatch<16, false>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
-        else lean_list_window_dispatch<16, true>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
-      } else {
-        if (fin) lean_list_window_dispatch<32, false>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
-        else lean_list_window_dispatch<32, true>(item.group_log, g.col, li, list, n, w, &nb_next, bal, unb);
-      }
-      n_visits += tid == 0 ? n : 0;
-      __syncthreads();  // also publishes the appends made to later windows' lists
-      if (cw == 8) {
-        if (fin) lean_clear<8, true>(cnt_words, w.words, bal, unb);
-        else lean_clear<8, false>(cnt_words, w.words, bal, unb);
-      } else if (cw == 16) {
-        if (fin) lean_clear<16, true>(cnt_words, w.words, bal, unb);
-        else lean_clear<16, false>(cnt_words, w.words, bal, unb);
-      } else {
-        if (fin) lean_clear<32, true>(cnt_words, w.words, bal, unb);
-        else lean_clear<32, false>(cnt_words, w.words, bal, unb);
-      }
-      if (tid == 0) nb_next = 0u;
-      __syncthreads();
-    }
-    in_buf ^= 1;
-  }
-  return n_visits;
-}
-
 // Items are pulled dynamically in descending estimated work (LPT). An item in
-// list mode (count_device.cuh) uses per-window neighbour lists in `lists`
+// list mode (sweep_device.cuh) uses per-window neighbour lists in `lists`
 // (list_cap slots per CTA); with no room for them (list_cap below three slots
 // per lower neighbour) it is swept by cursors like every other item, which
-// gives the same counts. The walk itself is in sweep_device.cuh.
+// gives the same counts.
 __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, const SweepItem* __restrict__ items,
                                                                       int64_t n_items, int* next_item,
                                                                       uint2* __restrict__ cursors, int64_t cur_cap,
@@ -182,12 +102,11 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
   uint32_t* cnt_words = reinterpret_cast<uint32_t*>(sweep_smem);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sweep_smem);
   __shared__ int item_sh;
-  __shared__ int cnt[kListMaxWindows];
-  __shared__ int ocnt[2];
-  __shared__ uint32_t nb_next;
+  __shared__ ListState ls;
+  __shared__ uint32_t nbn[2];
   const int tid = threadIdx.x;
   zero_words(cnt_words, kSweepWords);
-  if (tid == 0) nb_next = 0u;
+  if (tid < 2) nbn[tid] = 0u;
   uint2* cur = cursors + (int64_t)blockIdx.x * cur_cap;
   uint2* my_lists = lists ? lists + (int64_t)blockIdx.x * list_cap : nullptr;
   uint64_t bal = 0, unb = 0, n_visits = 0;
@@ -199,14 +118,9 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
     if (it >= n_items) break;
     const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    const ItemWindows iw(item);
-    const uint32_t R = iw.count();
-    const bool fin = (item.flags & kItemFinalize) != 0;
-    // list scratch per item: Rsub window lists + two overflow lists of L slots
     const int64_t per_nb = q.L ? list_cap / (int64_t)q.L : 0;
-    const bool listed = (item.flags & kItemList) != 0 && my_lists != nullptr && per_nb >= 3;
-    if (listed) {
-      n_visits += sweep_list_item(g, item, q, my_lists, list_cap, cnt, ocnt, sbase, cnt_words, &nb_next, bal, unb);
+    if ((item.flags & kItemList) != 0 && my_lists != nullptr && per_nb >= 3) {
+      n_visits += sweep_list_item_dispatch(g, item, q, my_lists, list_cap, ls, sbase, cnt_words, nbn, bal, unb);
       continue;
     }
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
@@ -215,12 +129,8 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
       cur[i] = lean_slot(b, en, s1);
     }
     __syncthreads();
-    for (uint32_t r = 0; r < R; r++) {
-      uint32_t lo, hi;
-      int cw;
-      iw.window(r, lo, hi, cw);
-      lean_sweep_cursor(cw, fin, item.group_log, g.col, q.L, cur, lo, hi, sbase, cnt_words, &nb_next, bal, unb);
-    }
+    sweep_cursor_item_dispatch(item.group_log, g.col, q.L, cur, ItemWindows(item), (item.flags & kItemFinalize) != 0,
+                               sbase, cnt_words, nbn, bal, unb);
   }
   block_add_pair<kSweepThreads>(bal, unb, out);
   if (visits && tid == 0 && n_visits) atomicAdd(visits, (unsigned long long)n_visits);

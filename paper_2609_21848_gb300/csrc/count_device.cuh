@@ -213,7 +213,6 @@ constexpr int kMediumWarps = kMediumThreads / 32;
 // count can exceed that), else (asym << 32) | sym.
 constexpr int kSweepThreads = DBBC_SWEEP_THREADS;
 constexpr int kSweepUnroll = DBBC_SWEEP_UNROLL;
-constexpr int kSweepBatch = DBBC_SWEEP_BATCH;
 static_assert(kSweepWindow16 % 4 == 0, "window buffers are cleared 16 bytes at a time");
 
 // Clear the first `words` 32-bit words of a window (16 bytes per store; the
@@ -251,15 +250,12 @@ __device__ __forceinline__ uint32_t window_words(uint32_t ranks) {  // 32-bit wo
   return CW == 8 ? (ranks + 1) >> 1 : CW == 16 ? ranks : 2 * ranks;
 }
 
-__device__ __forceinline__ uint32_t item_words(int cw, uint32_t ranks) {
-  return cw == 8 ? window_words<8>(ranks) : cw == 16 ? window_words<16>(ranks) : window_words<32>(ranks);
-}
-
 // The windows of a work item: tiny ones over [lo, te), narrow ones over
 // [te, ne), wide ones over [ne, hi), numbered in rank order.
 struct ItemWindows {
   uint32_t lo, te, ne, hi;
   uint32_t rt, rn, rw;
+  ItemWindows() = default;
   __device__ __forceinline__ explicit ItemWindows(const SweepItem& it) {
     lo = it.lo;
     hi = it.hi;
@@ -363,60 +359,6 @@ __device__ __forceinline__ uint32_t walk_segment(const uint32_t* col, uint32_t c
   return c;
 }
 
-// One window of one item: every group of G lanes takes lower neighbours
-// gid, gid + groups, ... and walks the neighbour's row from its cursor until
-// an entry leaves the window. A group takes kSweepBatch neighbours at a time
-// and issues all their cursor loads, then all their first-chunk loads, before
-// walking any of them, so that kSweepBatch dependent load chains are in flight
-// per group instead of one. Warps loop in lockstep (see walk_segment).
-template <int G, int CW>
-__device__ __forceinline__ void sweep_window(const CsrView& g, const PivotGeom& q, uint32_t* cur, uint32_t lo,
-                                             uint32_t hl, uint32_t* c16, unsigned long long* c32, uint64_t& bal,
-                                             uint64_t& unb) {
-  const int gl = threadIdx.x & (G - 1);
-  const uint32_t gid = threadIdx.x / G;
-  constexpr uint32_t groups = kSweepThreads / G;
-  const uint32_t lo2 = lo << 1;
-  const uint32_t* col = g.col;
-  for (uint32_t i0 = gid; __any_sync(kFullMask, i0 < q.L); i0 += groups * kSweepBatch) {
-    uint32_t c[kSweepBatch], en[kSweepBatch], s1[kSweepBatch], x[kSweepBatch][kSweepUnroll];
-#pragma unroll
-    for (int k = 0; k < kSweepBatch; k++) {
-      const uint32_t i = i0 + k * groups;
-      c[k] = en[k] = s1[k] = 0;
-      if (i < q.L) {
-        const uint2 ce = *reinterpret_cast<const uint2*>(cur + 2 * i);  // cursor and row end
-        c[k] = ce.x;
-        en[k] = ce.y;
-        s1[k] = __ldg(col + q.rb + i) & 1u;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kSweepBatch; k++) load_chunk<G>(col, c[k], en[k], gl, x[k]);
-#pragma unroll
-    for (int k = 0; k < kSweepBatch; k++) {
-      const uint32_t i = i0 + k * groups;
-      const bool active = i < q.L;
-      const uint32_t cn =
-          walk_segment<G, CW>(col, c[k], en[k], s1[k], x[k], lo2, hl, gl, active, c16, c32, bal, unb);
-      if (active && gl == 0 && cn != c[k]) cur[2 * i] = cn;
-    }
-  }
-}
-
-template <int CW>
-__device__ __forceinline__ void sweep_window_dispatch(int group_log, const CsrView& g, const PivotGeom& q,
-                                                      uint32_t* cur, uint32_t lo, uint32_t hl, uint32_t* c16,
-                                                      unsigned long long* c32, uint64_t& bal, uint64_t& unb) {
-  switch (group_log) {
-    case 0: sweep_window<1, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
-    case 2: sweep_window<4, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
-    case 3: sweep_window<8, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
-    case 4: sweep_window<16, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
-    default: sweep_window<32, CW>(g, q, cur, lo, hl, c16, c32, bal, unb); break;
-  }
-}
-
 // Cursors of an item: the first entry of each lower neighbour's row at or
 // after rank `lo_rank`, and the row end.
 __device__ __forceinline__ void init_cursor(const CsrView& g, const PivotGeom& q, uint32_t i, uint32_t lo_rank,
@@ -438,90 +380,6 @@ __device__ __forceinline__ void init_cursor(const CsrView& g, const PivotGeom& q
   en_out = (uint32_t)en;
   cur[2 * i] = b_out;
   cur[2 * i + 1] = en_out;
-}
-
-// ------------------------------------------------------------------ hub tier, list mode
-// In a sparse hub most (lower neighbour, window) pairs are empty: the
-// neighbour's row has no entry in that window, yet the cursor sweep above
-// still reads its cursor there. In list mode a neighbour is visited only in the
-// windows that hold its entries. Window r of an item keeps a list (global
-// memory, L slots per window) of the neighbours whose next entry falls in it;
-// a slot carries the neighbour's whole state (cursor, entries left in its row,
-// edge sign), so a visit reads its slot and then the row. After walking its
-// entries in window r, a neighbour is appended to the list of the window of
-// its next entry (always a later window), or drops out at the end of its row
-// or of the item. Each neighbour is in at most one list at a time and in each
-// list at most once, so L slots per window never overflow.
-// An item in list mode runs as consecutive spans of at most `Rsub` windows
-// (so that the lists of a span fit the CTA's list scratch). A neighbour whose
-// next entry lies past the current span but inside the item waits in an
-// overflow list and is queued into the next span's windows when that span
-// starts, so each neighbour's row is searched only once per item.
-struct ListItem {
-  uint2* lists;      // [windows][L] {cursor, entries left | sign << 31}
-  int* cnt;          // [windows] list lengths (shared memory)
-  uint2* over;       // [L] neighbours waiting for a later span
-  int* ocnt;         // their count (shared memory)
-  uint32_t L;
-  ItemWindows iw;    // the item's windows
-  uint32_t s0;       // first window of the span
-  uint32_t hl;       // (last rank of the span + 1) << 1
-  uint32_t item_hl;  // (last rank of the item + 1) << 1
-};
-
-// Queue a neighbour whose cursor c (row end en, edge sign s1) stopped at entry
-// x: into the list of x's window in this span, into the overflow list if x
-// lies in a later span of the item, else nowhere (the neighbour is done).
-__device__ __forceinline__ void list_append(const ListItem& li, uint32_t x, uint32_t c, uint32_t en, uint32_t s1) {
-  const uint2 slot = make_uint2(c, (en - c) | (s1 << 31));
-  if (x < li.hl) {
-    const uint32_t r = li.iw.index_of(x >> 1) - li.s0;
-    const int pos = atomicAdd(&li.cnt[r], 1);
-    li.lists[(size_t)r * li.L + (uint32_t)pos] = slot;
-  } else if (x < li.item_hl) {
-    const int pos = atomicAdd(li.ocnt, 1);
-    li.over[pos] = slot;
-  }
-}
-
-// One window of a list-mode item: groups of G lanes take the listed
-// neighbours j = gid, gid + groups, ... of `list` (n of them), walk each from
-// its cursor like sweep_window, then requeue it by its first entry past the
-// window. The next listed slot is loaded while the current one is walked.
-template <int G, int CW>
-__device__ __forceinline__ void list_window(const CsrView& g, const ListItem& li, const uint2* list, uint32_t n,
-                                            uint32_t lo, uint32_t hl, uint32_t* c16, unsigned long long* c32,
-                                            uint64_t& bal, uint64_t& unb) {
-  const int gl = threadIdx.x & (G - 1);
-  const uint32_t gid = threadIdx.x / G;
-  constexpr uint32_t groups = kSweepThreads / G;
-  const uint32_t lo2 = lo << 1;
-  const uint32_t* col = g.col;
-  uint2 e_nx = make_uint2(0u, 0u);
-  if (gid < n) e_nx = list[gid];
-  for (uint32_t j = gid; __any_sync(kFullMask, j < n); j += groups) {
-    const bool active = j < n;
-    const uint32_t c0 = e_nx.x, en = e_nx.x + (e_nx.y & 0x7FFFFFFFu), s1 = e_nx.y >> 31;
-    if (j + groups < n) e_nx = list[j + groups];
-    uint32_t x[kSweepUnroll];
-    load_chunk<G>(col, c0, active ? en : c0, gl, x);
-    const uint32_t c = walk_segment<G, CW>(col, c0, en, s1, x, lo2, hl, gl, active, c16, c32, bal, unb);
-    if (active && gl == 0 && c < en) list_append(li, col[c], c, en, s1);
-  }
-}
-
-template <int CW>
-__device__ __forceinline__ void list_window_dispatch(int group_log, const CsrView& g, const ListItem& li,
-                                                     const uint2* list, uint32_t n, uint32_t lo, uint32_t hl,
-                                                     uint32_t* c16, unsigned long long* c32, uint64_t& bal,
-                                                     uint64_t& unb) {
-  switch (group_log) {
-    case 0: list_window<1, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    case 2: list_window<4, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    case 3: list_window<8, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    case 4: list_window<16, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
-    default: list_window<32, CW>(g, li, list, n, lo, hl, c16, c32, bal, unb); break;
-  }
 }
 
 inline int blocks_per_sm(const void* fn, int threads, size_t smem) {

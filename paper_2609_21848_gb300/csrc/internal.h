@@ -29,10 +29,6 @@ constexpr int kMediumSlots = 8192;
 #ifndef DBBC_SWEEP_UNROLL
 #define DBBC_SWEEP_UNROLL 2
 #endif
-// neighbours a lane group loads together before walking them
-#ifndef DBBC_SWEEP_BATCH
-#define DBBC_SWEEP_BATCH 4
-#endif
 constexpr uint32_t kSweepWindow16 = DBBC_SWEEP_WINDOW16;     // 32-bit counters packing two 16-bit halves
 constexpr uint32_t kSweepWindow32 = DBBC_SWEEP_WINDOW16 / 2;  // 64-bit counters packing two 32-bit halves
 constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per work item

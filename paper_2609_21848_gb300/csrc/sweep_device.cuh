@@ -210,8 +210,10 @@ __device__ __forceinline__ uint32_t lean_walk(const uint32_t* __restrict__ col, 
   return c + n_ok;
 }
 
-// Neighbour cursors of an item, one uint2 per lower neighbour i:
+// Neighbour slots: one uint2 per lower neighbour,
 // {position, (entries left in its row) | (sign bit of the hub's edge to it) << 31}.
+// Cursor mode keeps one per lower neighbour of the item; list mode keeps the
+// same slots in per-window lists.
 __device__ __forceinline__ void lean_cursor_start(const CsrView& g, const PivotGeom& q, uint32_t i, uint32_t lo_rank,
                                                   uint32_t& b_out, uint32_t& en_out, uint32_t& s1_out) {
   const uint32_t e = g.col[q.rb + i];
@@ -236,90 +238,113 @@ __device__ __forceinline__ uint2 lean_slot(uint32_t c, uint32_t en, uint32_t s1)
   return make_uint2(c, (en - c) | (s1 << 31));
 }
 
-// The next batch of neighbour indices for this warp: groups of the warp take
-// base + group, base + group + groups_per_warp, ... (kLB each), handed out
-// through a shared counter so that warps that finish early take more.
+// Block-uniform state of the list-mode item being swept, kept in shared
+// memory (it would otherwise occupy registers the walk needs). In list mode a
+// neighbour is visited only in the windows that hold its entries: window r
+// of the current span has a list (global memory, L slots) of the neighbours
+// whose next entry falls in it; after walking its entries in window r, a
+// neighbour is appended to the list of the window of its next entry (always
+// a later window), to the overflow list if that entry lies in a later span of
+// the item, or to no list at the end of its row or of the item. A neighbour is
+// in at most one list at a time and in each list at most once, so L slots
+// per list never overflow.
+struct ListState {
+  uint2* lists;                // [Rsub][L] window lists of the span
+  uint2* over;                 // [L] neighbours waiting for the next span
+  int cnt[kListMaxWindows];    // list lengths
+  int ocnt;                    // overflow list length
+  uint32_t L;
+  ItemWindows iw;              // the item's windows
+  uint32_t s0;                 // first window of the span
+  uint32_t hl;                 // (last rank of the span + 1) << 1
+  uint32_t item_hl;            // (last rank of the item + 1) << 1
+};
+
+// Queue a neighbour whose cursor c (row end en, edge sign s1) stopped at entry
+// x (see ListState).
+__device__ __forceinline__ void list_queue(ListState& ls, uint32_t x, uint32_t c, uint32_t en, uint32_t s1) {
+  const uint2 slot = lean_slot(c, en, s1);
+  if (x < ls.hl) {
+    const uint32_t r = ls.iw.index_of(x >> 1) - ls.s0;
+    const int pos = atomicAdd(&ls.cnt[r], 1);
+    ls.lists[(size_t)r * ls.L + (uint32_t)pos] = slot;
+  } else if (x < ls.item_hl) {
+    const int pos = atomicAdd(&ls.ocnt, 1);
+    ls.over[pos] = slot;
+  }
+}
+
+// The neighbours a warp starts together: its groups of G lanes take slots
+// base + group, base + group + 32/G, ... (kLB each) of a slot array, with the
+// slots and the first chunk of each segment loaded. `base` is handed out
+// through a shared counter, so warps that finish early take more.
+struct LaneBatch {
+  uint32_t base;
+  uint32_t c[kLB], en[kLB], s1[kLB];
+  uint32_t x[kLB][kLU];
+};
+
 template <int G>
-__device__ __forceinline__ uint32_t lean_grab(uint32_t* nb_next) {
+__device__ __forceinline__ void batch_fetch(const uint32_t* __restrict__ col, const uint2* slots, uint32_t n,
+                                            uint32_t* next, LaneBatch& b) {
+  const int gl = threadIdx.x & (G - 1);
+  const uint32_t gw = lane_id() / G;
+  constexpr uint32_t gpw = 32 / G;
   uint32_t base = 0;
-  if (lane_id() == 0) base = atomicAdd(nb_next, (uint32_t)(32 / G) * kLB);
-  return __shfl_sync(kFullMask, base, 0);
+  if (lane_id() == 0) base = atomicAdd(next, gpw * (uint32_t)kLB);
+  b.base = __shfl_sync(kFullMask, base, 0);
+#pragma unroll
+  for (int k = 0; k < kLB; k++) {
+    const uint32_t i = b.base + gw + k * gpw;
+    b.c[k] = b.en[k] = b.s1[k] = 0;
+    if (i < n) {
+      const uint2 e = slots[i];
+      b.c[k] = e.x;
+      b.en[k] = e.x + (e.y & 0x7FFFFFFFu);
+      b.s1[k] = e.y >> 31;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kLB; k++) lean_load<G>(col, b.c[k], b.en[k], gl, b.x[k]);
 }
 
-// One window, cursor mode: every lower neighbour (L of them) is walked from its
-// cursor.
-template <int G, int CW, bool RET>
-__device__ __forceinline__ void lean_cursor_window(const uint32_t* __restrict__ col, uint32_t L, uint2* cur,
-                                                   const Win& w, uint32_t* nb_next, uint64_t& bal, uint64_t& unb) {
+// Walk a fetched batch in window w. Cursor mode (LIST false) writes each
+// neighbour's new position back to its slot in `slots`; list mode queues the
+// neighbour by its next entry.
+template <int G, int CW, bool RET, bool LIST>
+__device__ __forceinline__ void batch_walk(const uint32_t* __restrict__ col, LaneBatch& b, uint32_t n, uint2* slots,
+                                           ListState* ls, const Win& w, uint64_t& bal, uint64_t& unb) {
   const int gl = threadIdx.x & (G - 1);
   const uint32_t gw = lane_id() / G;
   constexpr uint32_t gpw = 32 / G;
-  for (;;) {
-    const uint32_t base = lean_grab<G>(nb_next);
-    if (base >= L) break;
-    uint32_t c[kLB], en[kLB], s1[kLB], x[kLB][kLU];
 #pragma unroll
-    for (int k = 0; k < kLB; k++) {
-      const uint32_t i = base + gw + k * gpw;
-      c[k] = en[k] = s1[k] = 0;
-      if (i < L) {
-        const uint2 e = cur[i];
-        c[k] = e.x;
-        en[k] = e.x + (e.y & 0x7FFFFFFFu);
-        s1[k] = e.y >> 31;
+  for (int k = 0; k < kLB; k++) {
+    const uint32_t i = b.base + gw + k * gpw;
+    const bool active = i < n;
+    uint32_t xn;
+    const uint32_t cn = lean_walk<G, CW, RET>(col, b.c[k], b.en[k], b.s1[k], b.x[k], w, gl, active, bal, unb, xn);
+    if (active && gl == 0) {
+      if constexpr (LIST) {
+        if (cn < b.en[k]) list_queue(*ls, xn, cn, b.en[k], b.s1[k]);
+      } else if (cn != b.c[k]) {
+        slots[i] = lean_slot(cn, b.en[k], b.s1[k]);
       }
-    }
-#pragma unroll
-    for (int k = 0; k < kLB; k++) lean_load<G>(col, c[k], en[k], gl, x[k]);
-#pragma unroll
-    for (int k = 0; k < kLB; k++) {
-      const uint32_t i = base + gw + k * gpw;
-      const bool active = i < L;
-      uint32_t xn;
-      const uint32_t cn = lean_walk<G, CW, RET>(col, c[k], en[k], s1[k], x[k], w, gl, active, bal, unb, xn);
-      if (active && gl == 0 && cn != c[k]) cur[i] = lean_slot(cn, en[k], s1[k]);
     }
   }
 }
 
-// One window of a list-mode item (see ListItem in count_device.cuh): the n
-// neighbours listed for it are walked from their slots, then queued by their
-// first entry past the window.
-template <int G, int CW, bool RET>
-__device__ __forceinline__ void lean_list_window(const uint32_t* __restrict__ col, const ListItem& li,
-                                                 const uint2* list, uint32_t n, const Win& w, uint32_t* nb_next,
-                                                 uint64_t& bal, uint64_t& unb) {
-  const int gl = threadIdx.x & (G - 1);
-  const uint32_t gw = lane_id() / G;
-  constexpr uint32_t gpw = 32 / G;
-  for (;;) {
-    const uint32_t base = lean_grab<G>(nb_next);
-    if (base >= n) break;
-    uint32_t c[kLB], en[kLB], s1[kLB], x[kLB][kLU];
-#pragma unroll
-    for (int k = 0; k < kLB; k++) {
-      const uint32_t j = base + gw + k * gpw;
-      c[k] = en[k] = s1[k] = 0;
-      if (j < n) {
-        const uint2 e = list[j];
-        c[k] = e.x;
-        en[k] = e.x + (e.y & 0x7FFFFFFFu);
-        s1[k] = e.y >> 31;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kLB; k++) lean_load<G>(col, c[k], en[k], gl, x[k]);
-#pragma unroll
-    for (int k = 0; k < kLB; k++) {
-      const uint32_t j = base + gw + k * gpw;
-      const bool active = j < n;
-      uint32_t xn;
-      const uint32_t cn = lean_walk<G, CW, RET>(col, c[k], en[k], s1[k], x[k], w, gl, active, bal, unb, xn);
-      if (active && gl == 0 && cn < en[k]) list_append(li, xn, cn, en[k], s1[k]);
-    }
+// All n slots of one window: the warp's first batch `b` was fetched already
+// (possibly while the previous window was being cleared); the warp then
+// fetches and walks batches until the slots run out.
+template <int G, int CW, bool RET, bool LIST>
+__device__ __forceinline__ void window_walk(const uint32_t* __restrict__ col, LaneBatch& b, const uint2* src,
+                                            uint32_t n, uint32_t* next, uint2* slots, ListState* ls, const Win& w,
+                                            uint64_t& bal, uint64_t& unb) {
+  while (b.base < n) {  // warp-uniform
+    batch_walk<G, CW, RET, LIST>(col, b, n, slots, ls, w, bal, unb);
+    batch_fetch<G>(col, src, n, next, b);
   }
 }
-
 // Clear the window's `words` counter words for the next window. With FIN,
 // first add every endpoint's Lemma 1 total from its final counter:
 // C(p,2) + C(q,2) balanced and p * q unbalanced butterflies.
@@ -377,62 +402,161 @@ __device__ __forceinline__ void lean_clear(uint32_t* cnt, uint32_t words, uint64
   }
 }
 
-template <int CW, bool RET>
-__device__ __forceinline__ void lean_cursor_window_dispatch(int group_log, const uint32_t* __restrict__ col,
-                                                            uint32_t L, uint2* cur, const Win& w, uint32_t* nb_next,
-                                                            uint64_t& bal, uint64_t& unb) {
-  switch (group_log) {
-    case 0: lean_cursor_window<1, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
-    case 2: lean_cursor_window<4, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
-    case 3: lean_cursor_window<8, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
-    case 4: lean_cursor_window<16, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
-    default: lean_cursor_window<32, CW, RET>(col, L, cur, w, nb_next, bal, unb); break;
+
+__device__ __forceinline__ void window_clear(int cw, bool fin, uint32_t* cnt, uint32_t words, uint64_t& bal,
+                                             uint64_t& unb) {
+  if (cw == 8) {
+    if (fin) lean_clear<8, true>(cnt, words, bal, unb); else lean_clear<8, false>(cnt, words, bal, unb);
+  } else if (cw == 16) {
+    if (fin) lean_clear<16, true>(cnt, words, bal, unb); else lean_clear<16, false>(cnt, words, bal, unb);
+  } else {
+    if (fin) lean_clear<32, true>(cnt, words, bal, unb); else lean_clear<32, false>(cnt, words, bal, unb);
   }
 }
 
-// The list-mode walker is a separate function (one call per window): the
-// list bookkeeping around it then costs the walk loop no registers.
-template <int CW, bool RET>
-__device__ __noinline__ void lean_list_window_dispatch(int group_log, const uint32_t* __restrict__ col,
-                                                          const ListItem& li, const uint2* list, uint32_t n,
-                                                          const Win& w, uint32_t* nb_next, uint64_t& bal,
-                                                          uint64_t& unb) {
-  switch (group_log) {
-    case 0: lean_list_window<1, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
-    case 2: lean_list_window<4, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
-    case 3: lean_list_window<8, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
-    case 4: lean_list_window<16, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
-    default: lean_list_window<32, CW, RET>(col, li, list, n, w, nb_next, bal, unb); break;
+template <int G, bool LIST>
+__device__ __forceinline__ void window_walk_dispatch(int cw, bool fin, const uint32_t* __restrict__ col, LaneBatch& b,
+                                                     const uint2* src, uint32_t n, uint32_t* next, uint2* slots,
+                                                     ListState* ls, const Win& w, uint64_t& bal, uint64_t& unb) {
+  if (cw == 8) {
+    if (fin) window_walk<G, 8, false, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
+    else window_walk<G, 8, true, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
+  } else if (cw == 16) {
+    if (fin) window_walk<G, 16, false, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
+    else window_walk<G, 16, true, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
+  } else {
+    if (fin) window_walk<G, 32, false, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
+    else window_walk<G, 32, true, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
   }
 }
 
-// One window of a cursor-mode item: walk, then clear (finalising with FIN).
-// `nb_next` must be zero on entry and is zero again on return; the caller
-// has synchronised the block after the cursors were written.
-__device__ __forceinline__ void lean_sweep_cursor(int cw, bool fin, int group_log, const uint32_t* __restrict__ col,
-                                                  uint32_t L, uint2* cur, uint32_t wlo, uint32_t whi, uint32_t sbase,
-                                                  uint32_t* cnt, uint32_t* nb_next, uint64_t& bal, uint64_t& unb) {
-  const Win w = make_win(cw, wlo, whi, sbase);
-  if (cw == 8) {
-    if (fin) lean_cursor_window_dispatch<8, false>(group_log, col, L, cur, w, nb_next, bal, unb);
-    else lean_cursor_window_dispatch<8, true>(group_log, col, L, cur, w, nb_next, bal, unb);
-  } else if (cw == 16) {
-    if (fin) lean_cursor_window_dispatch<16, false>(group_log, col, L, cur, w, nb_next, bal, unb);
-    else lean_cursor_window_dispatch<16, true>(group_log, col, L, cur, w, nb_next, bal, unb);
-  } else {
-    if (fin) lean_cursor_window_dispatch<32, false>(group_log, col, L, cur, w, nb_next, bal, unb);
-    else lean_cursor_window_dispatch<32, true>(group_log, col, L, cur, w, nb_next, bal, unb);
+// Every window of a cursor-mode item, in rank order. On entry the L cursors
+// are written and the block is synchronised, and both window counters nbn[0]
+// and nbn[1] are zero (they are again on return). Each window ends with two
+// barriers: after the first, every count and cursor of the window is final,
+// so the warps fetch their first batch of the next window (cursors and first
+// chunks) and only then clear the counters, which hides that load latency
+// behind the clear.
+template <int G>
+__device__ __forceinline__ void sweep_cursor_item(const uint32_t* __restrict__ col, uint32_t L, uint2* cur,
+                                                  const ItemWindows& iw, bool fin, uint32_t sbase, uint32_t* cnt_words,
+                                                  uint32_t* nbn, uint64_t& bal, uint64_t& unb) {
+  const uint32_t R = iw.count();
+  LaneBatch b;
+  batch_fetch<G>(col, cur, L, &nbn[0], b);
+  for (uint32_t r = 0; r < R; r++) {
+    uint32_t lo, hi;
+    int cw;
+    iw.window(r, lo, hi, cw);
+    const Win w = make_win(cw, lo, hi, sbase);
+    window_walk_dispatch<G, false>(cw, fin, col, b, cur, L, &nbn[r & 1], cur, nullptr, w, bal, unb);
+    __syncthreads();
+    if (r + 1 < R) batch_fetch<G>(col, cur, L, &nbn[(r + 1) & 1], b);
+    window_clear(cw, fin, cnt_words, w.words, bal, unb);
+    if (threadIdx.x == 0) nbn[r & 1] = 0u;
+    __syncthreads();
   }
-  __syncthreads();
-  if (cw == 8) {
-    if (fin) lean_clear<8, true>(cnt, w.words, bal, unb); else lean_clear<8, false>(cnt, w.words, bal, unb);
-  } else if (cw == 16) {
-    if (fin) lean_clear<16, true>(cnt, w.words, bal, unb); else lean_clear<16, false>(cnt, w.words, bal, unb);
-  } else {
-    if (fin) lean_clear<32, true>(cnt, w.words, bal, unb); else lean_clear<32, false>(cnt, w.words, bal, unb);
+}
+
+__device__ __forceinline__ void sweep_cursor_item_dispatch(int group_log, const uint32_t* __restrict__ col,
+                                                           uint32_t L, uint2* cur, const ItemWindows& iw, bool fin,
+                                                           uint32_t sbase, uint32_t* cnt_words, uint32_t* nbn,
+                                                           uint64_t& bal, uint64_t& unb) {
+  switch (group_log) {
+    case 0: sweep_cursor_item<1>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
+    case 2: sweep_cursor_item<4>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
+    case 3: sweep_cursor_item<8>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
+    case 4: sweep_cursor_item<16>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
+    default: sweep_cursor_item<32>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
   }
-  if (threadIdx.x == 0) *nb_next = 0u;
-  __syncthreads();
+}
+
+// A list-mode item (see ListState): consecutive spans of at most Rsub windows,
+// whose Rsub lists plus two overflow lists of L slots fit the CTA's list_cap
+// slots in `lists`. Each neighbour's row is searched once per item (for its
+// first entry at or after the item's first rank); a neighbour whose next entry
+// lies past the current span waits in an overflow list and is queued when its
+// span starts. Windows end as in sweep_cursor_item. Returns the visits
+// (listed neighbours), counted by thread 0.
+template <int G>
+__device__ __forceinline__ uint64_t sweep_list_item(const CsrView& g, const SweepItem& item, const PivotGeom& q,
+                                                    uint2* lists, int64_t list_cap, ListState& ls, uint32_t sbase,
+                                                    uint32_t* cnt_words, uint32_t* nbn, uint64_t& bal, uint64_t& unb) {
+  const int tid = threadIdx.x;
+  const ItemWindows iw(item);
+  const uint32_t R = iw.count();
+  const bool fin = (item.flags & kItemFinalize) != 0;
+  const int64_t per_nb = list_cap / (int64_t)q.L;
+  const uint32_t Rsub = (uint32_t)(per_nb - 2 < kListMaxWindows ? per_nb - 2 : kListMaxWindows);
+  uint64_t visits = 0;
+  int in_buf = 0;  // the overflow list that feeds the next span
+  for (uint32_t s0 = 0; s0 < R; s0 += Rsub) {
+    const uint32_t nwin = min(Rsub, R - s0);
+    uint32_t span_lo, span_hi, wlo, whi;
+    int cw;
+    iw.window(s0, span_lo, whi, cw);
+    iw.window(s0 + nwin - 1, wlo, span_hi, cw);
+    uint2* over_in = lists + (size_t)(Rsub + in_buf) * q.L;
+    const uint32_t n_in = s0 == 0 ? 0u : (uint32_t)ls.ocnt;  // final since the last barrier of the previous span
+    __syncthreads();  // every thread has read ls.ocnt
+    if (tid == 0) {
+      ls.lists = lists;
+      ls.over = lists + (size_t)(Rsub + (in_buf ^ 1)) * q.L;
+      ls.ocnt = 0;
+      ls.L = q.L;
+      ls.iw = iw;
+      ls.s0 = s0;
+      ls.hl = span_hi << 1;
+      ls.item_hl = item.hi << 1;
+    }
+    if (tid < kListMaxWindows) ls.cnt[tid] = 0;
+    __syncthreads();
+    if (s0 == 0) {  // each neighbour joins the list of the window of its first entry
+      for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
+        uint32_t b, en, s1;
+        lean_cursor_start(g, q, i, item.lo, b, en, s1);
+        if (b < en) list_queue(ls, g.col[b], b, en, s1);
+      }
+    } else {  // the neighbours that waited for this span
+      for (uint32_t j = tid; j < n_in; j += kSweepThreads) {
+        const uint2 e = over_in[j];
+        const uint32_t c = e.x, en = e.x + (e.y & 0x7FFFFFFFu);
+        list_queue(ls, g.col[c], c, en, e.y >> 31);
+      }
+    }
+    __syncthreads();
+    LaneBatch b;
+    batch_fetch<G>(g.col, lists, (uint32_t)ls.cnt[0], &nbn[0], b);
+    for (uint32_t r = 0; r < nwin; r++) {
+      iw.window(s0 + r, wlo, whi, cw);
+      const Win w = make_win(cw, wlo, whi, sbase);
+      const uint32_t n = (uint32_t)ls.cnt[r];
+      window_walk_dispatch<G, true>(cw, fin, g.col, b, lists + (size_t)r * q.L, n, &nbn[r & 1], nullptr, &ls, w,
+                                    bal, unb);
+      visits += tid == 0 ? n : 0;
+      __syncthreads();  // also publishes the appends to later windows' lists
+      if (r + 1 < nwin)
+        batch_fetch<G>(g.col, lists + (size_t)(r + 1) * q.L, (uint32_t)ls.cnt[r + 1], &nbn[(r + 1) & 1], b);
+      window_clear(cw, fin, cnt_words, w.words, bal, unb);
+      if (tid == 0) nbn[r & 1] = 0u;
+      __syncthreads();
+    }
+    in_buf ^= 1;
+  }
+  return visits;
+}
+
+__device__ __forceinline__ uint64_t sweep_list_item_dispatch(const CsrView& g, const SweepItem& item,
+                                                             const PivotGeom& q, uint2* lists, int64_t list_cap,
+                                                             ListState& ls, uint32_t sbase, uint32_t* cnt_words,
+                                                             uint32_t* nbn, uint64_t& bal, uint64_t& unb) {
+  switch (item.group_log) {
+    case 0: return sweep_list_item<1>(g, item, q, lists, list_cap, ls, sbase, cnt_words, nbn, bal, unb);
+    case 2: return sweep_list_item<4>(g, item, q, lists, list_cap, ls, sbase, cnt_words, nbn, bal, unb);
+    case 3: return sweep_list_item<8>(g, item, q, lists, list_cap, ls, sbase, cnt_words, nbn, bal, unb);
+    case 4: return sweep_list_item<16>(g, item, q, lists, list_cap, ls, sbase, cnt_words, nbn, bal, unb);
+    default: return sweep_list_item<32>(g, item, q, lists, list_cap, ls, sbase, cnt_words, nbn, bal, unb);
+  }
 }
 
 }  // namespace dbbc

@@ -135,3 +135,11 @@ def test_tuning_reads_are_whole_under_concurrent_sets(lib):
         assert all(r in (a, b, base) for r in seen)
     finally:
         dbbc.dbbc_set_tuning(base)
+
+
+def test_timeout_status_is_reserved():
+    """DBBC_ETIMEOUT is reserved: no kernel of the library waits on a flag, a
+    peer or a barrier that another launch sets, so no call returns it."""
+    text = open(HEADER).read()
+    assert "reserved" in text.split("DBBC_ETIMEOUT = 4,", 1)[1].split("\n", 1)[0]
+    assert dbbc.dbbc_status_string(4) == "bounded device wait gave up"

@@ -350,17 +350,44 @@ def test_sign_ratio_changes_the_split_not_the_total():
     assert fracs[1] < fracs[0] and fracs[1] < fracs[2]  # P(+) = 1/2 balances least
 
 
+def _lpt_parts_from_export(h, parts):
+    """The pivots of each LPT part, recomputed from the exported CSR: pivots
+    are the rows with at least two lower neighbours and accepted wedges, in
+    descending work (ties by row); Phase 3's greedy packing of their work
+    (dbbc_lpt_partition, itself checked against the oracle's LPT on the CPU)
+    assigns each to a part. Returns the unified ids of each part's pivots."""
+    ex = dbbc.dbbc_graph_export(h)
+    rows = np.nonzero((ex["lower"] >= 2) & (ex["work"] > 0))[0]
+    rows = rows[np.lexsort((rows, -ex["work"][rows].astype(np.float64)))]
+    assert np.all(np.diff(ex["work"][rows].astype(np.int64)) <= 0)
+    part, _ = dbbc.dbbc_lpt_partition(ex["work"][rows], parts)
+    return [ex["vertex"][rows[part == p]] for p in range(parts)]
+
+
 @pytest.mark.parametrize("parts", [1, 2, 3, 8])
-def test_partitions_add_up_to_the_count(parts):
-    """dbbc_count_partition: the LPT parts of one graph (as on `parts` GPUs)
-    add up to its count, on a graph with hubs, medium and light pivots."""
+def test_partition_parts_match_the_oracle(parts):
+    """dbbc_count_partition (Phase 3 greedy packing, Section IV-A, Example 2):
+    each part's counts equal the oracle's per-pivot counts summed over that
+    part's pivots, on a graph with hubs (several work items each), medium and
+    light pivots; the parts add up to the oracle's totals (Theorem 1)."""
     g = synth.workload("chunglu-1m-200k-20m", scale=0.02)
-    with dbbc.dbbc_graph_from_coo(g.u, g.v, g.s, g.n_u, g.n_v) as h:
-        total = dbbc.dbbc_count(h)
-        sums = [dbbc.dbbc_count_partition(h, p, parts) for p in range(parts)]
-    assert (sum(x[0] for x in sums), sum(x[1] for x in sums)) == total
+    bal, unb, wed = oracle.count_per_pivot(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)
+    want_total = oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[:2]
+    base = dbbc.dbbc_get_tuning()
+    dbbc.dbbc_set_tuning({"hub_item_work": 1 << 14})  # several sweep items per hub
+    try:
+        with dbbc.dbbc_graph_from_coo(g.u, g.v, g.s, g.n_u, g.n_v) as h:
+            info = h.info
+            assert info["n_hub"] > 0 and info["n_medium"] > 0 and info["n_light"] > 0
+            got = [dbbc.dbbc_count_partition(h, p, parts) for p in range(parts)]
+            ids = _lpt_parts_from_export(h, parts)
+    finally:
+        dbbc.dbbc_set_tuning(base)
+    for p in range(parts):
+        assert got[p] == (int(bal[ids[p]].sum()), int(unb[ids[p]].sum())), p
+    assert (sum(x[0] for x in got), sum(x[1] for x in got)) == want_total
     if parts > 1:
-        assert all(x != (0, 0) for x in sums)
+        assert all(x != (0, 0) for x in got)
 
 
 def test_torch_allocator_hook():

@@ -198,16 +198,32 @@ def test_union_handle_uses_union_ids():
         assert np.array_equal(vu[NU + vo[i]:NU + vo[i + 1]], wu[x.n_u:])
 
 
-def test_chunglu_full_size_sums_match_stored_totals():
-    """At 1M x 200k x 20M edges (the oracle's per-vertex walk is too slow
-    here): each vertex array sums to four times the totals the oracle stored,
-    and two calls give the same arrays."""
+def _digest(balanced, unbalanced):
+    """SHA-256 of two count arrays as little-endian uint64, one after the other
+    (the form tests/golden/make_expected.py stores for the oracle's arrays)."""
+    import hashlib
+    h = hashlib.sha256()
+    for a in (balanced, unbalanced):
+        h.update(np.ascontiguousarray(a, dtype="<u8").tobytes())
+    return h.hexdigest()
+
+
+def _stored_digest(workload, kind):
+    return dict(read_golden("expected_digests.txt")[workload])[kind]
+
+
+def test_chunglu_full_size_matches_the_oracle_element_by_element():
+    """At 1M x 200k x 20M edges: every vertex's balanced and unbalanced counts
+    equal the oracle's (compared through the SHA-256 of the whole arrays that
+    the oracle's per-vertex walk stored), each array sums to four times the
+    stored totals, and two calls give the same arrays."""
     g = synth.workload("chunglu-1m-200k-20m")
     exp = read_golden("expected_counts.txt")["chunglu-1m-200k-20m"][0]
     vb, vu, tot, _ = gpu_vertices(g.u, g.v, g.s, g.n_u, g.n_v)
     assert tot == (exp[0], exp[1])
     assert int(vb.sum(dtype=np.uint64)) == 4 * exp[0]
     assert int(vu.sum(dtype=np.uint64)) == 4 * exp[1]
+    assert _digest(vb, vu) == _stored_digest("chunglu-1m-200k-20m", "vertices")
     vb2, vu2, _, _ = gpu_vertices(g.u, g.v, g.s, g.n_u, g.n_v)
     assert np.array_equal(vb, vb2) and np.array_equal(vu, vu2)
 
@@ -332,7 +348,7 @@ def test_edges_do_not_depend_on_tuning():
     assert np.array_equal(eb, want_b) and np.array_equal(eu, want_u)
 
 
-def test_edges_chunglu_full_size_sums():
+def test_edges_chunglu_full_size_match_the_oracle():
     g = synth.workload("chunglu-1m-200k-20m")
     exp = read_golden("expected_counts.txt")["chunglu-1m-200k-20m"][0]
     pairs = np.unique(g.u.astype(np.int64) * g.n_v + g.v)
@@ -340,3 +356,5 @@ def test_edges_chunglu_full_size_sums():
                             (pairs % g.n_v).astype(np.int32))
     assert tot == (exp[0], exp[1])
     assert int(eb.sum(dtype=np.uint64)) == 4 * exp[0] and int(eu.sum(dtype=np.uint64)) == 4 * exp[1]
+    # every edge against the oracle's per-edge walk (stored as a digest)
+    assert _digest(eb, eu) == _stored_digest("chunglu-1m-200k-20m", "edges")
