@@ -35,8 +35,9 @@ SPACE = [
     ("hash_mult_log", [1, 2]),
     ("hub_item_work", [1 << 19, 1 << 20, 1 << 21, 1 << 22]),
     ("group_density", [[40.0, 16.0, 6.0, 2.0], [64.0, 24.0, 8.0, 3.0], [24.0, 10.0, 4.0, 1.5],
-                       [96.0, 32.0, 12.0, 4.0], [128.0, 48.0, 12.0, 4.0], [128.0, 48.0, 16.0, 6.0]]),
-    ("list_density", [0.0, 4.0, 8.0, 16.0, 32.0]),
+                       [96.0, 32.0, 12.0, 4.0], [128.0, 48.0, 12.0, 4.0], [128.0, 48.0, 16.0, 6.0],
+                       [192.0, 64.0, 16.0, 6.0], [256.0, 96.0, 24.0, 8.0]]),
+    ("list_density", [0.0, 4.0, 8.0, 16.0, 32.0, 64.0]),
     ("list_group_log", [2, 3, 4, 5]),
     ("finalize_window_wedges", [0, 16384, 65536, 262144, 2**64 - 1]),
 ]

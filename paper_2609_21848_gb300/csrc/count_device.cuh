@@ -238,11 +238,12 @@ __device__ __forceinline__ void load_chunk(const uint32_t* col, uint32_t c, uint
 // (asym << 16) | sym, kSweepWindow16 ranks per window. CW = 8: two endpoints
 // per 32-bit word, each (asym << 8) | sym, twice the ranks per window; used
 // where every endpoint has degree < 256 or the hub has fewer than 256 lower
-// neighbours (a count never exceeds either). CW = 32: one 64-bit word per
-// endpoint, half the ranks.
+// neighbours (a count never exceeds either). CW = 4: four endpoints per word,
+// each (asym << 4) | sym, four times the ranks, where counts stay below 16.
+// CW = 32: one 64-bit word per endpoint, half the ranks.
 template <int CW>
 __host__ __device__ constexpr uint32_t window_ranks() {
-  return CW == 8 ? 2 * kSweepWindow16 : CW == 16 ? kSweepWindow16 : kSweepWindow32;
+  return CW == 4 ? 4 * kSweepWindow16 : CW == 8 ? 2 * kSweepWindow16 : CW == 16 ? kSweepWindow16 : kSweepWindow32;
 }
 
 template <int CW>
@@ -250,43 +251,52 @@ __device__ __forceinline__ uint32_t window_words(uint32_t ranks) {  // 32-bit wo
   return CW == 8 ? (ranks + 1) >> 1 : CW == 16 ? ranks : 2 * ranks;
 }
 
-// The windows of a work item: tiny ones over [lo, te), narrow ones over
-// [te, ne), wide ones over [ne, hi), numbered in rank order.
+// The windows of a work item: quarter ones over [lo, qe), tiny ones over
+// [qe, te), narrow ones over [te, ne), wide ones over [ne, hi), numbered in
+// rank order. `quarter` false folds the quarter part into the tiny one (for
+// sweeps that have no 4-bit counters).
 struct ItemWindows {
-  uint32_t lo, te, ne, hi;
-  uint32_t rt, rn, rw;
+  uint32_t lo, qe, te, ne, hi;
+  uint32_t rq, rt, rn, rw;
   ItemWindows() = default;
-  __device__ __forceinline__ explicit ItemWindows(const SweepItem& it) {
+  __device__ __forceinline__ explicit ItemWindows(const SweepItem& it, bool quarter = true) {
     lo = it.lo;
     hi = it.hi;
-    te = min(max(it.t_end, lo), hi);
+    qe = quarter ? min(max(it.q_end, lo), hi) : lo;
+    te = min(max(it.t_end, qe), hi);
     ne = min(max(it.n_end, te), hi);
-    rt = (te - lo + window_ranks<8>() - 1) / window_ranks<8>();
+    rq = (qe - lo + window_ranks<4>() - 1) / window_ranks<4>();
+    rt = (te - qe + window_ranks<8>() - 1) / window_ranks<8>();
     rn = (ne - te + window_ranks<16>() - 1) / window_ranks<16>();
     rw = (hi - ne + window_ranks<32>() - 1) / window_ranks<32>();
   }
-  __device__ __forceinline__ uint32_t count() const { return rt + rn + rw; }
+  __device__ __forceinline__ uint32_t count() const { return rq + rt + rn + rw; }
   // window r: its ranks [wlo, whi) and counter width
   __device__ __forceinline__ void window(uint32_t r, uint32_t& wlo, uint32_t& whi, int& cw) const {
-    if (r < rt) {
-      wlo = lo + r * window_ranks<8>();
+    if (r < rq) {
+      wlo = lo + r * window_ranks<4>();
+      whi = min(wlo + window_ranks<4>(), qe);
+      cw = 4;
+    } else if (r < rq + rt) {
+      wlo = qe + (r - rq) * window_ranks<8>();
       whi = min(wlo + window_ranks<8>(), te);
       cw = 8;
-    } else if (r < rt + rn) {
-      wlo = te + (r - rt) * window_ranks<16>();
+    } else if (r < rq + rt + rn) {
+      wlo = te + (r - rq - rt) * window_ranks<16>();
       whi = min(wlo + window_ranks<16>(), ne);
       cw = 16;
     } else {
-      wlo = ne + (r - rt - rn) * window_ranks<32>();
+      wlo = ne + (r - rq - rt - rn) * window_ranks<32>();
       whi = min(wlo + window_ranks<32>(), hi);
       cw = 32;
     }
   }
   // the window holding rank x (lo <= x < hi)
   __device__ __forceinline__ uint32_t index_of(uint32_t x) const {
-    if (x < te) return (x - lo) / window_ranks<8>();
-    if (x < ne) return rt + (x - te) / window_ranks<16>();
-    return rt + rn + (x - ne) / window_ranks<32>();
+    if (x < qe) return (x - lo) / window_ranks<4>();
+    if (x < te) return rq + (x - qe) / window_ranks<8>();
+    if (x < ne) return rq + rt + (x - te) / window_ranks<16>();
+    return rq + rt + rn + (x - ne) / window_ranks<32>();
   }
 };
 

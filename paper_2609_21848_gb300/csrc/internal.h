@@ -74,16 +74,18 @@ constexpr int32_t kNarrowCountLimit = 65536;
 
 // One unit of hub work: endpoints with side ranks [lo, hi) of hub row `row`,
 // swept in windows whose counters are as narrow as the counts allow: ranks
-// below t_end in tiny windows (8-bit halves, 2 * kSweepWindow16 ranks), below
+// below q_end in quarter windows (4-bit halves, 4 * kSweepWindow16 ranks),
+// below t_end in tiny ones (8-bit halves, 2 * kSweepWindow16 ranks), below
 // n_end in narrow ones (16-bit halves, kSweepWindow16 ranks), the rest in wide
-// ones (32-bit halves, kSweepWindow32 ranks); t_end and n_end are the hub's
-// boundaries (clamped to the item). Each lower neighbour's segment is walked
-// by 2^group_log lanes. A count never exceeds the endpoint's degree nor the
-// hub's lower-neighbour count.
+// ones (32-bit halves, kSweepWindow32 ranks); q_end, t_end and n_end are the
+// hub's boundaries (clamped to the item). Each lower neighbour's segment is
+// walked by 2^group_log lanes. A count never exceeds the endpoint's degree nor
+// the hub's lower-neighbour count.
 struct SweepItem {
   int32_t row;
   uint32_t lo;
   uint32_t hi;
+  uint32_t q_end;
   uint32_t t_end;
   uint32_t n_end;
   int16_t group_log;
@@ -93,8 +95,10 @@ constexpr int16_t kItemList = 2;  // list mode: visit a neighbour only in window
 // counters of a window are finalised when it is cleared (C(p,2) + C(q,2) and
 // p*q per endpoint) instead of wedge by wedge
 constexpr int16_t kItemFinalize = 4;
-// Counts below this fit the 8-bit halves of a tiny counter.
+// Counts below this fit the 8-bit halves of a tiny counter, and below the
+// next the 4-bit halves of a quarter counter.
 constexpr int32_t kTinyCountLimit = 256;
+constexpr int32_t kQuarterCountLimit = 16;
 
 // Read-only view of the device CSR passed to kernels by value.
 // Rows [0, n_u) are U vertices in ascending Def. 3 priority, rows [n_u, n)
@@ -144,6 +148,8 @@ struct dbbc_graph {
   int64_t sweep_list_cap = 0;   // largest windows x lower neighbours of a list-mode item (list slots per CTA)
   int64_t narrow_ranks_u = 0, narrow_ranks_v = 0;  // per side: vertices of degree < 2^16 (a rank prefix)
   int64_t tiny_ranks_u = 0, tiny_ranks_v = 0;      // per side: vertices of degree < 2^8 (a rank prefix)
+  int64_t quarter_ranks_u = 0, quarter_ranks_v = 0;  // per side: vertices of degree < 2^4 (a rank prefix)
+  int64_t zero_ranks_u = 0, zero_ranks_v = 0;      // per side: vertices of degree 0 (a rank prefix; no row lists them)
   // disjoint union of several graphs (dbbc_graph_from_coo_multi): component
   // of every row, 0 for a plain handle (n_components == 1)
   int32_t n_components = 1;

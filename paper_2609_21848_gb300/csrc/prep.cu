@@ -310,14 +310,19 @@ __global__ void pivot_keys_kernel(const uint64_t* __restrict__ work, const uint3
   }
 }
 
-// Per side, how many vertices have degree below `narrow` and below `tiny`
-// (ranks ascend by degree within a side).
-__global__ void narrow_ranks_kernel(const int32_t* __restrict__ rowdeg, int64_t n, int32_t n_u, int32_t narrow,
-                                    int32_t tiny, int64_t* out) {
-  if (threadIdx.x == 0) out[0] = lower_bound_dev<int32_t>(rowdeg, n_u, narrow);
-  if (threadIdx.x == 1) out[1] = lower_bound_dev<int32_t>(rowdeg + n_u, n - n_u, narrow);
-  if (threadIdx.x == 2) out[2] = lower_bound_dev<int32_t>(rowdeg, n_u, tiny);
-  if (threadIdx.x == 3) out[3] = lower_bound_dev<int32_t>(rowdeg + n_u, n - n_u, tiny);
+// Per side, how many vertices have degree below each of four limits (ranks
+// ascend by degree within a side): out[2k] for U, out[2k + 1] for V.
+struct DegreeLimits {
+  int32_t d[4];
+};
+__global__ void narrow_ranks_kernel(const int32_t* __restrict__ rowdeg, int64_t n, int32_t n_u, DegreeLimits lim,
+                                    int64_t* out) {
+  const int t = threadIdx.x;
+  if (t < 8) {
+    const bool u = (t & 1) == 0;
+    out[t] = u ? lower_bound_dev<int32_t>(rowdeg, n_u, lim.d[t >> 1])
+               : lower_bound_dev<int32_t>(rowdeg + n_u, n - n_u, lim.d[t >> 1]);
+  }
 }
 
 // Union of several graphs: graph i's local ids are validated against its own
@@ -444,29 +449,38 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
         (uint64_t)off[(size_t)(std::upper_bound(off.begin(), off.end(), (int64_t)sp) - off.begin() - 1)];
     // counter widths by the counts they must hold: a count never exceeds the
     // endpoint's degree nor the hub's lower-neighbour count L. Ranks ascend by
-    // degree, so tiny (8-bit halves) counters serve the ranks below the side's
-    // first endpoint of degree >= 2^8 and narrow (16-bit) ones those below
-    // degree 2^16; for a union, whose ranks are component-major, only L bounds
-    // the counts.
+    // degree, so quarter (4-bit halves) counters serve the ranks below the
+    // side's first endpoint of degree >= 2^4, tiny (8-bit) ones those below
+    // degree 2^8 and narrow (16-bit) ones those below degree 2^16; for a union,
+    // whose ranks are component-major, only L bounds the counts. Endpoints of
+    // degree 0 (the lowest ranks) are in no row, so the windows start after
+    // them.
     auto clamp_rank = [&](int64_t x) {
       return std::max<uint64_t>(start, std::min<uint64_t>(sp, (uint64_t)std::max<int64_t>(x, 0)));
     };
+    const bool plain = un.n_graphs == 1;
+    const uint64_t first = plain ? clamp_rank(is_u ? g->zero_ranks_u : g->zero_ranks_v) : start;
+    const uint64_t quarter_end = L < (uint32_t)kQuarterCountLimit ? sp
+                                 : plain ? std::max<uint64_t>(first, clamp_rank(is_u ? g->quarter_ranks_u
+                                                                                     : g->quarter_ranks_v))
+                                         : first;
     const uint64_t tiny_end = L < (uint32_t)kTinyCountLimit ? sp
-                              : un.n_graphs > 1            ? start
-                                                           : clamp_rank(is_u ? g->tiny_ranks_u : g->tiny_ranks_v);
+                              : plain ? std::max<uint64_t>(quarter_end, clamp_rank(is_u ? g->tiny_ranks_u
+                                                                                        : g->tiny_ranks_v))
+                                      : quarter_end;
     const uint64_t narrow_end =
         L < (uint32_t)kNarrowCountLimit ? sp
-        : un.n_graphs > 1               ? tiny_end
-                                        : std::max<uint64_t>(tiny_end,
-                                                             clamp_rank(is_u ? g->narrow_ranks_u : g->narrow_ranks_v));
-    const uint64_t H8 = 2ull * kSweepWindow16;
-    const uint64_t Rt = (tiny_end - start + H8 - 1) / H8;
+        : plain ? std::max<uint64_t>(tiny_end, clamp_rank(is_u ? g->narrow_ranks_u : g->narrow_ranks_v))
+                : tiny_end;
+    const uint64_t H4 = 4ull * kSweepWindow16, H8 = 2ull * kSweepWindow16;
+    const uint64_t Rq = (quarter_end - first + H4 - 1) / H4;
+    const uint64_t Rt = (tiny_end - quarter_end + H8 - 1) / H8;
     const uint64_t Rn = (narrow_end - tiny_end + kSweepWindow16 - 1) / kSweepWindow16;
     const uint64_t Rw = (sp - narrow_end + kSweepWindow32 - 1) / kSweepWindow32;
     const uint64_t target = std::max<uint64_t>(g->tune.hub_item_work, 64ull * L);
     max_lower = std::max<int64_t>(max_lower, L);
     // lanes per (neighbour, window) segment from the hub's mean segment length
-    const double density = (double)W / ((double)L * (double)std::max<uint64_t>(1, Rt + Rn + Rw));
+    const double density = (double)W / ((double)L * (double)std::max<uint64_t>(1, Rq + Rt + Rn + Rw));
     const double* gd = g->tune.group_density;
     const int16_t dense_log = density >= gd[0] ? 5 : density >= gd[1] ? 4 : density >= gd[2] ? 3 : density >= gd[3] ? 2 : 0;
     // sparse hubs sweep in list mode: one item per hub, run in spans of at
@@ -474,14 +488,15 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
     // the per-CTA list scratch
     const uint64_t per_nb = (uint64_t)kListCapEntries / std::max<uint32_t>(L, 1);
     const uint64_t Rsub = per_nb >= 3 ? std::min<uint64_t>(kListMaxWindows, per_nb - 2) : 0;
-    const uint64_t R_all = Rt + Rn + Rw;
+    const uint64_t R_all = Rq + Rt + Rn + Rw;
     const bool listed = density < g->tune.list_density && Rsub >= 1 && R_all >= 2;
     // the first rank of window w of the hub (windows numbered in rank order
-    // over the tiny, narrow and wide parts)
+    // over the quarter, tiny, narrow and wide parts)
     auto window_start = [&](uint64_t w) -> uint64_t {
-      if (w < Rt) return start + w * H8;
-      if (w < Rt + Rn) return tiny_end + (w - Rt) * kSweepWindow16;
-      return std::min<uint64_t>(sp, narrow_end + (w - Rt - Rn) * kSweepWindow32);
+      if (w < Rq) return first + w * H4;
+      if (w < Rq + Rt) return quarter_end + (w - Rq) * H8;
+      if (w < Rq + Rt + Rn) return tiny_end + (w - Rq - Rt) * kSweepWindow16;
+      return std::min<uint64_t>(sp, narrow_end + (w - Rq - Rt - Rn) * kSweepWindow32);
     };
     // items of roughly `target` wedges over consecutive windows (one item in
     // list mode); an item crosses width boundaries freely
@@ -493,6 +508,7 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
       p.it.row = row;
       p.it.lo = (uint32_t)window_start(w0);
       p.it.hi = (uint32_t)(w1 == R_all ? sp : window_start(w1));
+      p.it.q_end = (uint32_t)quarter_end;
       p.it.t_end = (uint32_t)tiny_end;
       p.it.n_end = (uint32_t)narrow_end;
       p.it.group_log = listed ? (int16_t)g->tune.list_group_log : dense_log;
@@ -795,18 +811,24 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
     if (alt)
       DBBC_CUDA(cudaMemcpyAsync(pr0, pr1, (size_t)g->n_piv * 4, cudaMemcpyDeviceToDevice, s));
   }
-  // per side: how many vertices have degree < 2^16 and < 2^8 (ranks ascend by degree)
+  // per side: how many vertices have degree < 2^16, < 2^8, < 2^4 and 0
+  // (ranks ascend by degree)
   {
-    int64_t* d_t = sc.get<int64_t>(4);
-    narrow_ranks_kernel<<<1, 32, 0, s>>>(rowdeg, n, n_u, kNarrowCountLimit, kTinyCountLimit, d_t);
+    int64_t* d_t = sc.get<int64_t>(8);
+    const DegreeLimits lim{{kNarrowCountLimit, kTinyCountLimit, kQuarterCountLimit, 1}};
+    narrow_ranks_kernel<<<1, 32, 0, s>>>(rowdeg, n, n_u, lim, d_t);
     DBBC_LAUNCH_CHECK();
-    int64_t ht[4];
+    int64_t ht[8];
     DBBC_CUDA(cudaMemcpyAsync(ht, d_t, sizeof(ht), cudaMemcpyDeviceToHost, s));
     DBBC_CUDA(cudaStreamSynchronize(s));
     g->narrow_ranks_u = ht[0];
     g->narrow_ranks_v = ht[1];
     g->tiny_ranks_u = ht[2];
     g->tiny_ranks_v = ht[3];
+    g->quarter_ranks_u = ht[4];
+    g->quarter_ranks_v = ht[5];
+    g->zero_ranks_u = ht[6];
+    g->zero_ranks_v = ht[7];
   }
   plan_hubs(g, s, *un);
   DBBC_CUDA(cudaStreamSynchronize(s));

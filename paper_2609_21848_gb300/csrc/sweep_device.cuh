@@ -39,14 +39,16 @@ constexpr int kLU = DBBC_LEAN_UNROLL;
 constexpr int kLB = DBBC_LEAN_BATCH;
 
 // Shared counters of the sweep: one window, plus one word so that a window of
-// 8-bit counters may start at the even rank below its first rank.
+// 4-bit (8-bit) counters may start at the multiple of 4 (even rank) below its
+// first rank.
 constexpr uint32_t kSweepWords = kSweepWindow16 + 4;
 constexpr size_t kSweepSmem = (size_t)kSweepWords * 4;
 
 // A window of side ranks [wlo, whi): entries below h lie in it (cursors start
 // at its first rank), and the counter word of rank r is at shared byte address
-// wb + (r >> 1) * 4 (8-bit counters, two ranks per word, rank pairs aligned to
-// an even rank), wb + r * 4 (16-bit) or wb + r * 8 (32-bit).
+// wb + (r >> 2) * 4 (4-bit counters, four ranks per word, aligned to a
+// multiple of 4), wb + (r >> 1) * 4 (8-bit counters, two ranks per word,
+// aligned to an even rank), wb + r * 4 (16-bit) or wb + r * 8 (32-bit).
 struct Win {
   uint32_t h;
   uint32_t wb;
@@ -56,7 +58,11 @@ struct Win {
 __device__ __forceinline__ Win make_win(int cw, uint32_t wlo, uint32_t whi, uint32_t sbase) {
   Win w;
   w.h = whi << 1;
-  if (cw == 8) {
+  if (cw == 4) {
+    const uint32_t l4 = wlo & ~3u;
+    w.wb = sbase - l4;
+    w.words = (whi - l4 + 3u) >> 2;
+  } else if (cw == 8) {
     const uint32_t l2 = wlo & ~1u;
     w.wb = sbase - l2 * 2u;
     w.words = (whi - l2 + 1u) >> 1;
@@ -102,7 +108,20 @@ __device__ __forceinline__ uint64_t atom_if_u64(uint32_t x, uint32_t h, uint32_t
 template <int CW, bool RET>
 __device__ __forceinline__ void lean_add(uint32_t x, uint32_t h, uint32_t s1, uint32_t wb, uint32_t& a_lo,
                                          uint32_t& a_hi, uint64_t& bal, uint64_t& unb) {
-  if constexpr (CW == 8) {
+  if constexpr (CW == 4) {
+    // nibble (2 * (rank & 3) + asym) of the word: byte k = (asym_k << 4) | sym_k
+    const uint32_t sel = (x ^ s1) & 7u;
+    const uint32_t addr = wb + ((x >> 1) & ~3u);
+    const uint32_t inc = 1u << (sel << 2);
+    if constexpr (!RET) {
+      red_if_u32(x, h, addr, inc);
+    } else {
+      const uint32_t old = atom_if_u32(x, h, addr, inc);
+      const uint32_t own = (old >> (sel << 2)) & 0xFu, other = (old >> ((sel ^ 1u) << 2)) & 0xFu;
+      a_lo += own | (other << 16);
+      a_hi += other;
+    }
+  } else if constexpr (CW == 8) {
     // byte (2 * (rank & 1) + asym) of the word: (asym1, sym1, asym0, sym0)
     const uint32_t sel = (x ^ s1) & 3u;
     const uint32_t addr = wb + (x & ~3u);
@@ -202,8 +221,8 @@ __device__ __forceinline__ uint32_t lean_walk(const uint32_t* __restrict__ col, 
   x_next = G == 1 ? t : __shfl_sync(kFullMask, t, gbase + (n_ok & (G - 1)));
   if constexpr (RET && CW != 32) {
     // a_lo = own + (other << 16) mod 2^32; the own-class sum of one segment
-    // stays below 2^32 (at most 57,344 entries of counts < 2^16, or 114,688
-    // of counts < 2^8)
+    // stays below 2^32 (at most 57,344 entries of counts < 2^16, 114,688 of
+    // counts < 2^8 or 229,376 of counts < 2^4)
     bal += a_lo - (a_hi << 16);
     unb += a_hi;
   }
@@ -354,6 +373,25 @@ __device__ __forceinline__ void lean_clear(uint32_t* cnt, uint32_t words, uint64
   const uint32_t quads = (words + 3u) >> 2;
   if constexpr (!FIN) {
     for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) q4[j] = make_uint4(0u, 0u, 0u, 0u);
+  } else if constexpr (CW == 4) {
+    // nibbles (q3, p3, ..., q0, p0): the p's and q's as bytes, then byte dot
+    // products as for 8-bit counters (per-thread sums stay far below 2^32)
+    uint32_t sq = 0, s = 0, pq = 0;
+    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) {
+      const uint4 v = q4[j];
+      if ((v.x | v.y | v.z | v.w) == 0u) continue;
+      const uint32_t a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const uint32_t p = a[k] & 0x0F0F0F0Fu, q = (a[k] >> 4) & 0x0F0F0F0Fu;
+        sq = __dp4a(p, p, __dp4a(q, q, sq));
+        s = __dp4a(p + q, 0x01010101u, s);
+        pq = __dp4a(p, q, pq);
+      }
+      q4[j] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    bal += (uint64_t)((sq - s) >> 1);
+    unb += (uint64_t)pq;
   } else if constexpr (CW == 8) {
     // bytes (q1, p1, q0, p0): sum of squares, sum, and twice the sum of
     // p * q, by 4-way byte dot products (each per-thread sum < 2^32: at most
@@ -405,7 +443,9 @@ __device__ __forceinline__ void lean_clear(uint32_t* cnt, uint32_t words, uint64
 
 __device__ __forceinline__ void window_clear(int cw, bool fin, uint32_t* cnt, uint32_t words, uint64_t& bal,
                                              uint64_t& unb) {
-  if (cw == 8) {
+  if (cw == 4) {
+    if (fin) lean_clear<4, true>(cnt, words, bal, unb); else lean_clear<4, false>(cnt, words, bal, unb);
+  } else if (cw == 8) {
     if (fin) lean_clear<8, true>(cnt, words, bal, unb); else lean_clear<8, false>(cnt, words, bal, unb);
   } else if (cw == 16) {
     if (fin) lean_clear<16, true>(cnt, words, bal, unb); else lean_clear<16, false>(cnt, words, bal, unb);
@@ -418,7 +458,10 @@ template <int G, bool LIST>
 __device__ __forceinline__ void window_walk_dispatch(int cw, bool fin, const uint32_t* __restrict__ col, LaneBatch& b,
                                                      const uint2* src, uint32_t n, uint32_t* next, uint2* slots,
                                                      ListState* ls, const Win& w, uint64_t& bal, uint64_t& unb) {
-  if (cw == 8) {
+  if (cw == 4) {
+    if (fin) window_walk<G, 4, false, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
+    else window_walk<G, 4, true, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
+  } else if (cw == 8) {
     if (fin) window_walk<G, 8, false, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
     else window_walk<G, 8, true, LIST>(col, b, src, n, next, slots, ls, w, bal, unb);
   } else if (cw == 16) {

@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) tips_sweep_kernel(CsrView g,
     if (it >= n_items) break;
     const SweepItem item = items[it];
     const PivotGeom q = pivot_geom(g, item.row);
-    const ItemWindows iw(item);
+    const ItemWindows iw(item, false);  // this sweep has no 4-bit counters
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en;
       init_cursor(g, q, i, item.lo, cur, b, en);
