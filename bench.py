@@ -44,16 +44,18 @@ DEFAULT_WORKLOAD = "polarized-20m-2m-300m"
 UNIT = "G wedges/s"
 L2_BYTES = 129 * 2**20
 
-# Algorithmic bytes per unit of work of the hub window-sweep kernel (the
-# dominant kernel; its counters live in shared memory; cursors are two uint32):
-#   per accepted wedge               : 4 B CSR entry
-#   per (item, lower neighbour) init : 4 B pivot-row entry + 16 B row offsets + 8 B cursor write
-#   per (window, lower neighbour)    : 4 B pivot-row entry (edge sign) + 8 B cursor read
-#   visited by cursor                  + 4 B cursor write + 4 B first entry past the window
-#   per list-mode visit              : the same 20 B + 4 B list entry read + 4 B list append
-# Light / medium tiers: 4 B per wedge + 28 B per lower neighbour (entry,
-# row offsets, end-of-row probe).
-B_WEDGE, B_CUR_INIT, B_CUR_STEP, B_LIST_VISIT, B_LOWER = 4, 28, 20, 28, 28
+# Algorithmic bytes of the method (the roofline's numerator), per unit of
+# work of Algorithm 1's Phase 5 with shared-memory counters:
+#   per accepted wedge                     : 4 B CSR entry of the endpoint
+#   per (pivot, lower neighbour) step      : 4 B pivot-row entry + 16 B row offsets + 8 B end probe
+# (the global-counter terms of a touched-list design are zero: the hub
+# sweep's counters live in shared memory).
+B_WEDGE, B_LOWER = 4, 28
+# Bytes the hub sweep's design adds on top (reported beside the roofline, not
+# in it): per (item, neighbour) slot initialisation 8 B written, per
+# (neighbour, window) cursor step 8 B slot read + 8 B written + 4 B first entry
+# past the window, per list-mode visit the same 20 B + 8 B list append.
+B_CUR_INIT, B_CUR_STEP, B_LIST_VISIT = 8, 20, 28
 
 
 def parse():
@@ -353,8 +355,8 @@ def batch_record(a, torch, dbbc, world, rank, local, dist, barrier, graphs=None,
     union_exact = list(zip(ub.tolist(), uu.tolist())) == plain
 
     # algorithmic bytes of one batch count (all tiers)
-    nbytes = sum(B_WEDGE * i["wedges"] + B_LOWER * (i["lower_light"] + i["lower_medium"])
-                 + B_CUR_INIT * i["hub_cursor_inits"] + B_CUR_STEP * i["hub_cursor_steps"] for i in infos)
+    nbytes = sum(B_WEDGE * i["wedges"] + B_LOWER * (i["lower_light"] + i["lower_medium"] + i["lower_hub"])
+                 for i in infos)
     peaks, peak_kind = measured_peaks()
     per_replay_s = t_ms / 1e3 / a.steps
     achieved = nbytes / per_replay_s / 1e9
@@ -743,8 +745,9 @@ def main():
     n_agg = max(1, int(prof.get("launches_hub_aggregate", 0)))
     agg_s = prof.get("ms_hub_aggregate", 0.0) / 1e3
     list_visits = prof.get("hub_list_visits", 0) / max(1, a.steps)
-    bytes_hub_step = (B_WEDGE * info["wedges_hub"] + B_CUR_INIT * info["hub_cursor_inits"]
-                      + B_CUR_STEP * info["hub_cursor_steps"] + B_LIST_VISIT * list_visits)
+    bytes_hub_step = B_WEDGE * info["wedges_hub"] + B_LOWER * info["lower_hub"]
+    overhead_hub_step = (B_CUR_INIT * info["hub_cursor_inits"] + B_CUR_STEP * info["hub_cursor_steps"]
+                         + B_LIST_VISIT * list_visits)
     per_launch_bytes = bytes_hub_step * a.steps / n_agg
     per_launch_s = agg_s / n_agg
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
@@ -753,7 +756,11 @@ def main():
                 "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                 "traffic": known_traffic("hub_sweep_kernel", a.workload) if a.scale == 1.0 else None,
                 "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "bytes_per_launch": per_launch_bytes, "launches_per_step": n_agg / a.steps,
+                "bytes_per_launch": per_launch_bytes,
+                "bytes_model": "method terms: 4 B per accepted hub wedge + 28 B per hub lower-neighbour step",
+                "design_overhead_bytes_per_launch": overhead_hub_step * a.steps / n_agg,
+                "list_visits_per_launch": list_visits * a.steps / n_agg,
+                "launches_per_step": n_agg / a.steps,
                 "ms_per_launch": 1e3 * per_launch_s,
                 "wedges_per_s_in_kernel": info["wedges_hub"] * a.steps / agg_s if agg_s > 0 else None}
     tiers_ms = {k: prof.get(k, 0.0) / a.steps for k in ("ms_build", "ms_light", "ms_medium", "ms_hub_aggregate",
