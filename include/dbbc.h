@@ -304,7 +304,10 @@ DBBC_API dbbc_status dbbc_count_partition(const dbbc_graph* g, void* cuda_stream
  *                     one scan of its counters (C(p,2) + C(q,2) and p*q per
  *                     endpoint, Lemma 1) when clearing it; sparser items add
  *                     every wedge's Lemma 1 contribution as it is counted
- *                     (0: every item scans; UINT64_MAX: none does).
+ *                     (0: every item scans; UINT64_MAX: none does);
+ *   list_wide_density : list-mode items whose mean (lower neighbour, window)
+ *                     segment is at least this (>= 0) walk each segment with
+ *                     at least 8 lanes instead of 2^list_group_log.
  * Setting and reading the tuning is safe against builds on other threads. */
 typedef struct {
   uint64_t light_max_work;
@@ -315,6 +318,7 @@ typedef struct {
   double list_density;
   int32_t list_group_log;
   uint64_t finalize_window_wedges;
+  double list_wide_density;
 } dbbc_tuning;
 DBBC_API dbbc_status dbbc_set_tuning(const dbbc_tuning* t); /* NULL restores the defaults; DBBC_EINVAL if out of range */
 DBBC_API void dbbc_get_tuning(dbbc_tuning* t);

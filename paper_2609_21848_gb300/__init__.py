@@ -76,7 +76,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("light_max_work", ctypes.c_uint64), ("medium_max_work", ctypes.c_uint64),
                 ("hub_item_work", ctypes.c_uint64), ("group_density", ctypes.c_double * 4),
                 ("hash_mult_log", ctypes.c_int32), ("list_density", ctypes.c_double),
-                ("list_group_log", ctypes.c_int32), ("finalize_window_wedges", ctypes.c_uint64)]
+                ("list_group_log", ctypes.c_int32), ("finalize_window_wedges", ctypes.c_uint64),
+                ("list_wide_density", ctypes.c_double)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -508,8 +509,8 @@ def dbbc_count_partition(g: Graph, part: int, n_parts: int, stream=None) -> tupl
 def dbbc_set_tuning(tuning: dict | None) -> None:
     """Set the tier tuning for graphs built afterwards (None: defaults). Keys:
     light_max_work, medium_max_work, hub_item_work, group_density (4 values),
-    hash_mult_log, list_density, list_group_log, finalize_window_wedges; keys
-    left out keep their current values."""
+    hash_mult_log, list_density, list_group_log, finalize_window_wedges,
+    list_wide_density; keys left out keep their current values."""
     if tuning is None:
         _check(lib().dbbc_set_tuning(None), "dbbc_set_tuning")
         return
@@ -517,7 +518,7 @@ def dbbc_set_tuning(tuning: dict | None) -> None:
     t = Tuning(int(tuning["light_max_work"]), int(tuning["medium_max_work"]), int(tuning["hub_item_work"]),
                (ctypes.c_double * 4)(*[float(x) for x in tuning["group_density"]]), int(tuning["hash_mult_log"]),
                float(tuning["list_density"]), int(tuning["list_group_log"]),
-               min(int(tuning["finalize_window_wedges"]), 2**64 - 1))
+               min(int(tuning["finalize_window_wedges"]), 2**64 - 1), float(tuning["list_wide_density"]))
     _check(lib().dbbc_set_tuning(ctypes.byref(t)), "dbbc_set_tuning")
 
 
@@ -527,7 +528,7 @@ def dbbc_get_tuning() -> dict:
     return {"light_max_work": t.light_max_work, "medium_max_work": t.medium_max_work,
             "hub_item_work": t.hub_item_work, "group_density": list(t.group_density),
             "hash_mult_log": t.hash_mult_log, "list_density": t.list_density, "list_group_log": t.list_group_log,
-            "finalize_window_wedges": t.finalize_window_wedges}
+            "finalize_window_wedges": t.finalize_window_wedges, "list_wide_density": t.list_wide_density}
 
 
 def dbbc_status_string(status: int) -> str:

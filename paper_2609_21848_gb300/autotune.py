@@ -27,7 +27,7 @@ TUNING_DIR = os.path.join(HERE, "tuning")
 
 DEFAULT = {"light_max_work": 512, "medium_max_work": 4096, "hub_item_work": 1 << 20,
            "group_density": [40.0, 16.0, 6.0, 2.0], "hash_mult_log": 1, "list_density": 8.0, "list_group_log": 2,
-           "finalize_window_wedges": 65536}
+           "finalize_window_wedges": 65536, "list_wide_density": 1e30}
 
 SPACE = [
     ("light_max_work", [128, 256, 512]),
@@ -37,9 +37,10 @@ SPACE = [
     ("group_density", [[40.0, 16.0, 6.0, 2.0], [64.0, 24.0, 8.0, 3.0], [24.0, 10.0, 4.0, 1.5],
                        [96.0, 32.0, 12.0, 4.0], [128.0, 48.0, 12.0, 4.0], [128.0, 48.0, 16.0, 6.0],
                        [192.0, 64.0, 16.0, 6.0], [256.0, 96.0, 24.0, 8.0]]),
-    ("list_density", [0.0, 4.0, 8.0, 16.0, 32.0, 64.0]),
+    ("list_density", [0.0, 4.0, 8.0, 16.0, 32.0, 64.0, 128.0]),
     ("list_group_log", [2, 3, 4, 5]),
     ("finalize_window_wedges", [0, 16384, 65536, 262144, 2**64 - 1]),
+    ("list_wide_density", [16.0, 32.0, 48.0, 1e30]),
 ]
 
 

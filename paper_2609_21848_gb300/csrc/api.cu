@@ -142,7 +142,7 @@ dbbc_status dbbc_set_tuning(const dbbc_tuning* t) {
   if (t->light_max_work < 1 || t->light_max_work > kLightMaxWork || t->medium_max_work < t->light_max_work ||
       t->medium_max_work > kMediumMaxWork || t->hub_item_work < 1024 || t->hash_mult_log < 1 ||
       t->hash_mult_log > 3 || !(t->list_density >= 0) || t->list_group_log < 0 || t->list_group_log > 5 ||
-      t->list_group_log == 1)
+      t->list_group_log == 1 || !(t->list_wide_density >= 0))
     return DBBC_EINVAL;
   for (int i = 0; i < 4; i++)
     if (!(t->group_density[i] >= 0) || (i > 0 && t->group_density[i] > t->group_density[i - 1])) return DBBC_EINVAL;
@@ -155,6 +155,7 @@ dbbc_status dbbc_set_tuning(const dbbc_tuning* t) {
   n.list_density = t->list_density;
   n.list_group_log = t->list_group_log;
   n.finalize_window_wedges = t->finalize_window_wedges;
+  n.list_wide_density = t->list_wide_density;
   std::lock_guard<std::mutex> lock(g_tuning_mu);
   g_tuning = n;
   return DBBC_OK;
@@ -171,6 +172,7 @@ void dbbc_get_tuning(dbbc_tuning* t) {
   t->list_density = c.list_density;
   t->list_group_log = c.list_group_log;
   t->finalize_window_wedges = c.finalize_window_wedges;
+  t->list_wide_density = c.list_wide_density;
 }
 
 void dbbc_set_allocator(void* (*alloc_fn)(size_t, void*, void*), void (*free_fn)(void*, void*, void*), void* ctx) {

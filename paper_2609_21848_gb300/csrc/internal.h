@@ -66,6 +66,7 @@ struct Tuning {
   double list_density = 8.0;  // hubs with a mean (neighbour, window) segment shorter than this use list mode
   int32_t list_group_log = 2; // lanes per neighbour segment in list mode (log2)
   uint64_t finalize_window_wedges = kFinalizeWindowWedges;  // see kItemFinalize
+  double list_wide_density = 1e30;  // list-mode items with a mean segment at least this use >= 8 lanes
 };
 Tuning current_tuning();  // a copy, taken under the tuning lock
 

@@ -511,7 +511,12 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
       p.it.q_end = (uint32_t)quarter_end;
       p.it.t_end = (uint32_t)tiny_end;
       p.it.n_end = (uint32_t)narrow_end;
-      p.it.group_log = listed ? (int16_t)g->tune.list_group_log : dense_log;
+      // list-mode items take list_group_log lanes per segment, at least 8 when
+      // their mean segment reaches list_wide_density
+      const int16_t list_log = (int16_t)(density >= g->tune.list_wide_density
+                                             ? std::max<int32_t>(3, g->tune.list_group_log)
+                                             : g->tune.list_group_log);
+      p.it.group_log = listed ? list_log : dense_log;
       p.it.flags = listed ? kItemList : 0;
       // dense items: finalise each window from its counters when clearing it
       if ((double)W / (double)R_all >= (double)g->tune.finalize_window_wedges) p.it.flags |= kItemFinalize;

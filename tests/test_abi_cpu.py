@@ -82,13 +82,14 @@ def test_tuning_round_trip_and_validation(lib):
     try:
         t = dict(light_max_work=128, medium_max_work=2048, hub_item_work=1 << 19,
                  group_density=[64.0, 24.0, 8.0, 3.0], hash_mult_log=2, list_density=12.0, list_group_log=4,
-                 finalize_window_wedges=1 << 17)
+                 finalize_window_wedges=1 << 17, list_wide_density=24.0)
         dbbc.dbbc_set_tuning(t)
         assert dbbc.dbbc_get_tuning() == t
         for bad in (dict(t, light_max_work=0), dict(t, light_max_work=1024), dict(t, medium_max_work=64),
                     dict(t, medium_max_work=8192), dict(t, hub_item_work=10), dict(t, hash_mult_log=0),
                     dict(t, hash_mult_log=4), dict(t, group_density=[1.0, 2.0, 3.0, 4.0]),
-                    dict(t, list_density=-1.0), dict(t, list_group_log=1), dict(t, list_group_log=6)):
+                    dict(t, list_density=-1.0), dict(t, list_group_log=1), dict(t, list_group_log=6),
+                    dict(t, list_wide_density=-1.0)):
             with pytest.raises(dbbc.DbbcError):
                 dbbc.dbbc_set_tuning(bad)
         assert dbbc.dbbc_get_tuning() == t  # rejected settings change nothing
@@ -108,10 +109,10 @@ def test_tuning_reads_are_whole_under_concurrent_sets(lib):
     base = dbbc.dbbc_get_tuning()
     a = dict(light_max_work=128, medium_max_work=1024, hub_item_work=1 << 19,
              group_density=[40.0, 16.0, 6.0, 2.0], hash_mult_log=1, list_density=4.0, list_group_log=2,
-             finalize_window_wedges=0)
+             finalize_window_wedges=0, list_wide_density=32.0)
     b = dict(light_max_work=512, medium_max_work=4096, hub_item_work=1 << 22,
              group_density=[128.0, 48.0, 12.0, 4.0], hash_mult_log=3, list_density=32.0, list_group_log=5,
-             finalize_window_wedges=2**64 - 1)
+             finalize_window_wedges=2**64 - 1, list_wide_density=1e30)
     seen, errors = [], []
 
     def writer(t):

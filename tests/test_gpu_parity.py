@@ -305,6 +305,9 @@ def test_union_build_validates_each_component():
     dict(light_max_work=1, medium_max_work=1, hub_item_work=1024, group_density=[1e9, 1e9, 1e9, 1e9],
          hash_mult_log=1, list_density=1e9, list_group_log=0,
          finalize_window_wedges=2**64 - 1),   # every wedge's Lemma 1 term from its atomic, one lane
+    dict(light_max_work=1, medium_max_work=1, hub_item_work=1024, group_density=[40.0, 16.0, 6.0, 2.0],
+         hash_mult_log=1, list_density=1e9, list_group_log=2,
+         list_wide_density=0.0),   # every pivot a list-mode hub, 8-lane groups
 ])
 def test_counts_do_not_depend_on_tuning(tuning):
     base = dbbc.dbbc_get_tuning()
