@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     const PivotGeom q = pivot_geom(g, item.row);
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en, s1;
-      lean_cursor_start(g, q, i, item.lo, b, en, s1);
+      lean_cursor_start(g, q, i, (item.flags & kItemFirst) ? 0u : item.lo, b, en, s1);
       cur[i] = lean_slot(b, en, s1);
     }
     __syncthreads();

@@ -96,6 +96,9 @@ constexpr int16_t kItemList = 2;  // list mode: visit a neighbour only in window
 // counters of a window are finalised when it is cleared (C(p,2) + C(q,2) and
 // p*q per endpoint) instead of wedge by wedge
 constexpr int16_t kItemFinalize = 4;
+// the item starts at its hub's first accepted rank: no row lists a rank below
+// it, so a neighbour's cursor starts at the row's first entry (no search)
+constexpr int16_t kItemFirst = 8;
 // Counts below this fit the 8-bit halves of a tiny counter, and below the
 // next the 4-bit halves of a quarter counter.
 constexpr int32_t kTinyCountLimit = 256;

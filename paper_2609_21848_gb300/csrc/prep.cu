@@ -520,6 +520,7 @@ static void plan_hubs(dbbc_graph* g, cudaStream_t s, const UnionSpec& un) {
       p.it.flags = listed ? kItemList : 0;
       // dense items: finalise each window from its counters when clearing it
       if ((double)W / (double)R_all >= (double)g->tune.finalize_window_wedges) p.it.flags |= kItemFinalize;
+      if (w0 == 0) p.it.flags |= kItemFirst;
       p.est = std::max<uint64_t>(1, W / spans);
       plan.push_back(p);
       const int64_t R = (int64_t)(w1 - w0);

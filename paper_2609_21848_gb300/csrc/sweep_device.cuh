@@ -557,7 +557,7 @@ __device__ __forceinline__ uint64_t sweep_list_item(const CsrView& g, const Swee
     if (s0 == 0) {  // each neighbour joins the list of the window of its first entry
       for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
         uint32_t b, en, s1;
-        lean_cursor_start(g, q, i, item.lo, b, en, s1);
+        lean_cursor_start(g, q, i, (item.flags & kItemFirst) ? 0u : item.lo, b, en, s1);
         if (b < en) list_queue(ls, g.col[b], b, en, s1);
       }
     } else {  // the neighbours that waited for this span

@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) tips_sweep_kernel(CsrView g,
     const ItemWindows iw(item, false);  // this sweep has no 4-bit counters
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en;
-      init_cursor(g, q, i, item.lo, cur, b, en);
+      init_cursor(g, q, i, (item.flags & kItemFirst) ? 0u : item.lo, cur, b, en);
     }
     __syncthreads();
     uint64_t pb = 0, pu = 0;
