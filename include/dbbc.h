@@ -326,8 +326,29 @@ DBBC_API void dbbc_get_tuning(dbbc_tuning* t);
 /* Static description of a status code. */
 DBBC_API const char* dbbc_status_string(dbbc_status s);
 
-/* Library version as "major.minor.patch". */
+/* Library version as "major.minor.patch" ("+checked" appended in a checked build). */
 DBBC_API const char* dbbc_version(void);
+
+/* Checked builds. A library compiled with -DDBBC_CHECKED=1 is a debug build of
+   the same kernels in which every index derived from graph data is tested
+   before the access it guards: CSR row and entry positions, the shared-memory
+   address of every window counter of the hub sweep (and that the entry lies at
+   or past the window's first rank), cursor and neighbour-list slots against
+   their capacity, and per-vertex / per-edge output positions. A failed test
+   skips the access (the counts are then wrong) and records bit 2 in a flag
+   word of the library; nothing traps. Synchronous calls (dbbc_count,
+   dbbc_count_profiled, dbbc_graph_from_coo[_multi], dbbc_count_vertices,
+   dbbc_count_edges, dbbc_batch_count, ...) collect the flags before they
+   return and fail with DBBC_EINTERNAL when one is set.
+
+   dbbc_is_checked: 1 in a checked build, 0 in a regular one.
+   dbbc_checked_flags: synchronizes the current device, stores in *flags the OR
+   of the bits recorded since the last collection (2: an index left its array)
+   and clears them; in a regular build stores 0. DBBC_EINVAL if flags is NULL,
+   DBBC_ECUDA if the device cannot be synchronized. The flag words are per
+   device and per process: calls on several host threads share them. */
+DBBC_API int dbbc_is_checked(void);
+DBBC_API dbbc_status dbbc_checked_flags(uint32_t* flags);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,9 @@ Functions carry the C names (``EXPORTED`` lists them all):
 - several GPUs: :func:`dbbc_lpt_partition`, :func:`dbbc_count_partition`;
 - housekeeping: :func:`dbbc_set_tuning`, :func:`dbbc_get_tuning`,
   :func:`dbbc_set_allocator`, :func:`dbbc_kernel_launches`,
-  :func:`dbbc_status_string`, :func:`dbbc_version`.
+  :func:`dbbc_status_string`, :func:`dbbc_version`;
+- the bounds-checked debug build (``buildlib.build_checked()``, loaded when
+  ``DBBC_LIBRARY`` names it): :func:`dbbc_is_checked`, :func:`dbbc_checked_flags`.
 """
 from __future__ import annotations
 
@@ -43,7 +45,7 @@ EXPORTED = (
     "dbbc_kernel_launches", "dbbc_count_noalloc", "dbbc_batch_create", "dbbc_batch_count_async",
     "dbbc_batch_count", "dbbc_batch_free", "dbbc_graph_from_coo_multi", "dbbc_count_components",
     "dbbc_set_tuning", "dbbc_get_tuning", "dbbc_lpt_partition", "dbbc_count_partition",
-    "dbbc_count_vertices", "dbbc_count_edges",
+    "dbbc_count_vertices", "dbbc_count_edges", "dbbc_is_checked", "dbbc_checked_flags",
 )
 
 
@@ -158,6 +160,10 @@ def lib() -> ctypes.CDLL:
         L.dbbc_status_string.restype = ctypes.c_char_p
         L.dbbc_version.argtypes = []
         L.dbbc_version.restype = ctypes.c_char_p
+        L.dbbc_is_checked.argtypes = []
+        L.dbbc_is_checked.restype = ctypes.c_int
+        L.dbbc_checked_flags.argtypes = [P]
+        L.dbbc_checked_flags.restype = st
         _lib = L
         if not os.environ.get("DBBC_NO_TUNING"):
             from . import autotune
@@ -537,6 +543,19 @@ def dbbc_status_string(status: int) -> str:
 
 def dbbc_version() -> str:
     return lib().dbbc_version().decode()
+
+
+def dbbc_is_checked() -> bool:
+    """True when the loaded library is the bounds-checked build (-DDBBC_CHECKED=1)."""
+    return bool(lib().dbbc_is_checked())
+
+
+def dbbc_checked_flags() -> int:
+    """Bounds-check flags recorded since the last call (2: an index left its
+    array), then cleared; always 0 in a regular build. Synchronizes the device."""
+    f = ctypes.c_uint32(0)
+    _check(lib().dbbc_checked_flags(ctypes.byref(f)), "dbbc_checked_flags")
+    return f.value
 
 
 def count_coo(u, v, sign, n_u: int, n_v: int, stream=None) -> tuple[int, int]:

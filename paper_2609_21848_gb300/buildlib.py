@@ -38,10 +38,27 @@ def _deps():
         [os.path.join(os.path.dirname(HERE), "include", "dbbc.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+# The bounds-checked debug build (-DDBBC_CHECKED=1): kernels test every index
+# they derive from graph data and record a flag instead of accessing out of
+# bounds (see dbbc_checked_flags in include/dbbc.h).
+CHECKED_DIR = os.path.join(OUT_DIR, "checked")
+CHECKED_FLAGS = ["-DDBBC_CHECKED=1"]
+
+
+def _stamp(lib_path: str) -> str:
+    return lib_path + ".flags"
+
+
+def up_to_date(lib_path: str = LIB, extra_flags: list[str] | None = None) -> bool:
+    """The library at lib_path exists, is newer than every source and was
+    built with the same extra flags."""
+    if not os.path.exists(lib_path):
         return False
-    t = os.path.getmtime(LIB)
+    want = " ".join(extra_flags or [])
+    have = open(_stamp(lib_path)).read() if os.path.exists(_stamp(lib_path)) else ""
+    if have != want:
+        return False
+    t = os.path.getmtime(lib_path)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -50,8 +67,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     """Build the library (into ``out_dir`` instead of ``_build/`` when given,
     e.g. for a variant with -D overrides)."""
     lib_path = os.path.join(out_dir, "libdbbc.so") if out_dir else LIB
-    if not force and up_to_date() and not extra_flags and not out_dir:
-        return LIB
+    if not force and up_to_date(lib_path, extra_flags):
+        return lib_path
     obj_dir = out_dir or OUT_DIR
     os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
@@ -74,8 +91,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    with open(_stamp(lib_path), "w") as f:
+        f.write(" ".join(extra_flags or []))
     os.replace(tmp, lib_path)
     return lib_path
+
+
+def build_checked(force: bool = False) -> str:
+    """Build the bounds-checked library into ``_build/checked/``."""
+    return build(force=force, extra_flags=CHECKED_FLAGS, out_dir=CHECKED_DIR)
 
 
 if __name__ == "__main__":

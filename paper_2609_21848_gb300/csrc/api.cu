@@ -30,6 +30,36 @@ Tuning current_tuning() {
   return g_tuning;
 }
 
+// Flag words of the translation units of a checked build (see common.cuh).
+namespace {
+std::mutex g_checked_mu;
+std::vector<unsigned (*)()>& checked_units() {
+  static std::vector<unsigned (*)()> units;
+  return units;
+}
+}  // namespace
+
+void checked_register(unsigned (*take)()) {
+  std::lock_guard<std::mutex> lock(g_checked_mu);
+  checked_units().push_back(take);
+}
+
+unsigned checked_take_all() {
+  if (!DBBC_CHECKED) return 0u;
+  DBBC_CUDA(cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lock(g_checked_mu);
+  unsigned f = 0;
+  for (unsigned (*take)() : checked_units()) f |= take();
+  return f;
+}
+
+void raise_device_status(unsigned h) {
+  h |= checked_take_all();
+  if (h & DBBC_DEV_RANGE) throw Error{DBBC_EINTERNAL, "index out of range (checked build)"};
+  if (h & DBBC_DEV_HASH_FULL) throw Error{DBBC_EINTERNAL, "shared hash table overflow"};
+  if (h) throw Error{DBBC_EINTERNAL, "device status"};
+}
+
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
@@ -108,8 +138,7 @@ static void check_status_word(const unsigned* d_status, cudaStream_t s) {
   unsigned h = 0;
   DBBC_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
   DBBC_CUDA(cudaStreamSynchronize(s));
-  if (h & DBBC_DEV_HASH_FULL) throw Error{DBBC_EINTERNAL, "shared hash table overflow"};
-  if (h) throw Error{DBBC_EINTERNAL, "device status"};
+  raise_device_status(h);
 }
 
 }  // namespace dbbc
@@ -118,7 +147,14 @@ using namespace dbbc;
 
 extern "C" {
 
-const char* dbbc_version(void) { return "0.1.0"; }
+const char* dbbc_version(void) { return DBBC_CHECKED ? "0.1.0+checked" : "0.1.0"; }
+
+int dbbc_is_checked(void) { return DBBC_CHECKED ? 1 : 0; }
+
+dbbc_status dbbc_checked_flags(uint32_t* flags) {
+  if (!flags) return DBBC_EINVAL;
+  return guarded([&] { *flags = checked_take_all(); });
+}
 
 const char* dbbc_status_string(dbbc_status s) {
   switch (s) {
@@ -205,6 +241,7 @@ dbbc_status dbbc_graph_from_coo(const int32_t* u, const int32_t* v, const int8_t
   const dbbc_status st = guarded([&] {
     DBBC_CUDA(cudaGetDevice(&g->device));
     build_graph(g, u, v, sign, m, (flags & DBBC_INPUT_DEVICE) != 0, (flags & DBBC_DUP_REJECT) != 0, g->stream);
+    if (DBBC_CHECKED) raise_device_status(0u);
   });
   if (st != DBBC_OK) {
     free_graph_memory(g);
@@ -234,6 +271,7 @@ dbbc_status dbbc_graph_from_coo_multi(const int32_t* u, const int32_t* v, const 
     DBBC_CUDA(cudaGetDevice(&g->device));
     build_graph_multi(g, u, v, sign, n_graphs > 0 ? edge_offsets : &zero, n_u, n_v, n_graphs,
                       (flags & DBBC_INPUT_DEVICE) != 0, (flags & DBBC_DUP_REJECT) != 0, g->stream);
+    if (DBBC_CHECKED) raise_device_status(0u);
   });
   if (st != DBBC_OK) {
     free_graph_memory(g);

@@ -18,6 +18,7 @@ struct GraphDesc {
   const uint32_t* lower;
   const uint64_t* work;
   int64_t n;
+  int64_t nnz;
   int32_t n_u;
   int32_t hash_mult_log;
 };
@@ -39,7 +40,7 @@ struct GatherJob {
   int64_t medium_off, light_off;
 };
 
-__device__ __forceinline__ CsrView view_of(const GraphDesc& d) { return CsrView{d.row_ptr, d.col, d.lower, d.n_u, d.n}; }
+__device__ __forceinline__ CsrView view_of(const GraphDesc& d) { return CsrView{d.row_ptr, d.col, d.lower, d.n_u, d.n, d.nnz}; }
 
 // One CTA per graph copies its medium and light pivots into the batch lists.
 __global__ void gather_pivots_kernel(const GatherJob* __restrict__ jobs, BatchPivot* __restrict__ med,
@@ -198,14 +199,15 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     const SweepItem item = bi.it;
     const CsrView g = view_of(desc[bi.graph]);
     const PivotGeom q = pivot_geom(g, item.row);
-    for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
+    const uint32_t L = DBBC_CHECK((int64_t)q.L <= cur_cap) ? q.L : 0u;  // checked builds: cursor capacity
+    for (uint32_t i = tid; i < L; i += kSweepThreads) {
       uint32_t b, en, s1;
       lean_cursor_start(g, q, i, (item.flags & kItemFirst) ? 0u : item.lo, b, en, s1);
       cur[i] = lean_slot(b, en, s1);
     }
     __syncthreads();
     uint64_t bal = 0, unb = 0;
-    sweep_cursor_item_dispatch(item.group_log, g.col, q.L, cur, ItemWindows(item), (item.flags & kItemFinalize) != 0,
+    sweep_cursor_item_dispatch(item.group_log, g.col, L, cur, ItemWindows(item), (item.flags & kItemFinalize) != 0,
                                sbase, cnt_words, nbn, bal, unb);
     block_add_pair<kSweepThreads>(bal, unb, out + 2 * bi.graph);
   }
@@ -257,7 +259,7 @@ static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector
 // union's CSR; pivots and hub items are tagged with their component.
 static void plan_components(dbbc_batch* b, const dbbc_graph* g) {
   cudaStream_t s = b->stream;
-  std::vector<GraphDesc> desc((size_t)b->n_graphs, GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u, g->tune.hash_mult_log});
+  std::vector<GraphDesc> desc((size_t)b->n_graphs, GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->nnz, g->n_u, g->tune.hash_mult_log});
   b->n_medium = g->n_medium;
   b->n_light = g->n_light;
   b->max_lower = std::max<int64_t>(1, g->sweep_max_lower);
@@ -301,7 +303,7 @@ static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
   std::vector<HubRef> hubs;
   for (int32_t i = 0; i < n; i++) {
     const dbbc_graph* g = gs[i];
-    desc[(size_t)i] = GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u, g->tune.hash_mult_log};
+    desc[(size_t)i] = GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->nnz, g->n_u, g->tune.hash_mult_log};
     jobs[(size_t)i] = GatherJob{g->order, g->n_hub, g->n_medium, g->n_light, b->n_medium, b->n_light};
     b->n_medium += g->n_medium;
     b->n_light += g->n_light;
@@ -391,7 +393,7 @@ static void check_batch_status(const dbbc_batch* b, cudaStream_t s) {
   unsigned h = 0;
   DBBC_CUDA(cudaMemcpyAsync(&h, b->status, sizeof(h), cudaMemcpyDeviceToHost, s));
   DBBC_CUDA(cudaStreamSynchronize(s));
-  if (h) throw Error{DBBC_EINTERNAL, "device status"};
+  raise_device_status(h);
 }
 
 template <typename F>
@@ -421,7 +423,7 @@ void count_subset(const dbbc_graph* g, cudaStream_t s, const std::vector<int32_t
   try {
     DBBC_CUDA(cudaGetDevice(&b->device));
     set_batch_attributes();
-    std::vector<GraphDesc> desc(1, GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->n_u,
+    std::vector<GraphDesc> desc(1, GraphDesc{g->row_ptr, g->col, g->lower, g->work, g->n, g->nnz, g->n_u,
                                               g->tune.hash_mult_log});
     b->n_medium = (int64_t)medium_rows.size();
     b->n_light = (int64_t)light_rows.size();

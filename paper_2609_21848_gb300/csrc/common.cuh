@@ -31,6 +31,59 @@ struct Error {
     }                                                             \
   } while (0)
 
+// Status bits written by kernels (device status word).
+enum : unsigned {
+  DBBC_DEV_HASH_FULL = 1u,  // a shared hash table ran out of slots (tier sizing bug)
+  DBBC_DEV_RANGE = 2u,      // an index left its array (checked builds only)
+};
+
+// ---------------------------------------------------------------- checked builds
+// A library built with -DDBBC_CHECKED=1 tests the indexes its kernels derive
+// from graph data before each access: CSR row and entry positions, the
+// shared-memory address of every window counter, cursor and list slots, and
+// per-vertex / per-edge output positions. A failed test skips the access and
+// sets DBBC_DEV_RANGE in a flag word of the translation unit; the host
+// collects every unit's word with checked_take_all(). In a regular build
+// DBBC_CHECK(cond) is the constant true and generates no code.
+#ifndef DBBC_CHECKED
+#define DBBC_CHECKED 0
+#endif
+
+void checked_register(unsigned (*take)());
+// OR of every unit's flag word since the last call, then cleared (synchronizes
+// the current device); 0 without synchronizing in a regular build.
+unsigned checked_take_all();
+
+#if DBBC_CHECKED
+static __device__ unsigned g_checked_flags;
+
+__device__ __forceinline__ bool checked_ok(bool ok) {
+  if (!ok) atomicOr(&g_checked_flags, DBBC_DEV_RANGE);
+  return ok;
+}
+#define DBBC_CHECK(cond) (::dbbc::checked_ok(cond))
+
+namespace {
+// Registers this translation unit's flag word with the collector.
+struct CheckedUnit {
+  static unsigned take() {
+    unsigned h = 0;
+    const unsigned z = 0;
+    if (cudaMemcpyFromSymbol(&h, g_checked_flags, sizeof(h)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return DBBC_DEV_RANGE;  // an unreadable flag word counts as a failed check
+    }
+    if (h && cudaMemcpyToSymbol(g_checked_flags, &z, sizeof(z)) != cudaSuccess) (void)cudaGetLastError();
+    return h;
+  }
+  CheckedUnit() { checked_register(&take); }
+};
+static CheckedUnit checked_unit_;
+}  // namespace
+#else
+#define DBBC_CHECK(cond) true
+#endif
+
 void note_launch();                // counts kernels launched by the library
 void note_launches(uint64_t k);    // k kernels launched at once (a CUDA graph replay)
 uint64_t launches_so_far();

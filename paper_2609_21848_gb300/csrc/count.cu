@@ -123,13 +123,14 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_kernel(CsrView g, con
       n_visits += sweep_list_item_dispatch(g, item, q, my_lists, list_cap, ls, sbase, cnt_words, nbn, bal, unb);
       continue;
     }
-    for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
+    const uint32_t L = DBBC_CHECK((int64_t)q.L <= cur_cap) ? q.L : 0u;  // checked builds: cursor capacity
+    for (uint32_t i = tid; i < L; i += kSweepThreads) {
       uint32_t b, en, s1;
       lean_cursor_start(g, q, i, (item.flags & kItemFirst) ? 0u : item.lo, b, en, s1);
       cur[i] = lean_slot(b, en, s1);
     }
     __syncthreads();
-    sweep_cursor_item_dispatch(item.group_log, g.col, q.L, cur, ItemWindows(item), (item.flags & kItemFinalize) != 0,
+    sweep_cursor_item_dispatch(item.group_log, g.col, L, cur, ItemWindows(item), (item.flags & kItemFinalize) != 0,
                                sbase, cnt_words, nbn, bal, unb);
   }
   block_add_pair<kSweepThreads>(bal, unb, out);
@@ -223,7 +224,7 @@ static void launch_hub(const dbbc_graph* g, const CsrView& view, cudaStream_t s,
 void enqueue_count(const dbbc_graph* g, cudaStream_t s, unsigned long long* d_out, unsigned* d_status,
                    Scratch& sc, CountProfiler* prof) {
   if (g->n_piv == 0) return;
-  const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
+  const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n, g->nnz};
   cudaEvent_t t_all = prof ? prof->begin(s) : nullptr;
   cudaEvent_t t0 = nullptr;
   if (g->n_light > 0) {
@@ -272,7 +273,7 @@ void enqueue_count_prealloc(const dbbc_graph* g, cudaStream_t s, unsigned long l
   DBBC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(unsigned), s));
   DBBC_CUDA(cudaMemsetAsync(d_out, 0, 2 * sizeof(unsigned long long), s));
   if (g->n_piv == 0) return;
-  const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
+  const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n, g->nnz};
   int64_t hub_grid = 0;
   if (g->n_hub > 0) {
     const size_t per_cta = (size_t)g->sweep_max_lower * sizeof(uint2);

@@ -69,12 +69,33 @@ struct PivotGeom {
 
 __device__ __forceinline__ PivotGeom pivot_geom(const CsrView& g, int32_t p) {
   PivotGeom q;
+  const bool ok = DBBC_CHECK(p >= 0 && p < g.n);  // checked builds: a bad pivot walks no neighbour
+  if (!ok) p = 0;
   q.rb = g.row_ptr[p];
-  q.L = g.lower[p];
+  q.L = ok ? g.lower[p] : 0u;
+#if DBBC_CHECKED
+  if (q.L && !DBBC_CHECK(q.rb >= 0 && q.rb + q.L <= g.row_ptr[p + 1] && g.row_ptr[p + 1] <= g.nnz)) q.L = 0;
+#endif
   const bool is_u = p < g.n_u;
   q.lim = (is_u ? (uint32_t)p : (uint32_t)(p - g.n_u)) << 1;
   q.base = is_u ? (int64_t)g.n_u : 0;
   return q;
+}
+
+// Row [b, en) of the vertex of the other side named by the CSR entry e of a
+// pivot with geometry q, and the sign bit of their edge. Checked builds test
+// the row index and bounds; a failed test gives an empty row.
+__device__ __forceinline__ uint32_t neighbour_row(const CsrView& g, const PivotGeom& q, uint32_t e, int64_t& b,
+                                                  int64_t& en) {
+  const int64_t vrow = q.base + (e >> 1);
+  if (DBBC_CHECK(vrow >= 0 && vrow < g.n)) {
+    b = g.row_ptr[vrow];
+    en = g.row_ptr[vrow + 1];
+    if (!DBBC_CHECK(b >= 0 && b <= en && en <= g.nnz)) en = b;
+  } else {
+    b = en = 0;
+  }
+  return e & 1u;
 }
 
 // The warp walks lower-neighbour positions [a, b) of the pivot in groups of
@@ -91,9 +112,7 @@ __device__ __forceinline__ void warp_walk(const CsrView& g, const PivotGeom& q, 
     int64_t vb = 0, ve = 0;
     if (i0 + lane < b) {
       e = g.col[q.rb + i0 + lane];
-      const int64_t vrow = q.base + (e >> 1);
-      vb = g.row_ptr[vrow];
-      ve = g.row_ptr[vrow + 1];
+      neighbour_row(g, q, e, vb, ve);
     }
     const uint32_t cnt = min(32u, b - i0);
     for (uint32_t k = 0; k < cnt; k++) {
@@ -144,23 +163,11 @@ __device__ __forceinline__ bool hash_walk(uint32_t gid, uint32_t groups, const C
   bool fits = true;
   int64_t b_nx = 0, en_nx = 0;
   uint32_t s1_nx = 0;
-  if (gid < q.L) {
-    const uint32_t e = g.col[q.rb + gid];
-    const int64_t vrow = q.base + (e >> 1);
-    b_nx = g.row_ptr[vrow];
-    en_nx = g.row_ptr[vrow + 1];
-    s1_nx = e & 1u;
-  }
+  if (gid < q.L) s1_nx = neighbour_row(g, q, g.col[q.rb + gid], b_nx, en_nx);
   for (uint32_t i = gid; i < q.L; i += groups) {
     const int64_t b = b_nx, en = en_nx;
     const uint32_t s1 = s1_nx;
-    if (i + groups < q.L) {
-      const uint32_t e = g.col[q.rb + i + groups];
-      const int64_t vrow = q.base + (e >> 1);
-      b_nx = g.row_ptr[vrow];
-      en_nx = g.row_ptr[vrow + 1];
-      s1_nx = e & 1u;
-    }
+    if (i + groups < q.L) s1_nx = neighbour_row(g, q, g.col[q.rb + i + groups], b_nx, en_nx);
     for (int64_t c = b; c < en; c += G) {
       const int64_t j = c + gl;
       const uint32_t x = j < en ? g.col[j] : 0xFFFFFFFFu;
@@ -310,6 +317,7 @@ struct ItemWindows {
 template <int CW>
 __device__ __forceinline__ void add_wedge(bool ok, uint32_t k, uint32_t asym, uint32_t* c16, unsigned long long* c32,
                                           uint32_t& acc_same, uint32_t& acc_other, uint64_t& bal, uint64_t& unb) {
+  if (ok && !DBBC_CHECK(k < window_ranks<CW>())) ok = false;
   if (CW == 8) {
     const uint32_t wsh = (k & 1u) << 4;  // which half of the word
     uint32_t old = 0;
@@ -373,10 +381,8 @@ __device__ __forceinline__ uint32_t walk_segment(const uint32_t* col, uint32_t c
 // after rank `lo_rank`, and the row end.
 __device__ __forceinline__ void init_cursor(const CsrView& g, const PivotGeom& q, uint32_t i, uint32_t lo_rank,
                                             uint32_t* cur, uint32_t& b_out, uint32_t& en_out) {
-  const uint32_t e = g.col[q.rb + i];
-  const int64_t vrow = q.base + (e >> 1);
-  int64_t b = g.row_ptr[vrow];
-  const int64_t en = g.row_ptr[vrow + 1];
+  int64_t b, en;
+  neighbour_row(g, q, g.col[q.rb + i], b, en);
   const uint32_t first = lo_rank << 1;
   if (first) {  // lower_bound of `first` in the row
     int64_t lo = b, hi = en;

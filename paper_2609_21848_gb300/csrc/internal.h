@@ -70,6 +70,11 @@ struct Tuning {
 };
 Tuning current_tuning();  // a copy, taken under the tuning lock
 
+// Throws the error a kernel status word h (already read back) stands for; in
+// a checked build it first adds the bounds-check flags of every kernel run
+// since the last collection (synchronizing the device).
+void raise_device_status(unsigned h);
+
 // Counts below this fit the 16-bit halves of a narrow counter.
 constexpr int32_t kNarrowCountLimit = 65536;
 
@@ -115,15 +120,11 @@ struct CsrView {
   const uint32_t* lower;
   int32_t n_u;
   int64_t n;
+  int64_t nnz;  // row_ptr[n]
 };
 
 }  // namespace dbbc
 
-// Status bits written by kernels (device status word).
-enum : unsigned {
-  DBBC_DEV_HASH_FULL = 1u,  // a shared hash table ran out of slots (tier sizing bug)
-  DBBC_DEV_RANGE = 2u,      // an index left its array (checked paths only)
-};
 
 struct dbbc_graph {
   int device = 0;

@@ -143,6 +143,7 @@ __global__ void ranks_kernel(const uint64_t* __restrict__ skey, int64_t n, int32
     const int32_t c = bits_comp ? (int32_t)((k >> (bits_deg + bits_id)) & comp_mask) : 0;
     const int64_t local = (int64_t)(k & id_mask);
     const int32_t x = side ? (int32_t)(n_u + un.voff[c] + local) : (int32_t)(un.uoff[c] + local);
+    if (!DBBC_CHECK(x >= 0 && x < n)) continue;
     vertex[r] = x;
     side_rank[x] = side ? (int32_t)(r - n_u) : (int32_t)r;
     rowdeg[r] = (int32_t)((k >> bits_id) & deg_mask);

@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const K* __re
 #pragma unroll
   for (int j = 0; j < kRsItems; j++) {
     const uint32_t d = dg[j];
-    if (d < 256u) {
-      const uint32_t pos = bstart[d] + wh[w * 256 + d] + loc[j];
+    const uint32_t pos = d < 256u ? bstart[d] + wh[w * 256 + d] + loc[j] : 0u;
+    if (d < 256u && DBBC_CHECK(pos < (uint32_t)kRsTile)) {
       sk[pos] = key[j];
       if (HAS_V) sv[pos] = val[j];
     }
@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const K* __re
     const K k = sk[i];
     const uint32_t d = rs_digit(k, shift);
     const int64_t g = (int64_t)gofs[d] + (i - (int64_t)bstart[d]);
+    if (!DBBC_CHECK(g >= 0 && g < n)) continue;
     kout[g] = k;
     if (HAS_V) vout[g] = sv[i];
   }

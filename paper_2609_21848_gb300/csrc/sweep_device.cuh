@@ -53,11 +53,20 @@ struct Win {
   uint32_t h;
   uint32_t wb;
   uint32_t words;  // 32-bit words in use
+#if DBBC_CHECKED
+  uint32_t l;             // wlo << 1: no entry below it may be counted
+  uint32_t s_lo, s_hi;    // the counter buffer's shared byte addresses [s_lo, s_hi)
+#endif
 };
 
 __device__ __forceinline__ Win make_win(int cw, uint32_t wlo, uint32_t whi, uint32_t sbase) {
   Win w;
   w.h = whi << 1;
+#if DBBC_CHECKED
+  w.l = wlo << 1;
+  w.s_lo = sbase;
+  w.s_hi = sbase + (uint32_t)kSweepSmem;
+#endif
   if (cw == 4) {
     const uint32_t l4 = wlo & ~3u;
     w.wb = sbase - l4;
@@ -72,6 +81,10 @@ __device__ __forceinline__ Win make_win(int cw, uint32_t wlo, uint32_t whi, uint
   } else {
     w.wb = sbase - wlo * 8u;
     w.words = 2u * (whi - wlo);
+  }
+  if (!DBBC_CHECK(wlo <= whi && w.words <= kSweepWords)) {  // checked builds: count nothing in it
+    w.h = 0u;
+    w.words = 0u;
   }
   return w;
 }
@@ -105,9 +118,19 @@ __device__ __forceinline__ uint64_t atom_if_u64(uint32_t x, uint32_t h, uint32_t
 // counter's old value gives the Lemma 1 contribution: rotated so that the
 // wedge's own class is in the low half, it is summed into a_lo (own + other
 // << 16, mod 2^32) and a_hi (other); the 64-bit width adds to bal / unb.
+// Checked builds skip an entry below the window or whose counter address
+// leaves the buffer.
 template <int CW, bool RET>
-__device__ __forceinline__ void lean_add(uint32_t x, uint32_t h, uint32_t s1, uint32_t wb, uint32_t& a_lo,
+__device__ __forceinline__ void lean_add(uint32_t x, uint32_t h, uint32_t s1, const Win& w, uint32_t& a_lo,
                                          uint32_t& a_hi, uint64_t& bal, uint64_t& unb) {
+  const uint32_t wb = w.wb;
+#if DBBC_CHECKED
+  if (x < h) {
+    const uint32_t addr = CW == 4 ? wb + ((x >> 1) & ~3u) : CW == 8 ? wb + (x & ~3u)
+                        : CW == 16 ? wb + ((x >> 1) << 2) : wb + ((x >> 1) << 3);
+    if (!DBBC_CHECK(x >= w.l && addr >= w.s_lo && addr + (CW == 32 ? 8u : 4u) <= w.s_hi)) h = 0u;
+  }
+#endif
   if constexpr (CW == 4) {
     // nibble (2 * (rank & 3) + asym) of the word: byte k = (asym_k << 4) | sym_k
     const uint32_t sel = (x ^ s1) & 7u;
@@ -197,7 +220,7 @@ __device__ __forceinline__ uint32_t lean_walk(const uint32_t* __restrict__ col, 
     const uint32_t cn = c + (uint32_t)(G * kLU);
     lean_load<G>(col, cn, cont ? en : cn, gl, y);  // the next chunk, while this one is counted
 #pragma unroll
-    for (int u = 0; u < kLU; u++) lean_add<CW, RET>(x[u], h, s1, w.wb, a_lo, a_hi, bal, unb);
+    for (int u = 0; u < kLU; u++) lean_add<CW, RET>(x[u], h, s1, w, a_lo, a_hi, bal, unb);
     if (!__any_sync(kFullMask, cont)) break;
     if (cont) {
       c = cn;
@@ -235,10 +258,8 @@ __device__ __forceinline__ uint32_t lean_walk(const uint32_t* __restrict__ col, 
 // same slots in per-window lists.
 __device__ __forceinline__ void lean_cursor_start(const CsrView& g, const PivotGeom& q, uint32_t i, uint32_t lo_rank,
                                                   uint32_t& b_out, uint32_t& en_out, uint32_t& s1_out) {
-  const uint32_t e = g.col[q.rb + i];
-  const int64_t vrow = q.base + (e >> 1);
-  int64_t b = g.row_ptr[vrow];
-  const int64_t en = g.row_ptr[vrow + 1];
+  int64_t b, en;
+  s1_out = neighbour_row(g, q, g.col[q.rb + i], b, en);
   const uint32_t first = lo_rank << 1;
   if (first) {  // lower_bound of `first` in the row
     int64_t lo = b, hi = en;
@@ -250,7 +271,6 @@ __device__ __forceinline__ void lean_cursor_start(const CsrView& g, const PivotG
   }
   b_out = (uint32_t)b;
   en_out = (uint32_t)en;
-  s1_out = e & 1u;
 }
 
 __device__ __forceinline__ uint2 lean_slot(uint32_t c, uint32_t en, uint32_t s1) {
@@ -273,6 +293,7 @@ struct ListState {
   int cnt[kListMaxWindows];    // list lengths
   int ocnt;                    // overflow list length
   uint32_t L;
+  uint32_t nwin;               // windows (lists) of the span
   ItemWindows iw;              // the item's windows
   uint32_t s0;                 // first window of the span
   uint32_t hl;                 // (last rank of the span + 1) << 1
@@ -285,11 +306,12 @@ __device__ __forceinline__ void list_queue(ListState& ls, uint32_t x, uint32_t c
   const uint2 slot = lean_slot(c, en, s1);
   if (x < ls.hl) {
     const uint32_t r = ls.iw.index_of(x >> 1) - ls.s0;
+    if (!DBBC_CHECK(r < ls.nwin)) return;
     const int pos = atomicAdd(&ls.cnt[r], 1);
-    ls.lists[(size_t)r * ls.L + (uint32_t)pos] = slot;
+    if (DBBC_CHECK((uint32_t)pos < ls.L)) ls.lists[(size_t)r * ls.L + (uint32_t)pos] = slot;
   } else if (x < ls.item_hl) {
     const int pos = atomicAdd(&ls.ocnt, 1);
-    ls.over[pos] = slot;
+    if (DBBC_CHECK((uint32_t)pos < ls.L)) ls.over[pos] = slot;
   }
 }
 
@@ -533,6 +555,11 @@ __device__ __forceinline__ uint64_t sweep_list_item(const CsrView& g, const Swee
   const uint32_t Rsub = (uint32_t)(per_nb - 2 < kListMaxWindows ? per_nb - 2 : kListMaxWindows);
   uint64_t visits = 0;
   int in_buf = 0;  // the overflow list that feeds the next span
+  // entries of list r (checked builds: at most its L slots)
+  auto listed = [&](uint32_t r) {
+    const uint32_t n = (uint32_t)ls.cnt[r];
+    return DBBC_CHECK(n <= q.L) ? n : q.L;
+  };
   for (uint32_t s0 = 0; s0 < R; s0 += Rsub) {
     const uint32_t nwin = min(Rsub, R - s0);
     uint32_t span_lo, span_hi, wlo, whi;
@@ -540,13 +567,15 @@ __device__ __forceinline__ uint64_t sweep_list_item(const CsrView& g, const Swee
     iw.window(s0, span_lo, whi, cw);
     iw.window(s0 + nwin - 1, wlo, span_hi, cw);
     uint2* over_in = lists + (size_t)(Rsub + in_buf) * q.L;
-    const uint32_t n_in = s0 == 0 ? 0u : (uint32_t)ls.ocnt;  // final since the last barrier of the previous span
+    uint32_t n_in = s0 == 0 ? 0u : (uint32_t)ls.ocnt;  // final since the last barrier of the previous span
+    if (!DBBC_CHECK(n_in <= q.L)) n_in = q.L;
     __syncthreads();  // every thread has read ls.ocnt
     if (tid == 0) {
       ls.lists = lists;
       ls.over = lists + (size_t)(Rsub + (in_buf ^ 1)) * q.L;
       ls.ocnt = 0;
       ls.L = q.L;
+      ls.nwin = nwin;
       ls.iw = iw;
       ls.s0 = s0;
       ls.hl = span_hi << 1;
@@ -564,22 +593,22 @@ __device__ __forceinline__ uint64_t sweep_list_item(const CsrView& g, const Swee
       for (uint32_t j = tid; j < n_in; j += kSweepThreads) {
         const uint2 e = over_in[j];
         const uint32_t c = e.x, en = e.x + (e.y & 0x7FFFFFFFu);
-        list_queue(ls, g.col[c], c, en, e.y >> 31);
+        if (DBBC_CHECK(c < en && (int64_t)en <= g.nnz)) list_queue(ls, g.col[c], c, en, e.y >> 31);
       }
     }
     __syncthreads();
     LaneBatch b;
-    batch_fetch<G>(g.col, lists, (uint32_t)ls.cnt[0], &nbn[0], b);
+    batch_fetch<G>(g.col, lists, listed(0), &nbn[0], b);
     for (uint32_t r = 0; r < nwin; r++) {
       iw.window(s0 + r, wlo, whi, cw);
       const Win w = make_win(cw, wlo, whi, sbase);
-      const uint32_t n = (uint32_t)ls.cnt[r];
+      const uint32_t n = listed(r);
       window_walk_dispatch<G, true>(cw, fin, g.col, b, lists + (size_t)r * q.L, n, &nbn[r & 1], nullptr, &ls, w,
                                     bal, unb);
       visits += tid == 0 ? n : 0;
       __syncthreads();  // also publishes the appends to later windows' lists
       if (r + 1 < nwin)
-        batch_fetch<G>(g.col, lists + (size_t)(r + 1) * q.L, (uint32_t)ls.cnt[r + 1], &nbn[(r + 1) & 1], b);
+        batch_fetch<G>(g.col, lists + (size_t)(r + 1) * q.L, listed(r + 1), &nbn[(r + 1) & 1], b);
       window_clear(cw, fin, cnt_words, w.words, bal, unb);
       if (tid == 0) nbn[r & 1] = 0u;
       __syncthreads();

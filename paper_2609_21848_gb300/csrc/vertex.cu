@@ -22,6 +22,7 @@ struct TipOut {
   unsigned long long* vu = nullptr;
   unsigned long long* eb = nullptr;  // [nnz] per CSR position (edge counts)
   unsigned long long* eu = nullptr;
+  int64_t n = 0, nnz = 0;            // their lengths
 };
 
 // Counter of endpoint w in a shared hash table (the key must be present).
@@ -58,6 +59,15 @@ __device__ __forceinline__ void add_pair(unsigned long long* b, unsigned long lo
   if (y) atomicAdd(&u[i], (unsigned long long)y);
 }
 
+// Per-row (vertex) and per-CSR-position (edge) sums; checked builds test the
+// position first.
+__device__ __forceinline__ void add_vertex(const TipOut& o, int64_t r, uint64_t x, uint64_t y) {
+  if (DBBC_CHECK(r >= 0 && r < o.n)) add_pair(o.vb, o.vu, r, x, y);
+}
+__device__ __forceinline__ void add_edge(const TipOut& o, int64_t j, uint64_t x, uint64_t y) {
+  if (DBBC_CHECK(j >= 0 && j < o.nnz)) add_pair(o.eb, o.eu, j, x, y);
+}
+
 // The second walk over a pivot's wedges (lower-neighbour positions [a, b),
 // `step` apart in groups of 32 per warp): each lane credits the far edge
 // (v, w) of its wedge; the warp sums v's wedges and one lane credits the
@@ -89,7 +99,7 @@ __device__ __forceinline__ void warp_second_walk(const CsrView& g, const PivotGe
         if (ok) {
           uint64_t cb, cu;
           wedge_pairs(lookup(x >> 1), ((x ^ s1) & 1u) == 0, cb, cu);
-          if (EDGE) add_pair(o.eb, o.eu, j, cb, cu);
+          if (EDGE) add_edge(o, j, cb, cu);
           sb += cb;
           su += cu;
         }
@@ -98,8 +108,8 @@ __device__ __forceinline__ void warp_second_walk(const CsrView& g, const PivotGe
       sb = warp_sum_u64(sb);
       su = warp_sum_u64(su);
       if (lane == 0) {
-        if (VERT) add_pair(o.vb, o.vu, q.base + (ek >> 1), sb, su);
-        if (EDGE) add_pair(o.eb, o.eu, q.rb + i0 + k, sb, su);
+        if (VERT) add_vertex(o, q.base + (ek >> 1), sb, su);
+        if (EDGE) add_edge(o, q.rb + i0 + k, sb, su);
       }
     }
   }
@@ -143,14 +153,14 @@ __global__ void __launch_bounds__(kLightWarps * 32) tips_light_kernel(CsrView g,
         if (keys[i] != kEmptyKey) {
           uint64_t eb = 0, eu = 0;
           endpoint_contrib(vals[i], eb, eu);
-          add_pair(o.vb, o.vu, end_base + keys[i], eb, eu);
+          add_vertex(o, end_base + keys[i], eb, eu);
           pb += eb;
           pu += eu;
         }
       }
       pb = warp_sum_u64(pb);
       pu = warp_sum_u64(pu);
-      if (lane == 0) add_pair(o.vb, o.vu, p, pb, pu);
+      if (lane == 0) add_vertex(o, p, pb, pu);
     }
     warp_second_walk<VERT, EDGE>(g, q, 0, q.L, 32, [&](uint32_t x) { return hash_find(keys, vals, log_h, x); }, o);
     __syncwarp();
@@ -199,14 +209,14 @@ __global__ void __launch_bounds__(kMediumThreads) tips_medium_kernel(CsrView g, 
         if (keys[i] != kEmptyKey) {
           uint64_t eb = 0, eu = 0;
           endpoint_contrib(vals[i], eb, eu);
-          add_pair(o.vb, o.vu, end_base + keys[i], eb, eu);
+          add_vertex(o, end_base + keys[i], eb, eu);
           pb += eb;
           pu += eu;
         }
       }
       pb = warp_sum_u64(pb);
       pu = warp_sum_u64(pu);
-      if (lane_id() == 0) add_pair(o.vb, o.vu, p, pb, pu);
+      if (lane_id() == 0) add_vertex(o, p, pb, pu);
     }
     warp_second_walk<VERT, EDGE>(g, q, (uint32_t)w * 32u, q.L, kMediumWarps * 32u,
                                  [&](uint32_t x) { return hash_find(keys, vals, log_h, x); }, o);
@@ -272,7 +282,7 @@ __device__ __forceinline__ void tips_window(const CsrView& g, const PivotGeom& q
       if (v) {
         uint64_t eb = 0, eu = 0;
         endpoint_contrib(v, eb, eu);
-        add_pair(o.vb, o.vu, end_base + lo + k, eb, eu);
+        add_vertex(o, end_base + lo + k, eb, eu);
         pb += eb;
         pu += eu;
       }
@@ -291,7 +301,7 @@ __device__ __forceinline__ void tips_window(const CsrView& g, const PivotGeom& q
         const uint32_t xx = col[pos];
         uint64_t cb, cu;
         wedge_pairs(window_value<CW>(c16, c32, (xx - lo2) >> 1), ((xx ^ s1) & 1u) == 0, cb, cu);
-        if (EDGE) add_pair(o.eb, o.eu, pos, cb, cu);
+        if (EDGE) add_edge(o, pos, cb, cu);
         sb += cb;
         su += cu;
       }
@@ -302,8 +312,8 @@ __device__ __forceinline__ void tips_window(const CsrView& g, const PivotGeom& q
       su += __shfl_xor_sync(kFullMask, su, off);
     }
     if (active && gl == 0) {
-      if (VERT) add_pair(o.vb, o.vu, q.base + (e >> 1), sb, su);
-      if (EDGE) add_pair(o.eb, o.eu, q.rb + i, sb, su);
+      if (VERT) add_vertex(o, q.base + (e >> 1), sb, su);
+      if (EDGE) add_edge(o, q.rb + i, sb, su);
     }
   }
   __syncthreads();
@@ -346,7 +356,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1) tips_sweep_kernel(CsrView g,
     __syncthreads();
     if (it >= n_items) break;
     const SweepItem item = items[it];
-    const PivotGeom q = pivot_geom(g, item.row);
+    PivotGeom q = pivot_geom(g, item.row);
+    if (!DBBC_CHECK((int64_t)q.L <= cur_cap)) q.L = 0;  // checked builds: cursor capacity
     const ItemWindows iw(item, false);  // this sweep has no 4-bit counters
     for (uint32_t i = tid; i < q.L; i += kSweepThreads) {
       uint32_t b, en;
@@ -374,7 +385,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) tips_sweep_kernel(CsrView g,
         uint64_t x = tid < kSweepThreads / 32 ? red[0][tid] : 0, y = tid < kSweepThreads / 32 ? red[1][tid] : 0;
         x = warp_sum_u64(x);
         y = warp_sum_u64(y);
-        if (tid == 0) add_pair(o.vb, o.vu, item.row, x, y);
+        if (tid == 0) add_vertex(o, item.row, x, y);
       }
       __syncthreads();
     }
@@ -434,7 +445,7 @@ __global__ void edge_query_kernel(CsrView g, const int32_t* __restrict__ row_of,
 template <bool VERT, bool EDGE>
 void enqueue_tips(const dbbc_graph* g, cudaStream_t s, const TipOut& o, unsigned* d_status, Scratch& sc) {
   if (g->n_piv == 0) return;
-  const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
+  const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n, g->nnz};
   const int sms = num_sms();
   if (g->n_light > 0) {
     auto fn = tips_light_kernel<VERT, EDGE>;
@@ -492,6 +503,7 @@ extern "C" dbbc_status dbbc_count_vertices(const dbbc_graph* g, void* cuda_strea
     TipOut o;
     o.vb = rows;
     o.vu = rows + n;
+    o.n = n;
     enqueue_tips<true, false>(g, s, o, d_status, sc);
     unsigned long long* ob = rows + 2 * n;
     unsigned long long* ou = rows + 3 * n;
@@ -502,7 +514,7 @@ extern "C" dbbc_status dbbc_count_vertices(const dbbc_graph* g, void* cuda_strea
     unsigned h = 0;
     DBBC_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
     DBBC_CUDA(cudaStreamSynchronize(s));
-    if (h) return DBBC_EINTERNAL;
+    raise_device_status(h);
   } catch (const Error& e) {
     return e.status;
   } catch (...) {
@@ -530,6 +542,7 @@ extern "C" dbbc_status dbbc_count_edges(const dbbc_graph* g, void* cuda_stream, 
     TipOut o;
     o.eb = acc;
     o.eu = acc + nnz;
+    o.nnz = nnz;
     enqueue_tips<false, true>(g, s, o, d_status, sc);
     row_of_id_kernel<<<grid_1d(n), 256, 0, s>>>(g->vertex, n, row_of);
     DBBC_LAUNCH_CHECK();
@@ -546,7 +559,7 @@ extern "C" dbbc_status dbbc_count_edges(const dbbc_graph* g, void* cuda_stream, 
       ob = sc.get<unsigned long long>((size_t)(2 * k));
       ou = ob + k;
     }
-    const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n};
+    const CsrView view{g->row_ptr, g->col, g->lower, g->n_u, g->n, g->nnz};
     edge_query_kernel<<<grid_1d(k), 256, 0, s>>>(view, row_of, dqu, dqv, k, o.eb, o.eu, ob, ou, d_status + 1);
     DBBC_LAUNCH_CHECK();
     if (!on_device) {
@@ -557,7 +570,7 @@ extern "C" dbbc_status dbbc_count_edges(const dbbc_graph* g, void* cuda_stream, 
     DBBC_CUDA(cudaMemcpyAsync(h, d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
     DBBC_CUDA(cudaStreamSynchronize(s));
     if (h[1]) return DBBC_EINVAL;
-    if (h[0]) return DBBC_EINTERNAL;
+    raise_device_status(h[0]);
   } catch (const Error& e) {
     return e.status;
   } catch (...) {

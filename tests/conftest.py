@@ -24,3 +24,16 @@ def read_golden(name):
             key, *vals = line.split()
             out.setdefault(key, []).append([int(x) if x.lstrip("-").isdigit() else x for x in vals])
     return out
+
+
+def pytest_runtest_teardown(item, nextitem):
+    """Under the bounds-checked library (the library built with
+    -DDBBC_CHECKED=1, loaded through DBBC_LIBRARY), every GPU test must also
+    leave no bounds violation recorded by any kernel it ran."""
+    if item.get_closest_marker("gpu") is None:
+        return
+    mod = sys.modules.get("paper_2609_21848_gb300")
+    if mod is None or getattr(mod, "_lib", None) is None or not mod.dbbc_is_checked():
+        return
+    flags = mod.dbbc_checked_flags()
+    assert flags == 0, f"{item.nodeid}: a kernel recorded bounds violations (flags {flags:#x})"

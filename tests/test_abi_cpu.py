@@ -144,3 +144,21 @@ def test_timeout_status_is_reserved():
     text = open(HEADER).read()
     assert "reserved" in text.split("DBBC_ETIMEOUT = 4,", 1)[1].split("\n", 1)[0]
     assert dbbc.dbbc_status_string(4) == "bounded device wait gave up"
+
+
+def test_regular_build_is_not_checked(lib):
+    """The regular library checks no index in its kernels, reports so, and
+    its check-flag query needs no GPU (it returns 0 without synchronizing)."""
+    if dbbc.dbbc_is_checked():
+        pytest.skip("DBBC_LIBRARY names the checked build")
+    assert lib.dbbc_is_checked() == 0
+    assert dbbc.dbbc_checked_flags() == 0
+    assert lib.dbbc_checked_flags(None) == dbbc.DBBC_EINVAL
+
+
+def test_checked_build_flags_are_separate():
+    """The checked build goes to its own folder with its own flag stamp, so it
+    never replaces the regular library."""
+    assert os.path.dirname(os.path.join(buildlib.CHECKED_DIR, "libdbbc.so")) != os.path.dirname(buildlib.LIB)
+    assert buildlib.CHECKED_FLAGS == ["-DDBBC_CHECKED=1"]
+    assert not buildlib.up_to_date(buildlib.LIB, buildlib.CHECKED_FLAGS)
