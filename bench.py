@@ -112,7 +112,7 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-KERNEL_SOURCES = ("count.cu", "count_device.cuh", "internal.h", "common.cuh")
+KERNEL_SOURCES = ("count.cu", "sweep_device.cuh", "count_device.cuh", "internal.h", "common.cuh")
 
 
 def kernel_source_sha() -> str:

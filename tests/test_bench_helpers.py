@@ -33,9 +33,14 @@ def test_traffic_record_is_keyed_by_the_kernel_sources():
 
 
 def test_measured_peaks_are_used():
+    """The peak file written for this machine pool is used when present;
+    without it the bench falls back to the earlier GB300 measurement and says so."""
     b = load_bench()
     peaks, kind = b.measured_peaks()
-    assert kind == "measured" and float(peaks["hbm_gbs"]) > 1000
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert kind == "measured" and float(peaks["hbm_gbs"]) > 1000
+    else:
+        assert kind == "fallback" and peaks["hbm_gbs"] == 6800.0
 
 
 def test_default_arguments_keep_the_contract(monkeypatch):
