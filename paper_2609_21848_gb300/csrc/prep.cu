@@ -150,33 +150,59 @@ __global__ void ranks_kernel(const uint64_t* __restrict__ skey, int64_t n, int32
   }
 }
 
-// Two CSR entries per edge: key = (row << (bits_col + 1)) | (col << 1) | negative.
-__global__ void csr_keys_kernel(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-                                const int8_t* __restrict__ es, int64_t m, int32_t n_u,
-                                const int32_t* __restrict__ side_rank, int bits_col, uint64_t* __restrict__ key) {
+// CSR keys in two sorts. The U rows are the edges sorted by
+// ku = (U rank << (bits_v + 1)) | (V rank << 1) | negative; the V rows are the
+// same list re-sorted stably by V rank alone, as
+// kv = (V rank << (bits_u + 1)) | (U rank << 1) | negative, which keeps every
+// V row ascending by U rank.
+__global__ void csr_u_keys_kernel(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                                  const int8_t* __restrict__ es, int64_t m, int32_t n_u,
+                                  const int32_t* __restrict__ side_rank, int bits_v, uint64_t* __restrict__ ku) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t ru = (uint32_t)side_rank[eu[i]];
     const uint64_t rv = (uint32_t)side_rank[n_u + ev[i]];
-    const uint64_t neg = es[i] < 0 ? 1 : 0;
-    key[2 * i] = (ru << (bits_col + 1)) | (rv << 1) | neg;
-    key[2 * i + 1] = (((uint64_t)n_u + rv) << (bits_col + 1)) | (ru << 1) | neg;
+    ku[i] = (ru << (bits_v + 1)) | (rv << 1) | (es[i] < 0 ? 1u : 0u);
   }
 }
 
-// Flags a repeated (row, neighbour) pair: sorted CSR keys that agree in
-// everything but the sign bit are adjacent.
-__global__ void adjacent_dup_kernel(const uint64_t* __restrict__ key, int64_t nnz, unsigned* dup) {
+__global__ void csr_v_keys_kernel(const uint64_t* __restrict__ ku, int64_t m, int bits_u, int bits_v,
+                                  uint64_t* __restrict__ kv) {
+  const uint64_t mask_v = (1ull << bits_v) - 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = ku[i];
+    const uint64_t ru = k >> (bits_v + 1), rv = (k >> 1) & mask_v;
+    kv[i] = (rv << (bits_u + 1)) | (ru << 1) | (k & 1u);
+  }
+}
+
+// Flags a repeated (u, v) pair: U-sorted keys that agree in everything but the
+// sign bit are adjacent.
+__global__ void adjacent_dup_kernel(const uint64_t* __restrict__ key, int64_t m, unsigned* dup) {
   bool any = false;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < nnz; i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < m; i += (int64_t)gridDim.x * blockDim.x)
     any |= (key[i] >> 1) == (key[i + 1] >> 1);
   if (__any_sync(kFullMask, any) && lane_id() == 0) atomicOr(dup, 1u);
 }
 
-__global__ void csr_cols_kernel(const uint64_t* __restrict__ key, int64_t nnz, int bits_col,
-                                uint32_t* __restrict__ col) {
-  const uint64_t mask = (1ull << (bits_col + 1)) - 1;
+// Row and entry of CSR position i: the first m positions are the U rows, the
+// next m the V rows.
+struct CsrKeys {
+  const uint64_t* ku;
+  const uint64_t* kv;
+  int64_t m;
+  int32_t n_u;
+  int bits_u, bits_v;
+  __device__ __forceinline__ int64_t row(int64_t i) const {
+    return i < m ? (int64_t)(ku[i] >> (bits_v + 1)) : (int64_t)n_u + (int64_t)(kv[i - m] >> (bits_u + 1));
+  }
+  __device__ __forceinline__ uint32_t entry(int64_t i) const {
+    return i < m ? (uint32_t)(ku[i] & ((2ull << bits_v) - 1)) : (uint32_t)(kv[i - m] & ((2ull << bits_u) - 1));
+  }
+};
+
+__global__ void csr_cols_kernel(CsrKeys ck, int64_t nnz, uint32_t* __restrict__ col) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
-    col[i] = (uint32_t)(key[i] & mask);
+    col[i] = ck.entry(i);
 }
 
 // lower[r] = neighbours of row r with lower Def. 3 priority. A U vertex of
@@ -208,9 +234,9 @@ __global__ void lower_kernel(const int64_t* __restrict__ row_ptr, const uint32_t
 // work[p] = sum over lower neighbours v of p of |{w in row(v) : rank(w) < rank(p)}|,
 // i.e. the wedges Algorithm 1 accepts at pivot p. One thread per CSR entry;
 // entries of a row are contiguous, so a segmented warp sum merges them.
-__global__ void work_kernel(const uint64_t* __restrict__ key, const int64_t* __restrict__ row_ptr,
-                            const uint32_t* __restrict__ col, const uint32_t* __restrict__ lower, int64_t nnz,
-                            int32_t n_u, int bits_col, unsigned long long* __restrict__ work) {
+__global__ void work_kernel(CsrKeys ck, const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                            const uint32_t* __restrict__ lower, int64_t nnz, int32_t n_u,
+                            unsigned long long* __restrict__ work) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t iters = (nnz + stride - 1) / stride;
   const unsigned lane = lane_id();
@@ -219,7 +245,7 @@ __global__ void work_kernel(const uint64_t* __restrict__ key, const int64_t* __r
     int64_t r = -1;
     uint64_t acc = 0;
     if (i < nnz) {
-      r = (int64_t)(key[i] >> (bits_col + 1));
+      r = ck.row(i);
       if ((uint64_t)(i - row_ptr[r]) < lower[r]) {
         const uint32_t e = col[i];
         const bool is_u = r < n_u;
@@ -675,15 +701,10 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
   const int bits_u = bits_for(n_u > 0 ? (uint64_t)(n_u - 1) : 0);
   const int bits_v = bits_for(n_v > 0 ? (uint64_t)(n_v - 1) : 0);
   // rank keys: (side, component, degree, id within the component)
-  const int64_t max_side = std::max<int64_t>(n_u, n_v);
   const int bits_comp = un->n_graphs > 1 ? bits_for((uint64_t)(un->n_graphs - 1)) : 0;
   const int bits_lid = std::max(1, bits_for(un->max_side > 0 ? (uint64_t)(un->max_side - 1) : 0));
   const int bits_deg = std::max(1, bits_for((uint64_t)un->max_side));
   if (1 + bits_comp + bits_deg + bits_lid > 64) throw Error{DBBC_EINVAL, "union too large for 64-bit rank keys"};
-  const int bits_id = std::max(1, bits_for(max_side > 0 ? (uint64_t)(max_side - 1) : 0));
-  const int bits_col = bits_id;
-  const int bits_row = std::max(1, bits_for(n > 0 ? (uint64_t)(n - 1) : 0));
-  if (bits_row + bits_col + 1 > 64) throw Error{DBBC_EINVAL, "graph too large for 64-bit CSR keys"};
   int32_t* deg = sc.get<int32_t>((size_t)n);
   int32_t* side_rank = sc.get<int32_t>((size_t)n);
   int32_t* rowdeg = sc.get<int32_t>((size_t)n);
@@ -694,11 +715,12 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
   g->vertex = static_cast<int32_t*>(graph_alloc(g, (size_t)n * 4));
   g->row_ptr = static_cast<int64_t*>(graph_alloc(g, (size_t)(n + 1) * 8));
 
-  // a2 + a3 for an edge list: degrees, Def. 3 ranks per side, CSR keys
-  // sorted by (row, neighbour priority) with the sign in bit 0. Returns the
-  // sorted keys and whether any (u, v) pair occurs twice (adjacent keys).
+  // a2 + a3 for an edge list: degrees, Def. 3 ranks per side, and the CSR
+  // keys of both sides (CsrKeys: U rows sorted by (U rank, V rank), V rows
+  // by (V rank, U rank)) with the sign in bit 0. Returns the keys and whether
+  // any (u, v) pair occurs twice (adjacent U keys).
   auto csr_from_edges = [&](const int32_t* eu, const int32_t* ev, const int8_t* es, int64_t me,
-                            bool* dup) -> uint64_t* {
+                            bool* dup) -> CsrKeys {
     DBBC_CUDA(cudaMemsetAsync(deg, 0, (size_t)n * 4, s));
     if (me > 0) {
       degree_kernel<<<grid_for(me), 256, 0, s>>>(eu, ev, me, n_u, deg);
@@ -716,18 +738,25 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
       DBBC_LAUNCH_CHECK();
     }
     *dup = false;
-    if (me == 0) return ck0;
-    csr_keys_kernel<<<grid_for(me), 256, 0, s>>>(eu, ev, es, me, n_u, side_rank, bits_col, ck0);
+    CsrKeys k{ck0, ck0 + me, me, n_u, bits_u, bits_v};
+    if (me == 0) return k;
+    // the halves of ck0 / ck1 hold the U keys and the V keys; the sorts skip
+    // bit 0 (the sign), so repeated pairs stay in input order
+    csr_u_keys_kernel<<<grid_for(me), 256, 0, s>>>(eu, ev, es, me, n_u, side_rank, bits_v, ck0);
     DBBC_LAUNCH_CHECK();
-    // the sort skips bit 0 (the sign), so repeated pairs stay in input order
-    const bool alt = radix_sort<uint64_t, uint32_t, false>(ck0, ck1, nullptr, nullptr, 2 * me, 1,
-                                                           bits_row + bits_col + 1, s, sc);
-    uint64_t* ck = alt ? ck1 : ck0;
+    const bool alt_u = radix_sort<uint64_t, uint32_t, false>(ck0, ck1, nullptr, nullptr, me, 1, 1 + bits_v + bits_u,
+                                                             s, sc);
+    k.ku = alt_u ? ck1 : ck0;
     DBBC_CUDA(cudaMemsetAsync(d_flags + 3, 0, sizeof(unsigned), s));
-    adjacent_dup_kernel<<<grid_for(2 * me), 256, 0, s>>>(ck, 2 * me, d_flags + 3);
+    adjacent_dup_kernel<<<grid_for(me), 256, 0, s>>>(k.ku, me, d_flags + 3);
     DBBC_LAUNCH_CHECK();
+    csr_v_keys_kernel<<<grid_for(me), 256, 0, s>>>(k.ku, me, bits_u, bits_v, ck0 + me);
+    DBBC_LAUNCH_CHECK();
+    const bool alt_v = radix_sort<uint64_t, uint32_t, false>(ck0 + me, ck1 + me, nullptr, nullptr, me, 1 + bits_u,
+                                                             1 + bits_u + bits_v, s, sc);
+    k.kv = alt_v ? ck1 + me : ck0 + me;
     *dup = read_back(d_flags + 3, s) != 0;
-    return ck;
+    return k;
   };
 
   // ---- a1-a3: build straight from the input; only when some (u, v) pair
@@ -735,7 +764,7 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
   // the last of every run) and build again from the distinct edges.
   bool dup = false;
   int64_t mu = m;
-  uint64_t* ck = csr_from_edges(du, dv, ds, m, &dup);
+  CsrKeys ck = csr_from_edges(du, dv, ds, m, &dup);
   if (dup) {
     if (reject_duplicates) throw Error{DBBC_EINVAL, "duplicate edge under DBBC_DUP_REJECT"};
     uint64_t* k0 = ck0;  // reuse the CSR key buffers (2m entries each) for the (u, v) sort
@@ -769,7 +798,7 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
   exclusive_scan<int32_t, int64_t>(rowdeg, g->row_ptr, n, s, sc, g->row_ptr + n);
   DBBC_CUDA(cudaMemsetAsync(g->work, 0, (size_t)n * 8, s));
   if (g->nnz > 0) {
-    csr_cols_kernel<<<grid_for(g->nnz), 256, 0, s>>>(ck, g->nnz, bits_col, g->col);
+    csr_cols_kernel<<<grid_for(g->nnz), 256, 0, s>>>(ck, g->nnz, g->col);
     DBBC_LAUNCH_CHECK();
   }
   if (n > 0) {
@@ -779,7 +808,7 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
 
   // ---- a4: accepted wedges per pivot and the counting tiers
   if (g->nnz > 0) {
-    work_kernel<<<grid_for(g->nnz), 256, 0, s>>>(ck, g->row_ptr, g->col, g->lower, g->nnz, n_u, bits_col,
+    work_kernel<<<grid_for(g->nnz), 256, 0, s>>>(ck, g->row_ptr, g->col, g->lower, g->nnz, n_u,
                                                  reinterpret_cast<unsigned long long*>(g->work));
     DBBC_LAUNCH_CHECK();
   }
