@@ -174,19 +174,32 @@ __global__ void __launch_bounds__(kMediumThreads) count_medium_batch_kernel(cons
 }
 
 // Hub sweep over all graphs' hub items (see hub_sweep_kernel); sums are
-// flushed per item.
-__global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const GraphDesc* __restrict__ desc,
-                                                                        const BatchHubItem* __restrict__ items,
-                                                                        int64_t n_items, int* next_item,
-                                                                        uint2* __restrict__ cursors, int64_t cur_cap,
-                                                                        unsigned long long* out) {
+// flushed per item. Two shapes: wide CTAs (kSweepThreads threads, the full
+// window) for large items, and narrow ones (kNarrowThreads threads, a window
+// of kNarrowWords words, several CTAs per SM) for the many small items of
+// small graphs, whose per-item barriers, cursor set-up and sums would
+// otherwise occupy a whole SM each.
+constexpr int kNarrowThreads = 256;
+constexpr uint32_t kNarrowWords = 13312 + 4;
+constexpr size_t kNarrowSmem = (size_t)kNarrowWords * 4;
+static_assert(kNarrowWords % 4 == 0, "window buffers are cleared 16 bytes at a time");
+// items above this many estimated wedges stay on wide CTAs (a long item on a
+// narrow CTA would finish last)
+constexpr uint64_t kNarrowItemWork = 1u << 20;
+
+template <int THREADS, uint32_t WORDS>
+__global__ void __launch_bounds__(THREADS) hub_sweep_batch_kernel(const GraphDesc* __restrict__ desc,
+                                                                  const BatchHubItem* __restrict__ items,
+                                                                  int64_t n_items, int* next_item,
+                                                                  uint2* __restrict__ cursors, int64_t cur_cap,
+                                                                  unsigned long long* out) {
   extern __shared__ __align__(16) unsigned char sweep_smem[];
   uint32_t* cnt_words = reinterpret_cast<uint32_t*>(sweep_smem);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sweep_smem);
   __shared__ int item_sh;
   __shared__ uint32_t nbn[2];
   const int tid = threadIdx.x;
-  zero_words(cnt_words, kSweepWords);
+  zero_words<THREADS>(cnt_words, WORDS);
   if (tid < 2) nbn[tid] = 0u;
   uint2* cur = cursors + (int64_t)blockIdx.x * cur_cap;
   for (;;) {
@@ -200,17 +213,42 @@ __global__ void __launch_bounds__(kSweepThreads) hub_sweep_batch_kernel(const Gr
     const CsrView g = view_of(desc[bi.graph]);
     const PivotGeom q = pivot_geom(g, item.row);
     const uint32_t L = DBBC_CHECK((int64_t)q.L <= cur_cap) ? q.L : 0u;  // checked builds: cursor capacity
-    for (uint32_t i = tid; i < L; i += kSweepThreads) {
+    for (uint32_t i = tid; i < L; i += THREADS) {
       uint32_t b, en, s1;
       lean_cursor_start(g, q, i, (item.flags & kItemFirst) ? 0u : item.lo, b, en, s1);
       cur[i] = lean_slot(b, en, s1);
     }
     __syncthreads();
     uint64_t bal = 0, unb = 0;
-    sweep_cursor_item_dispatch(item.group_log, g.col, L, cur, ItemWindows(item), (item.flags & kItemFinalize) != 0,
-                               sbase, cnt_words, nbn, bal, unb);
-    block_add_pair<kSweepThreads>(bal, unb, out + 2 * bi.graph);
+    sweep_cursor_item_dispatch<THREADS, WORDS>(item.group_log, g.col, L, cur, ItemWindows(item),
+                                               (item.flags & kItemFinalize) != 0, sbase, cnt_words, nbn, bal, unb);
+    block_add_pair<THREADS>(bal, unb, out + 2 * bi.graph);
   }
+}
+
+#define DBBC_WIDE_SWEEP hub_sweep_batch_kernel<kSweepThreads, kSweepWords>
+#define DBBC_NARROW_SWEEP hub_sweep_batch_kernel<kNarrowThreads, kNarrowWords>
+
+// The largest counter buffer (32-bit words) a window of the item needs, with
+// the windows of ItemWindows: the first window of each counter width is its
+// widest.
+static uint32_t item_window_words(const SweepItem& it) {
+  const uint32_t lo = it.lo, hi = it.hi;
+  const uint32_t qe = std::min(std::max(it.q_end, lo), hi);
+  const uint32_t te = std::min(std::max(it.t_end, qe), hi);
+  const uint32_t ne = std::min(std::max(it.n_end, te), hi);
+  uint32_t w = 0;
+  if (qe > lo) {
+    const uint32_t wh = std::min(lo + window_ranks<4>(), qe);
+    w = std::max(w, (wh - (lo & ~3u) + 3u) >> 2);
+  }
+  if (te > qe) {
+    const uint32_t wh = std::min(qe + window_ranks<8>(), te);
+    w = std::max(w, (wh - (qe & ~1u) + 1u) >> 1);
+  }
+  if (ne > te) w = std::max(w, std::min(te + window_ranks<16>(), ne) - te);
+  if (hi > ne) w = std::max(w, 2u * (std::min(ne + window_ranks<32>(), hi) - ne));
+  return w;
 }
 
 }  // namespace dbbc
@@ -223,13 +261,15 @@ struct dbbc_batch {
   dbbc::GraphDesc* desc = nullptr;
   dbbc::BatchPivot* light = nullptr;
   dbbc::BatchPivot* medium = nullptr;
-  dbbc::BatchHubItem* hub = nullptr;
+  dbbc::BatchHubItem* hub = nullptr;         // items for wide CTAs, then items for narrow ones
   int64_t n_light = 0, n_medium = 0, n_hub_items = 0, max_lower = 1;
+  int64_t n_wide = 0, n_narrow = 0;
   unsigned long long* out = nullptr;  // [n_graphs][2]
-  uint2* cursors = nullptr;
-  int* counters = nullptr;  // [0] light chunks, [1] hub items
+  uint2* cursors = nullptr;         // wide CTAs'
+  uint2* narrow_cursors = nullptr;  // narrow CTAs'
+  int* counters = nullptr;  // [0] light chunks, [1] wide hub items, [2] narrow hub items
   unsigned* status = nullptr;
-  int hub_grid = 0, light_grid = 0, medium_grid = 0;
+  int hub_grid = 0, narrow_grid = 0, light_grid = 0, medium_grid = 0;
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels_per_replay = 0;
   std::vector<void*> allocations;
@@ -253,7 +293,8 @@ static void batch_release(dbbc_batch* b) {
   b->capture = nullptr;
 }
 
-static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector<BatchHubItem>& items);
+static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector<BatchHubItem>& items,
+                        const std::vector<uint64_t>& est);
 
 // Plan for the components of one union handle: every component shares the
 // union's CSR; pivots and hub items are tagged with their component.
@@ -281,7 +322,7 @@ static void plan_components(dbbc_batch* b, const dbbc_graph* g) {
   }
   // the union's items are already in descending estimated work
   for (size_t k = 0; k < nh; k++) items[k] = BatchHubItem{comps[k], 0, g->sweep_items_host[k]};
-  finish_plan(b, desc, items);
+  finish_plan(b, desc, items, g->sweep_est_host);
   if (b->n_medium + b->n_light > 0) {
     const int64_t total = b->n_medium + b->n_light;
     gather_component_pivots_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, s>>>(
@@ -313,8 +354,12 @@ static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
   }
   std::stable_sort(hubs.begin(), hubs.end(), [](const HubRef& a, const HubRef& c) { return a.est > c.est; });
   std::vector<BatchHubItem> items(hubs.size());
-  for (size_t k = 0; k < hubs.size(); k++) items[k] = hubs[k].item;
-  finish_plan(b, desc, items);
+  std::vector<uint64_t> est(hubs.size());
+  for (size_t k = 0; k < hubs.size(); k++) {
+    items[k] = hubs[k].item;
+    est[k] = hubs[k].est;
+  }
+  finish_plan(b, desc, items, est);
   GatherJob* d_jobs = static_cast<GatherJob*>(batch_alloc(b, jobs.size() * sizeof(GatherJob)));
   DBBC_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(GatherJob), cudaMemcpyHostToDevice, s));
   if (n > 0) {
@@ -325,20 +370,42 @@ static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
 }
 
 // Allocations, launch shapes and uploads shared by both kinds of plan.
-static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector<BatchHubItem>& items) {
+static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector<BatchHubItem>& items,
+                        const std::vector<uint64_t>& est) {
   cudaStream_t s = b->stream;
   const int32_t n = b->n_graphs;
+  // wide items first, then the narrow ones, each in their LPT order; an item
+  // goes to a narrow CTA when its windows fit kNarrowWords and its estimated
+  // work (est[k], absent: unknown) is small
+  {
+    std::vector<BatchHubItem> narrow;
+    size_t n_wide = 0;
+    for (size_t k = 0; k < items.size(); k++) {
+      if (k < est.size() && est[k] <= kNarrowItemWork && item_window_words(items[k].it) <= kNarrowWords)
+        narrow.push_back(items[k]);
+      else
+        items[n_wide++] = items[k];
+    }
+    std::copy(narrow.begin(), narrow.end(), items.begin() + (ptrdiff_t)n_wide);
+    b->n_wide = (int64_t)n_wide;
+    b->n_narrow = (int64_t)narrow.size();
+  }
   b->n_hub_items = (int64_t)items.size();
   b->desc = static_cast<GraphDesc*>(batch_alloc(b, desc.size() * sizeof(GraphDesc)));
   b->light = static_cast<BatchPivot*>(batch_alloc(b, (size_t)b->n_light * sizeof(BatchPivot)));
   b->medium = static_cast<BatchPivot*>(batch_alloc(b, (size_t)b->n_medium * sizeof(BatchPivot)));
   b->hub = static_cast<BatchHubItem*>(batch_alloc(b, items.size() * sizeof(BatchHubItem)));
   b->out = static_cast<unsigned long long*>(batch_alloc(b, (size_t)n * 2 * sizeof(unsigned long long)));
-  b->counters = static_cast<int*>(batch_alloc(b, 2 * sizeof(int)));
+  b->counters = static_cast<int*>(batch_alloc(b, 3 * sizeof(int)));
   b->status = static_cast<unsigned*>(batch_alloc(b, sizeof(unsigned)));
-  b->hub_grid = num_sms() * blocks_per_sm((const void*)hub_sweep_batch_kernel, kSweepThreads, kSweepSmem);
-  if (b->n_hub_items > 0)
+  b->hub_grid = (int)std::min<int64_t>(num_sms() * blocks_per_sm((const void*)DBBC_WIDE_SWEEP, kSweepThreads,
+                                                                 kSweepSmem), std::max<int64_t>(b->n_wide, 1));
+  b->narrow_grid = (int)std::min<int64_t>(num_sms() * blocks_per_sm((const void*)DBBC_NARROW_SWEEP, kNarrowThreads,
+                                                                    kNarrowSmem), std::max<int64_t>(b->n_narrow, 1));
+  if (b->n_wide > 0)
     b->cursors = static_cast<uint2*>(batch_alloc(b, (size_t)b->hub_grid * (size_t)b->max_lower * sizeof(uint2)));
+  if (b->n_narrow > 0)
+    b->narrow_cursors = static_cast<uint2*>(batch_alloc(b, (size_t)b->narrow_grid * (size_t)b->max_lower * sizeof(uint2)));
   {
     const int sms = num_sms();
     const int64_t want = ceil_div<int64_t>(ceil_div<int64_t>(b->n_light, 32), kLightWarps);
@@ -358,7 +425,7 @@ static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector
 // The batch count: clear outputs and counters, then the three tiers.
 static void enqueue_batch(dbbc_batch* b, cudaStream_t s) {
   DBBC_CUDA(cudaMemsetAsync(b->out, 0, (size_t)b->n_graphs * 2 * sizeof(unsigned long long), s));
-  DBBC_CUDA(cudaMemsetAsync(b->counters, 0, 2 * sizeof(int), s));
+  DBBC_CUDA(cudaMemsetAsync(b->counters, 0, 3 * sizeof(int), s));
   DBBC_CUDA(cudaMemsetAsync(b->status, 0, sizeof(unsigned), s));
   if (b->n_light > 0) {
     const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
@@ -372,10 +439,14 @@ static void enqueue_batch(dbbc_batch* b, cudaStream_t s) {
                                                                                      b->n_medium, b->out, b->status);
     DBBC_LAUNCH_CHECK();
   }
-  if (b->n_hub_items > 0) {
-    const int grid = (int)std::min<int64_t>(b->hub_grid, b->n_hub_items);
-    hub_sweep_batch_kernel<<<grid, kSweepThreads, kSweepSmem, s>>>(b->desc, b->hub, b->n_hub_items, b->counters + 1,
-                                                             b->cursors, b->max_lower, b->out);
+  if (b->n_wide > 0) {
+    DBBC_WIDE_SWEEP<<<b->hub_grid, kSweepThreads, kSweepSmem, s>>>(b->desc, b->hub, b->n_wide, b->counters + 1,
+                                                                  b->cursors, b->max_lower, b->out);
+    DBBC_LAUNCH_CHECK();
+  }
+  if (b->n_narrow > 0) {
+    DBBC_NARROW_SWEEP<<<b->narrow_grid, kNarrowThreads, kNarrowSmem, s>>>(
+        b->desc, b->hub + b->n_wide, b->n_narrow, b->counters + 2, b->narrow_cursors, b->max_lower, b->out);
     DBBC_LAUNCH_CHECK();
   }
 }
@@ -385,8 +456,8 @@ static void set_batch_attributes() {
                                  (int)((size_t)kLightWarps * kLightSlots * 12)));
   DBBC_CUDA(cudaFuncSetAttribute(count_medium_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)((size_t)kMediumSlots * 12)));
-  DBBC_CUDA(cudaFuncSetAttribute(hub_sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSweepSmem));
+  DBBC_CUDA(cudaFuncSetAttribute(DBBC_WIDE_SWEEP, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem));
+  DBBC_CUDA(cudaFuncSetAttribute(DBBC_NARROW_SWEEP, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNarrowSmem));
 }
 
 static void check_batch_status(const dbbc_batch* b, cudaStream_t s) {
@@ -430,7 +501,7 @@ void count_subset(const dbbc_graph* g, cudaStream_t s, const std::vector<int32_t
     b->max_lower = std::max<int64_t>(1, g->sweep_max_lower);
     std::vector<BatchHubItem> items(hub_items.size());
     for (size_t k = 0; k < hub_items.size(); k++) items[k] = BatchHubItem{0, 0, hub_items[k]};
-    finish_plan(b, desc, items);
+    finish_plan(b, desc, items, {});  // work unknown: every item on wide CTAs
     std::vector<BatchPivot> med(medium_rows.size()), light(light_rows.size());
     for (size_t k = 0; k < medium_rows.size(); k++) med[k] = BatchPivot{0, medium_rows[k]};
     for (size_t k = 0; k < light_rows.size(); k++) light[k] = BatchPivot{0, light_rows[k]};

@@ -224,10 +224,11 @@ static_assert(kSweepWindow16 % 4 == 0, "window buffers are cleared 16 bytes at a
 
 // Clear the first `words` 32-bit words of a window (16 bytes per store; the
 // window buffer holds a multiple of 4 words).
+template <int THREADS = kSweepThreads>
 __device__ __forceinline__ void zero_words(uint32_t* w, uint32_t words) {
   uint4* q = reinterpret_cast<uint4*>(w);
   const uint32_t quads = (words + 3) >> 2;
-  for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) q[j] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t j = threadIdx.x; j < quads; j += THREADS) q[j] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // x[u] = entry at position c + u*G + gl of a row ending at en, or ~0 past it.

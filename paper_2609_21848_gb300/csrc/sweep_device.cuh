@@ -59,13 +59,15 @@ struct Win {
 #endif
 };
 
+// WORDS: the counter buffer's size in 32-bit words.
+template <uint32_t WORDS = kSweepWords>
 __device__ __forceinline__ Win make_win(int cw, uint32_t wlo, uint32_t whi, uint32_t sbase) {
   Win w;
   w.h = whi << 1;
 #if DBBC_CHECKED
   w.l = wlo << 1;
   w.s_lo = sbase;
-  w.s_hi = sbase + (uint32_t)kSweepSmem;
+  w.s_hi = sbase + WORDS * 4u;
 #endif
   if (cw == 4) {
     const uint32_t l4 = wlo & ~3u;
@@ -82,7 +84,7 @@ __device__ __forceinline__ Win make_win(int cw, uint32_t wlo, uint32_t whi, uint
     w.wb = sbase - wlo * 8u;
     w.words = 2u * (whi - wlo);
   }
-  if (!DBBC_CHECK(wlo <= whi && w.words <= kSweepWords)) {  // checked builds: count nothing in it
+  if (!DBBC_CHECK(wlo <= whi && w.words <= WORDS)) {  // checked builds: count nothing in it
     w.h = 0u;
     w.words = 0u;
   }
@@ -389,17 +391,17 @@ __device__ __forceinline__ void window_walk(const uint32_t* __restrict__ col, La
 // Clear the window's `words` counter words for the next window. With FIN,
 // first add every endpoint's Lemma 1 total from its final counter:
 // C(p,2) + C(q,2) balanced and p * q unbalanced butterflies.
-template <int CW, bool FIN>
+template <int CW, bool FIN, int THREADS = kSweepThreads>
 __device__ __forceinline__ void lean_clear(uint32_t* cnt, uint32_t words, uint64_t& bal, uint64_t& unb) {
   uint4* q4 = reinterpret_cast<uint4*>(cnt);
   const uint32_t quads = (words + 3u) >> 2;
   if constexpr (!FIN) {
-    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) q4[j] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t j = threadIdx.x; j < quads; j += THREADS) q4[j] = make_uint4(0u, 0u, 0u, 0u);
   } else if constexpr (CW == 4) {
     // nibbles (q3, p3, ..., q0, p0): the p's and q's as bytes, then byte dot
     // products as for 8-bit counters (per-thread sums stay far below 2^32)
     uint32_t sq = 0, s = 0, pq = 0;
-    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) {
+    for (uint32_t j = threadIdx.x; j < quads; j += THREADS) {
       const uint4 v = q4[j];
       if ((v.x | v.y | v.z | v.w) == 0u) continue;
       const uint32_t a[4] = {v.x, v.y, v.z, v.w};
@@ -419,7 +421,7 @@ __device__ __forceinline__ void lean_clear(uint32_t* cnt, uint32_t words, uint64
     // p * q, by 4-way byte dot products (each per-thread sum < 2^32: at most
     // 60 words of bytes < 256 per window)
     uint32_t sq = 0, s = 0, pq2 = 0;
-    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) {
+    for (uint32_t j = threadIdx.x; j < quads; j += THREADS) {
       const uint4 v = q4[j];
       if ((v.x | v.y | v.z | v.w) == 0u) continue;
       const uint32_t a[4] = {v.x, v.y, v.z, v.w};
@@ -436,7 +438,7 @@ __device__ __forceinline__ void lean_clear(uint32_t* cnt, uint32_t words, uint64
   } else if constexpr (CW == 16) {
     // C(p,2) + C(q,2) = C(p+q,2) - p*q
     uint64_t ss = 0, pq = 0;
-    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) {
+    for (uint32_t j = threadIdx.x; j < quads; j += THREADS) {
       const uint4 v = q4[j];
       if ((v.x | v.y | v.z | v.w) == 0u) continue;
       const uint32_t a[4] = {v.x, v.y, v.z, v.w};
@@ -451,7 +453,7 @@ __device__ __forceinline__ void lean_clear(uint32_t* cnt, uint32_t words, uint64
     bal += (ss >> 1) - pq;
     unb += pq;
   } else {
-    for (uint32_t j = threadIdx.x; j < quads; j += kSweepThreads) {
+    for (uint32_t j = threadIdx.x; j < quads; j += THREADS) {
       const uint4 v = q4[j];
       if ((v.x | v.y | v.z | v.w) == 0u) continue;
       const uint64_t p0 = v.x, q0 = v.y, p1 = v.z, q1 = v.w;
@@ -463,16 +465,21 @@ __device__ __forceinline__ void lean_clear(uint32_t* cnt, uint32_t words, uint64
 }
 
 
+template <int THREADS = kSweepThreads>
 __device__ __forceinline__ void window_clear(int cw, bool fin, uint32_t* cnt, uint32_t words, uint64_t& bal,
                                              uint64_t& unb) {
   if (cw == 4) {
-    if (fin) lean_clear<4, true>(cnt, words, bal, unb); else lean_clear<4, false>(cnt, words, bal, unb);
+    if (fin) lean_clear<4, true, THREADS>(cnt, words, bal, unb);
+    else lean_clear<4, false, THREADS>(cnt, words, bal, unb);
   } else if (cw == 8) {
-    if (fin) lean_clear<8, true>(cnt, words, bal, unb); else lean_clear<8, false>(cnt, words, bal, unb);
+    if (fin) lean_clear<8, true, THREADS>(cnt, words, bal, unb);
+    else lean_clear<8, false, THREADS>(cnt, words, bal, unb);
   } else if (cw == 16) {
-    if (fin) lean_clear<16, true>(cnt, words, bal, unb); else lean_clear<16, false>(cnt, words, bal, unb);
+    if (fin) lean_clear<16, true, THREADS>(cnt, words, bal, unb);
+    else lean_clear<16, false, THREADS>(cnt, words, bal, unb);
   } else {
-    if (fin) lean_clear<32, true>(cnt, words, bal, unb); else lean_clear<32, false>(cnt, words, bal, unb);
+    if (fin) lean_clear<32, true, THREADS>(cnt, words, bal, unb);
+    else lean_clear<32, false, THREADS>(cnt, words, bal, unb);
   }
 }
 
@@ -502,7 +509,8 @@ __device__ __forceinline__ void window_walk_dispatch(int cw, bool fin, const uin
 // so the warps fetch their first batch of the next window (cursors and first
 // chunks) and only then clear the counters, which hides that load latency
 // behind the clear.
-template <int G>
+// THREADS and WORDS: the CTA's threads and counter words.
+template <int G, int THREADS = kSweepThreads, uint32_t WORDS = kSweepWords>
 __device__ __forceinline__ void sweep_cursor_item(const uint32_t* __restrict__ col, uint32_t L, uint2* cur,
                                                   const ItemWindows& iw, bool fin, uint32_t sbase, uint32_t* cnt_words,
                                                   uint32_t* nbn, uint64_t& bal, uint64_t& unb) {
@@ -513,26 +521,27 @@ __device__ __forceinline__ void sweep_cursor_item(const uint32_t* __restrict__ c
     uint32_t lo, hi;
     int cw;
     iw.window(r, lo, hi, cw);
-    const Win w = make_win(cw, lo, hi, sbase);
+    const Win w = make_win<WORDS>(cw, lo, hi, sbase);
     window_walk_dispatch<G, false>(cw, fin, col, b, cur, L, &nbn[r & 1], cur, nullptr, w, bal, unb);
     __syncthreads();
     if (r + 1 < R) batch_fetch<G>(col, cur, L, &nbn[(r + 1) & 1], b);
-    window_clear(cw, fin, cnt_words, w.words, bal, unb);
+    window_clear<THREADS>(cw, fin, cnt_words, w.words, bal, unb);
     if (threadIdx.x == 0) nbn[r & 1] = 0u;
     __syncthreads();
   }
 }
 
+template <int THREADS = kSweepThreads, uint32_t WORDS = kSweepWords>
 __device__ __forceinline__ void sweep_cursor_item_dispatch(int group_log, const uint32_t* __restrict__ col,
                                                            uint32_t L, uint2* cur, const ItemWindows& iw, bool fin,
                                                            uint32_t sbase, uint32_t* cnt_words, uint32_t* nbn,
                                                            uint64_t& bal, uint64_t& unb) {
   switch (group_log) {
-    case 0: sweep_cursor_item<1>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
-    case 2: sweep_cursor_item<4>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
-    case 3: sweep_cursor_item<8>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
-    case 4: sweep_cursor_item<16>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
-    default: sweep_cursor_item<32>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
+    case 0: sweep_cursor_item<1, THREADS, WORDS>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
+    case 2: sweep_cursor_item<4, THREADS, WORDS>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
+    case 3: sweep_cursor_item<8, THREADS, WORDS>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
+    case 4: sweep_cursor_item<16, THREADS, WORDS>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
+    default: sweep_cursor_item<32, THREADS, WORDS>(col, L, cur, iw, fin, sbase, cnt_words, nbn, bal, unb); break;
   }
 }
 
