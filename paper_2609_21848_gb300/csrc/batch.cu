@@ -257,6 +257,8 @@ struct dbbc_batch {
   int device = 0;
   cudaStream_t stream = nullptr;   // stream the plan was created on (frees are ordered on it)
   cudaStream_t capture = nullptr;  // private stream used only to capture the CUDA graph
+  cudaStream_t side = nullptr;     // second branch of a count (narrow hub items and the medium tier)
+  cudaEvent_t fork = nullptr, join = nullptr;
   int32_t n_graphs = 0;
   dbbc::GraphDesc* desc = nullptr;
   dbbc::BatchPivot* light = nullptr;
@@ -291,6 +293,11 @@ static void batch_release(dbbc_batch* b) {
   b->allocations.clear();
   if (b->capture) cudaStreamDestroy(b->capture);
   b->capture = nullptr;
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  b->side = nullptr;
+  b->fork = b->join = nullptr;
 }
 
 static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector<BatchHubItem>& items,
@@ -416,27 +423,42 @@ static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector
                                                       (size_t)kMediumSlots * 12);
     b->medium_grid = (int)std::max<int64_t>(1, std::min<int64_t>(b->n_medium, mcap));
   }
+  if (!b->side) {
+    DBBC_CUDA(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+    DBBC_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    DBBC_CUDA(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
+  }
   DBBC_CUDA(cudaMemcpyAsync(b->desc, desc.data(), desc.size() * sizeof(GraphDesc), cudaMemcpyHostToDevice, s));
   if (!items.empty())
     DBBC_CUDA(cudaMemcpyAsync(b->hub, items.data(), items.size() * sizeof(BatchHubItem), cudaMemcpyHostToDevice, s));
   DBBC_CUDA(cudaStreamSynchronize(s));  // host vectors must outlive the copies
 }
 
-// The batch count: clear outputs and counters, then the three tiers.
+// The batch count: clear outputs and counters, then the tiers on two
+// branches that run side by side (every kernel adds into the graphs' output
+// pairs with atomics, so their order does not matter): the wide hub items and
+// the light tier on `s`, the narrow hub items and the medium tier on the side
+// stream. The side branch forks from and joins back into `s`, also when `s`
+// is being captured.
 static void enqueue_batch(dbbc_batch* b, cudaStream_t s) {
   DBBC_CUDA(cudaMemsetAsync(b->out, 0, (size_t)b->n_graphs * 2 * sizeof(unsigned long long), s));
   DBBC_CUDA(cudaMemsetAsync(b->counters, 0, 3 * sizeof(int), s));
   DBBC_CUDA(cudaMemsetAsync(b->status, 0, sizeof(unsigned), s));
-  if (b->n_light > 0) {
-    const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
-    count_light_batch_kernel<<<(unsigned)b->light_grid, kLightWarps * 32, smem, s>>>(b->desc, b->light, b->n_light,
-                                                                                     b->counters, b->out, b->status);
+  const bool two = b->side && (b->n_narrow > 0 || b->n_medium > 0) && (b->n_wide > 0 || b->n_light > 0);
+  cudaStream_t s2 = two ? b->side : s;
+  if (two) {
+    DBBC_CUDA(cudaEventRecord(b->fork, s));
+    DBBC_CUDA(cudaStreamWaitEvent(s2, b->fork, 0));
+  }
+  if (b->n_narrow > 0) {
+    DBBC_NARROW_SWEEP<<<b->narrow_grid, kNarrowThreads, kNarrowSmem, s2>>>(
+        b->desc, b->hub + b->n_wide, b->n_narrow, b->counters + 2, b->narrow_cursors, b->max_lower, b->out);
     DBBC_LAUNCH_CHECK();
   }
   if (b->n_medium > 0) {
     const size_t smem = (size_t)kMediumSlots * 12;
-    count_medium_batch_kernel<<<(unsigned)b->medium_grid, kMediumThreads, smem, s>>>(b->desc, b->medium,
-                                                                                     b->n_medium, b->out, b->status);
+    count_medium_batch_kernel<<<(unsigned)b->medium_grid, kMediumThreads, smem, s2>>>(b->desc, b->medium,
+                                                                                      b->n_medium, b->out, b->status);
     DBBC_LAUNCH_CHECK();
   }
   if (b->n_wide > 0) {
@@ -444,10 +466,15 @@ static void enqueue_batch(dbbc_batch* b, cudaStream_t s) {
                                                                   b->cursors, b->max_lower, b->out);
     DBBC_LAUNCH_CHECK();
   }
-  if (b->n_narrow > 0) {
-    DBBC_NARROW_SWEEP<<<b->narrow_grid, kNarrowThreads, kNarrowSmem, s>>>(
-        b->desc, b->hub + b->n_wide, b->n_narrow, b->counters + 2, b->narrow_cursors, b->max_lower, b->out);
+  if (b->n_light > 0) {
+    const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
+    count_light_batch_kernel<<<(unsigned)b->light_grid, kLightWarps * 32, smem, s>>>(b->desc, b->light, b->n_light,
+                                                                                     b->counters, b->out, b->status);
     DBBC_LAUNCH_CHECK();
+  }
+  if (two) {
+    DBBC_CUDA(cudaEventRecord(b->join, s2));
+    DBBC_CUDA(cudaStreamWaitEvent(s, b->join, 0));
   }
 }
 
