@@ -229,6 +229,31 @@ def test_batch_plan_capture_and_replay_mixed_graphs():
             h.free()
 
 
+@pytest.mark.parametrize("medium_max_work", [4096, 256])
+def test_batch_plan_wide_and_narrow_hub_items(medium_max_work):
+    """A plan whose hub items go to both CTA shapes: the hubs of a 1M-edge
+    Chung-Lu graph (items of more than 2^20 estimated wedges and windows wider
+    than a narrow CTA's) on the full-window CTAs, the small graphs' items on the
+    narrow ones, counted side by side; every graph equals the oracle."""
+    base = dbbc.dbbc_get_tuning()
+    graphs = [synth.workload("chunglu-1m-200k-20m", scale=0.05)] + [synth.batch_graph(i) for i in range(24)]
+    want = [oracle.count(g.u, g.v, g.s, g.n_u, g.n_v, threads=NCPU)[:2] for g in graphs]
+    try:
+        dbbc.dbbc_set_tuning({"light_max_work": 128, "medium_max_work": medium_max_work, "hub_item_work": 1 << 22})
+        handles = [dbbc.dbbc_graph_from_coo(g.u, g.v, g.s, g.n_u, g.n_v) for g in graphs]
+        try:
+            assert max(h.info["wedges_hub"] for h in handles[:1]) > 1 << 22  # the large graph has large hub items
+            with dbbc.dbbc_batch_create(handles) as b:
+                for _ in range(2):  # capture, then replay
+                    bal, unb = dbbc.dbbc_batch_count(b)
+                    assert list(zip(bal.tolist(), unb.tolist())) == want
+        finally:
+            for h in handles:
+                h.free()
+    finally:
+        dbbc.dbbc_set_tuning(base)
+
+
 def _union_inputs(graphs):
     u = np.concatenate([g.u for g in graphs]).astype(np.int32)
     v = np.concatenate([g.v for g in graphs]).astype(np.int32)
