@@ -31,7 +31,7 @@ DEFAULT = {"light_max_work": 512, "medium_max_work": 4096, "hub_item_work": 1 <<
 
 SPACE = [
     ("light_max_work", [64, 128, 256, 512]),
-    ("medium_max_work", [256, 512, 1024, 2048, 4096]),
+    ("medium_max_work", [64, 128, 256, 512, 1024, 2048, 4096]),  # = light_max_work: no medium tier
     ("hash_mult_log", [1, 2]),
     ("hub_item_work", [1 << 19, 1 << 20, 1 << 21, 1 << 22]),
     ("group_density", [[40.0, 16.0, 6.0, 2.0], [64.0, 24.0, 8.0, 3.0], [24.0, 10.0, 4.0, 1.5],

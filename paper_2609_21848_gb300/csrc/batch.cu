@@ -84,22 +84,24 @@ __device__ __forceinline__ void warp_flush(int graph, uint64_t& bal, uint64_t& u
 
 // Light tier over all graphs: warps pull chunks of 32 consecutive pivots and
 // flush their sums whenever the graph changes.
+// Each warp's table has 2^slots_log slots (at most kLightSlots).
 __global__ void __launch_bounds__(kLightWarps * 32) count_light_batch_kernel(
     const GraphDesc* __restrict__ desc, const BatchPivot* __restrict__ piv, int64_t n_piv, int* next_chunk,
-    unsigned long long* out, unsigned* status) {
+    int slots_log, unsigned long long* out, unsigned* status) {
   extern __shared__ __align__(16) unsigned char light_smem[];
+  const int slots = 1 << slots_log;
   unsigned long long* vals_all = reinterpret_cast<unsigned long long*>(light_smem);
-  uint32_t* keys_all = reinterpret_cast<uint32_t*>(vals_all + kLightWarps * kLightSlots);
+  uint32_t* keys_all = reinterpret_cast<uint32_t*>(vals_all + kLightWarps * slots);
   const int w = threadIdx.x >> 5;
   const unsigned lane = lane_id();
-  uint32_t* keys = keys_all + w * kLightSlots;
-  unsigned long long* vals = vals_all + w * kLightSlots;
-  for (int i = lane; i < kLightSlots; i += 32) {
+  uint32_t* keys = keys_all + w * slots;
+  unsigned long long* vals = vals_all + w * slots;
+  for (int i = lane; i < slots; i += 32) {
     keys[i] = kEmptyKey;
     vals[i] = 0;
   }
   __syncwarp();
-  constexpr int max_log = 10;
+  const int max_log = slots_log;
   uint64_t bal = 0, unb = 0;
   bool full = false;
   int cur_graph = -1;
@@ -140,19 +142,22 @@ __global__ void __launch_bounds__(kLightWarps * 32) count_light_batch_kernel(
 }
 
 // Medium tier over all graphs: one CTA per pivot, sums flushed per pivot.
+// The CTA's table has 2^slots_log slots (at most kMediumSlots).
 __global__ void __launch_bounds__(kMediumThreads) count_medium_batch_kernel(const GraphDesc* __restrict__ desc,
                                                                             const BatchPivot* __restrict__ piv,
-                                                                            int64_t n_piv, unsigned long long* out,
+                                                                            int64_t n_piv, int slots_log,
+                                                                            unsigned long long* out,
                                                                             unsigned* status) {
   extern __shared__ __align__(16) unsigned char med_smem[];
+  const int slots = 1 << slots_log;
   unsigned long long* vals = reinterpret_cast<unsigned long long*>(med_smem);
-  uint32_t* keys = reinterpret_cast<uint32_t*>(vals + kMediumSlots);
-  for (int i = threadIdx.x; i < kMediumSlots; i += kMediumThreads) {
+  uint32_t* keys = reinterpret_cast<uint32_t*>(vals + slots);
+  for (int i = threadIdx.x; i < slots; i += kMediumThreads) {
     keys[i] = kEmptyKey;
     vals[i] = 0;
   }
   __syncthreads();
-  constexpr int max_log = 13;
+  const int max_log = slots_log;
   bool full = false;
   for (int64_t t = blockIdx.x; t < n_piv; t += gridDim.x) {
     const BatchPivot bp = piv[t];
@@ -283,6 +288,7 @@ struct dbbc_batch {
   int* counters = nullptr;  // [0] light chunks, [1] wide hub items, [2] narrow hub items
   unsigned* status = nullptr;
   int hub_grid = 0, narrow_grid = 0, light_grid = 0, medium_grid = 0;
+  int light_log = 10, medium_log = 13;  // log2 of the hash slots of a light / medium table
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels_per_replay = 0;
   std::vector<void*> allocations;
@@ -314,6 +320,22 @@ static void batch_release(dbbc_batch* b) {
 static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector<BatchHubItem>& items,
                         const std::vector<uint64_t>& est);
 
+// Hash table sizes of the plan's light and medium kernels: the largest any of
+// its graphs' tiers needs (each graph's pivots were tiered by its own tuning).
+static void plan_table_logs(dbbc_batch* b, const dbbc_graph* const* gs, int32_t n) {
+  b->light_log = 5;
+  b->medium_log = 5;
+  for (int32_t i = 0; i < n; i++) {
+    const Tuning& t = gs[i]->tune;
+    b->light_log = std::max(b->light_log, tier_slots_log(t.light_max_work, t.hash_mult_log, 10));
+    b->medium_log = std::max(b->medium_log, tier_slots_log(t.medium_max_work, t.hash_mult_log, 13));
+  }
+}
+static size_t light_smem_bytes(const dbbc_batch* b) {
+  return (size_t)kLightWarps * ((size_t)1 << b->light_log) * 12;
+}
+static size_t medium_smem_bytes(const dbbc_batch* b) { return ((size_t)1 << b->medium_log) * 12; }
+
 // Plan for the components of one union handle: every component shares the
 // union's CSR; pivots and hub items are tagged with their component.
 static void plan_components(dbbc_batch* b, const dbbc_graph* g) {
@@ -340,6 +362,7 @@ static void plan_components(dbbc_batch* b, const dbbc_graph* g) {
   }
   // the union's items are already in descending estimated work
   for (size_t k = 0; k < nh; k++) items[k] = BatchHubItem{comps[k], 0, g->sweep_items_host[k]};
+  plan_table_logs(b, &g, 1);
   finish_plan(b, desc, items, g->sweep_est_host);
   if (b->n_medium + b->n_light > 0) {
     const int64_t total = b->n_medium + b->n_light;
@@ -377,6 +400,7 @@ static void plan_batch(dbbc_batch* b, const dbbc_graph* const* gs) {
     items[k] = hubs[k].item;
     est[k] = hubs[k].est;
   }
+  plan_table_logs(b, gs, n);
   finish_plan(b, desc, items, est);
   GatherJob* d_jobs = static_cast<GatherJob*>(batch_alloc(b, jobs.size() * sizeof(GatherJob)));
   DBBC_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(GatherJob), cudaMemcpyHostToDevice, s));
@@ -428,10 +452,10 @@ static void finish_plan(dbbc_batch* b, std::vector<GraphDesc>& desc, std::vector
     const int sms = num_sms();
     const int64_t want = ceil_div<int64_t>(ceil_div<int64_t>(b->n_light, 32), kLightWarps);
     const int64_t cap = (int64_t)sms * blocks_per_sm((const void*)count_light_batch_kernel, kLightWarps * 32,
-                                                     (size_t)kLightWarps * kLightSlots * 12);
+                                                     light_smem_bytes(b));
     b->light_grid = (int)std::max<int64_t>(1, std::min(want, cap));
     const int64_t mcap = (int64_t)sms * blocks_per_sm((const void*)count_medium_batch_kernel, kMediumThreads,
-                                                      (size_t)kMediumSlots * 12);
+                                                      medium_smem_bytes(b));
     b->medium_grid = (int)std::max<int64_t>(1, std::min<int64_t>(b->n_medium, mcap));
   }
   if (!b->side) {
@@ -467,9 +491,8 @@ static void enqueue_batch(dbbc_batch* b, cudaStream_t s) {
     DBBC_LAUNCH_CHECK();
   }
   if (b->n_medium > 0) {
-    const size_t smem = (size_t)kMediumSlots * 12;
-    count_medium_batch_kernel<<<(unsigned)b->medium_grid, kMediumThreads, smem, s2>>>(b->desc, b->medium,
-                                                                                      b->n_medium, b->out, b->status);
+    count_medium_batch_kernel<<<(unsigned)b->medium_grid, kMediumThreads, medium_smem_bytes(b), s2>>>(
+        b->desc, b->medium, b->n_medium, b->medium_log, b->out, b->status);
     DBBC_LAUNCH_CHECK();
   }
   if (b->n_wide > 0) {
@@ -478,9 +501,8 @@ static void enqueue_batch(dbbc_batch* b, cudaStream_t s) {
     DBBC_LAUNCH_CHECK();
   }
   if (b->n_light > 0) {
-    const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
-    count_light_batch_kernel<<<(unsigned)b->light_grid, kLightWarps * 32, smem, s>>>(b->desc, b->light, b->n_light,
-                                                                                     b->counters, b->out, b->status);
+    count_light_batch_kernel<<<(unsigned)b->light_grid, kLightWarps * 32, light_smem_bytes(b), s>>>(
+        b->desc, b->light, b->n_light, b->counters, b->light_log, b->out, b->status);
     DBBC_LAUNCH_CHECK();
   }
   if (two) {
@@ -539,6 +561,7 @@ void count_subset(const dbbc_graph* g, cudaStream_t s, const std::vector<int32_t
     b->max_lower = std::max<int64_t>(1, g->sweep_max_lower);
     std::vector<BatchHubItem> items(hub_items.size());
     for (size_t k = 0; k < hub_items.size(); k++) items[k] = BatchHubItem{0, 0, hub_items[k]};
+    plan_table_logs(b, &g, 1);
     finish_plan(b, desc, items, {});  // work unknown: every item on wide CTAs
     std::vector<BatchPivot> med(medium_rows.size()), light(light_rows.size());
     for (size_t k = 0; k < medium_rows.size(); k++) med[k] = BatchPivot{0, medium_rows[k]};

@@ -17,23 +17,25 @@
 namespace dbbc {
 
 // ------------------------------------------------------------------ light tier
+// Each warp's table has 2^slots_log slots (at most kLightSlots).
 __global__ void __launch_bounds__(kLightWarps * 32) count_light_kernel(CsrView g, const int32_t* __restrict__ piv,
                                                                        const uint64_t* __restrict__ work, int64_t n_piv,
-                                                                       int hash_mult_log, unsigned long long* out,
-                                                                       unsigned* status) {
+                                                                       int hash_mult_log, int slots_log,
+                                                                       unsigned long long* out, unsigned* status) {
   extern __shared__ __align__(16) unsigned char light_smem[];
+  const int slots = 1 << slots_log;
   unsigned long long* vals_all = reinterpret_cast<unsigned long long*>(light_smem);
-  uint32_t* keys_all = reinterpret_cast<uint32_t*>(vals_all + kLightWarps * kLightSlots);
+  uint32_t* keys_all = reinterpret_cast<uint32_t*>(vals_all + kLightWarps * slots);
   const int w = threadIdx.x >> 5;
   const unsigned lane = lane_id();
-  uint32_t* keys = keys_all + w * kLightSlots;
-  unsigned long long* vals = vals_all + w * kLightSlots;
-  for (int i = lane; i < kLightSlots; i += 32) {
+  uint32_t* keys = keys_all + w * slots;
+  unsigned long long* vals = vals_all + w * slots;
+  for (int i = lane; i < slots; i += 32) {
     keys[i] = kEmptyKey;
     vals[i] = 0;
   }
   __syncwarp();
-  constexpr int max_log = 10;  // log2(kLightSlots)
+  const int max_log = slots_log;
   uint64_t bal = 0, unb = 0;
   bool full = false;
   const int64_t nw = (int64_t)gridDim.x * kLightWarps;
@@ -54,19 +56,21 @@ __global__ void __launch_bounds__(kLightWarps * 32) count_light_kernel(CsrView g
 }
 
 // ------------------------------------------------------------------ medium tier
+// The CTA's table has 2^slots_log slots (at most kMediumSlots).
 __global__ void __launch_bounds__(kMediumThreads) count_medium_kernel(CsrView g, const int32_t* __restrict__ piv,
                                                                       const uint64_t* __restrict__ work,
-                                                                      int64_t n_piv, int hash_mult_log,
+                                                                      int64_t n_piv, int hash_mult_log, int slots_log,
                                                                       unsigned long long* out, unsigned* status) {
   extern __shared__ __align__(16) unsigned char med_smem[];
+  const int slots = 1 << slots_log;
   unsigned long long* vals = reinterpret_cast<unsigned long long*>(med_smem);
-  uint32_t* keys = reinterpret_cast<uint32_t*>(vals + kMediumSlots);
-  for (int i = threadIdx.x; i < kMediumSlots; i += kMediumThreads) {
+  uint32_t* keys = reinterpret_cast<uint32_t*>(vals + slots);
+  for (int i = threadIdx.x; i < slots; i += kMediumThreads) {
     keys[i] = kEmptyKey;
     vals[i] = 0;
   }
   __syncthreads();
-  constexpr int max_log = 13;  // log2(kMediumSlots)
+  const int max_log = slots_log;
   uint64_t bal = 0, unb = 0;
   bool full = false;
   for (int64_t t = blockIdx.x; t < n_piv; t += gridDim.x) {
@@ -183,22 +187,27 @@ CountProfiler::~CountProfiler() {
 // enqueue_count_prealloc.
 static void launch_light(const dbbc_graph* g, const CsrView& view, cudaStream_t s, unsigned long long* d_out,
                          unsigned* d_status) {
-  const size_t smem = (size_t)kLightWarps * kLightSlots * 12;
-  DBBC_CUDA(cudaFuncSetAttribute(count_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int slots_log = tier_slots_log(g->tune.light_max_work, g->tune.hash_mult_log, 10);
+  const size_t smem = (size_t)kLightWarps * ((size_t)1 << slots_log) * 12;
+  DBBC_CUDA(cudaFuncSetAttribute(count_light_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)kLightWarps * kLightSlots * 12)));
   const int64_t want = ceil_div<int64_t>(g->n_light, kLightWarps);
   const int64_t cap = (int64_t)num_sms() * blocks_per_sm((const void*)count_light_kernel, kLightWarps * 32, smem);
   count_light_kernel<<<(unsigned)std::min(want, cap), kLightWarps * 32, smem, s>>>(
-      view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, d_out, d_status);
+      view, g->order + g->n_hub + g->n_medium, g->work, g->n_light, g->tune.hash_mult_log, slots_log, d_out,
+      d_status);
   DBBC_LAUNCH_CHECK();
 }
 
 static void launch_medium(const dbbc_graph* g, const CsrView& view, cudaStream_t s, unsigned long long* d_out,
                           unsigned* d_status) {
-  const size_t smem = (size_t)kMediumSlots * 12;
-  DBBC_CUDA(cudaFuncSetAttribute(count_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int slots_log = tier_slots_log(g->tune.medium_max_work, g->tune.hash_mult_log, 13);
+  const size_t smem = ((size_t)1 << slots_log) * 12;
+  DBBC_CUDA(cudaFuncSetAttribute(count_medium_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)kMediumSlots * 12)));
   const int64_t cap = (int64_t)num_sms() * blocks_per_sm((const void*)count_medium_kernel, kMediumThreads, smem);
   count_medium_kernel<<<(unsigned)std::min<int64_t>(g->n_medium, cap), kMediumThreads, smem, s>>>(
-      view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, d_out, d_status);
+      view, g->order + g->n_hub, g->work, g->n_medium, g->tune.hash_mult_log, slots_log, d_out, d_status);
   DBBC_LAUNCH_CHECK();
 }
 

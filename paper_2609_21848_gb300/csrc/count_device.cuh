@@ -202,6 +202,15 @@ __device__ __forceinline__ bool hash_walk_dispatch(int group_log, uint32_t tid, 
   }
 }
 
+// log2 of the hash slots a tier's tables need at most: table_log of the
+// tier's largest accepted-wedge count (5..cap). Kernels of a tier get this
+// many slots per table, so small tiers leave room for more CTAs per SM.
+inline int tier_slots_log(uint64_t max_work, int mult_log, int cap) {
+  int k = 5;
+  while (k < cap && (1ull << k) < (max_work << mult_log)) k++;
+  return k;
+}
+
 constexpr int kLightWarps = 8;
 
 constexpr int kMediumThreads = 256;
