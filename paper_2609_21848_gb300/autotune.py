@@ -111,9 +111,10 @@ def measure(graphs, tuning: dict, repeats: int = 5, stream=None) -> float:
     return times[len(times) // 2]
 
 
-def tune(graphs, repeats: int = 5, log=print) -> tuple[dict, float, float]:
-    """Coordinate search from the defaults; returns (best tuning, its ms, default ms)."""
-    best = dict(DEFAULT)
+def tune(graphs, repeats: int = 5, log=print, start: dict | None = None) -> tuple[dict, float, float]:
+    """Coordinate search from `start` (the defaults when None); returns (best
+    tuning, its ms, the start's ms)."""
+    best = dict(start or DEFAULT)
     best_ms = base_ms = measure(graphs, best, repeats)
     log(f"default: {base_ms:.3f} ms")
     for key, candidates in SPACE:
@@ -165,6 +166,8 @@ def main():
     ap.add_argument("--repeats", type=int, default=5)
     ap.add_argument("--out", default=None)
     ap.add_argument("--make-default", action="store_true", help="make this workload's tuning the GPU's default")
+    ap.add_argument("--from-saved", action="store_true",
+                    help="start the search from this workload's saved record instead of the defaults")
     a = ap.parse_args()
     os.environ["DBBC_NO_TUNING"] = "1"
     dev = torch.device("cuda")
@@ -173,7 +176,14 @@ def main():
     else:
         gs = [synth.workload(a.workload)]
     graphs = [tuple(torch.from_numpy(x).to(dev) for x in (g.u, g.v, g.s)) + (g.n_u, g.n_v) for g in gs]
-    best, ms, base = tune(graphs, a.repeats)
+    start = None
+    if a.from_saved:
+        path = a.out or saved_path()
+        if os.path.exists(path):
+            with open(path) as f:
+                entry = json.load(f)["workloads"].get(a.workload)
+            start = dict(DEFAULT, **entry["tuning"]) if entry else None
+    best, ms, base = tune(graphs, a.repeats, start=start)
     path = save(best, a.workload, ms, base, a.out, a.make_default)
     print(json.dumps({"tuning": best, "count_ms": ms, "default_ms": base, "saved": path}))
 
