@@ -68,8 +68,12 @@ uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); 
 // library. The pool keeps up to kPoolKeepBytes of freed memory mapped across
 // synchronizations (the default pool would unmap all of it at every
 // synchronize, and the next build or count would map it again); what it holds
-// beyond that goes back to the device.
-constexpr uint64_t kPoolKeepBytes = uint64_t{8} << 30;
+// beyond that goes back to the device. A 300M-edge build and count peak near
+// 20 GB of scratch and graph, so the pool keeps 32 GB.
+#ifndef DBBC_POOL_KEEP_GB
+#define DBBC_POOL_KEEP_GB 32
+#endif
+constexpr uint64_t kPoolKeepBytes = uint64_t{DBBC_POOL_KEEP_GB} << 30;
 
 static cudaMemPool_t library_pool(int dev) {
   static std::mutex mu;
