@@ -165,13 +165,16 @@ __global__ void csr_u_keys_kernel(const int32_t* __restrict__ eu, const int32_t*
   }
 }
 
+// V keys of the U-sorted list, each with its U position (the edge's position
+// in its U row) as the value the V sort carries along.
 __global__ void csr_v_keys_kernel(const uint64_t* __restrict__ ku, int64_t m, int bits_u, int bits_v,
-                                  uint64_t* __restrict__ kv) {
+                                  uint64_t* __restrict__ kv, uint32_t* __restrict__ upos) {
   const uint64_t mask_v = (1ull << bits_v) - 1;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = ku[i];
     const uint64_t ru = k >> (bits_v + 1), rv = (k >> 1) & mask_v;
     kv[i] = (rv << (bits_u + 1)) | (ru << 1) | (k & 1u);
+    upos[i] = (uint32_t)i;
   }
 }
 
@@ -189,6 +192,7 @@ __global__ void adjacent_dup_kernel(const uint64_t* __restrict__ key, int64_t m,
 struct CsrKeys {
   const uint64_t* ku;
   const uint64_t* kv;
+  const uint32_t* upos;  // upos[k]: the U position of the edge at V position m + k
   int64_t m;
   int32_t n_u;
   int bits_u, bits_v;
@@ -232,37 +236,42 @@ __global__ void lower_kernel(const int64_t* __restrict__ row_ptr, const uint32_t
 }
 
 // work[p] = sum over lower neighbours v of p of |{w in row(v) : rank(w) < rank(p)}|,
-// i.e. the wedges Algorithm 1 accepts at pivot p. One thread per CSR entry;
-// entries of a row are contiguous, so a segmented warp sum merges them.
-__global__ void work_kernel(CsrKeys ck, const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
-                            const uint32_t* __restrict__ lower, int64_t nnz, int32_t n_u,
+// i.e. the wedges Algorithm 1 accepts at pivot p. Every edge appears as the
+// entry at V position m + k (row v, index idx_v in it) and at U position
+// upos[k] (row u, index idx_u); rows ascend by rank, so idx_v entries of
+// row(v) rank below u and idx_u entries of row(u) rank below v. A lower
+// neighbour v of u (idx_u < lower[u]) thus adds idx_v to work[u], and a lower
+// neighbour u of v (idx_v < lower[v]) adds idx_u to work[v]. One thread per
+// edge, in V order: the V rows' sums are merged by a segmented warp sum, the
+// U rows' go to their rows directly.
+__global__ void work_kernel(CsrKeys ck, const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ lower,
                             unsigned long long* __restrict__ work) {
+  const int64_t m = ck.m;
+  const uint64_t mask_u = (1ull << ck.bits_u) - 1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t iters = (nnz + stride - 1) / stride;
+  const int64_t iters = (m + stride - 1) / stride;  // the same for every lane: the warp shuffles together
   const unsigned lane = lane_id();
   for (int64_t it = 0; it < iters; it++) {
-    const int64_t i = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t r = -1;
+    const int64_t k = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t v = -1;
     uint64_t acc = 0;
-    if (i < nnz) {
-      r = ck.row(i);
-      if ((uint64_t)(i - row_ptr[r]) < lower[r]) {
-        const uint32_t e = col[i];
-        const bool is_u = r < n_u;
-        const uint32_t sp = is_u ? (uint32_t)r : (uint32_t)(r - n_u);
-        const int64_t vrow = (is_u ? (int64_t)n_u : 0) + (e >> 1);
-        const int64_t b = row_ptr[vrow];
-        acc = (uint64_t)lower_bound_dev<uint32_t>(col + b, row_ptr[vrow + 1] - b, sp << 1);
-      }
+    if (k < m) {
+      const uint64_t key = ck.kv[k];
+      const int64_t ru = (int64_t)((key >> 1) & mask_u);
+      v = (int64_t)ck.n_u + (int64_t)(key >> (ck.bits_u + 1));
+      const uint64_t idx_v = (uint64_t)(m + k - row_ptr[v]);
+      const uint64_t idx_u = (uint64_t)((int64_t)ck.upos[k] - row_ptr[ru]);
+      if (idx_u < lower[ru] && idx_v) atomicAdd(&work[ru], (unsigned long long)idx_v);
+      if (idx_v < lower[v]) acc = idx_u;
     }
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint64_t y = __shfl_down_sync(kFullMask, acc, o);
-      const int64_t r2 = __shfl_down_sync(kFullMask, r, o);
-      if (lane + o < 32 && r2 == r) acc += y;
+      const int64_t v2 = __shfl_down_sync(kFullMask, v, o);
+      if (lane + o < 32 && v2 == v) acc += y;
     }
-    const int64_t rp = __shfl_up_sync(kFullMask, r, 1);
-    if (r >= 0 && acc && (lane == 0 || rp != r)) atomicAdd(&work[r], (unsigned long long)acc);
+    const int64_t vp = __shfl_up_sync(kFullMask, v, 1);
+    if (v >= 0 && acc && (lane == 0 || vp != v)) atomicAdd(&work[v], (unsigned long long)acc);
   }
 }
 
@@ -738,7 +747,7 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
       DBBC_LAUNCH_CHECK();
     }
     *dup = false;
-    CsrKeys k{ck0, ck0 + me, me, n_u, bits_u, bits_v};
+    CsrKeys k{ck0, ck0 + me, nullptr, me, n_u, bits_u, bits_v};
     if (me == 0) return k;
     // the halves of ck0 / ck1 hold the U keys and the V keys; the sorts skip
     // bit 0 (the sign), so repeated pairs stay in input order
@@ -750,11 +759,14 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
     DBBC_CUDA(cudaMemsetAsync(d_flags + 3, 0, sizeof(unsigned), s));
     adjacent_dup_kernel<<<grid_for(me), 256, 0, s>>>(k.ku, me, d_flags + 3);
     DBBC_LAUNCH_CHECK();
-    csr_v_keys_kernel<<<grid_for(me), 256, 0, s>>>(k.ku, me, bits_u, bits_v, ck0 + me);
+    uint32_t* up0 = sc.get<uint32_t>((size_t)me);
+    uint32_t* up1 = sc.get<uint32_t>((size_t)me);
+    csr_v_keys_kernel<<<grid_for(me), 256, 0, s>>>(k.ku, me, bits_u, bits_v, ck0 + me, up0);
     DBBC_LAUNCH_CHECK();
-    const bool alt_v = radix_sort<uint64_t, uint32_t, false>(ck0 + me, ck1 + me, nullptr, nullptr, me, 1 + bits_u,
-                                                             1 + bits_u + bits_v, s, sc);
+    const bool alt_v = radix_sort<uint64_t, uint32_t, true>(ck0 + me, ck1 + me, up0, up1, me, 1 + bits_u,
+                                                            1 + bits_u + bits_v, s, sc);
     k.kv = alt_v ? ck1 + me : ck0 + me;
+    k.upos = alt_v ? up1 : up0;
     *dup = read_back(d_flags + 3, s) != 0;
     return k;
   };
@@ -808,8 +820,8 @@ void build_graph(dbbc_graph* g, const int32_t* u_in, const int32_t* v_in, const 
 
   // ---- a4: accepted wedges per pivot and the counting tiers
   if (g->nnz > 0) {
-    work_kernel<<<grid_for(g->nnz), 256, 0, s>>>(ck, g->row_ptr, g->col, g->lower, g->nnz, n_u,
-                                                 reinterpret_cast<unsigned long long*>(g->work));
+    work_kernel<<<grid_for(g->m), 256, 0, s>>>(ck, g->row_ptr, g->lower,
+                                               reinterpret_cast<unsigned long long*>(g->work));
     DBBC_LAUNCH_CHECK();
   }
   PrepStats* d_st = sc.get<PrepStats>(1);
