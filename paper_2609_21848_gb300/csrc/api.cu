@@ -300,8 +300,9 @@ size_t dbbc_estimate_bytes(int64_t m, int32_t n_u, int32_t n_v) {
   const size_t n = (size_t)n_u + (size_t)n_v, mm = (size_t)m;
   // handle: row_ptr 8(n+1), col 8m, lower/vertex 8n, work 8n, order 4n, items
   const size_t handle = 8 * (n + 1) + 8 * mm + 8 * n + 8 * n + 4 * n + 16 * (mm / 64 + 16);
-  // build peak: inputs 9m, dedup 24m + flags/pos 8m, edges 9m, CSR keys 32m, vertex keys 16n + 16n
-  const size_t build = 9 * mm + 32 * mm + 9 * mm + 32 * mm + 48 * n + (mm / 4096 + 1) * 1024;
+  // build peak: inputs 9m, dedup 24m + flags/pos 8m, edges 9m, CSR keys 32m and their U positions 8m, vertex
+  // keys 16n + 16n
+  const size_t build = 9 * mm + 32 * mm + 9 * mm + 32 * mm + 8 * mm + 48 * n + (mm / 4096 + 1) * 1024;
   return handle + build;
 }
 
