@@ -239,7 +239,7 @@ DBBC_API size_t dbbc_graph_device_bytes(const dbbc_graph* g);
 /* Upper estimate of the peak device bytes dbbc_graph_from_coo needs for a
  * graph of this size (handle plus build scratch). A count needs scratch of its
  * own on top of the handle, mostly the hub sweep's neighbour lists: at most
- * 2^24 slots of 8 bytes per SM, in practice a few slots per lower neighbour of
+ * 2^23 slots of 8 bytes per SM, in practice a few slots per lower neighbour of
  * the largest sparse hub per SM. */
 DBBC_API size_t dbbc_estimate_bytes(int64_t m, int32_t n_u, int32_t n_v);
 

@@ -48,13 +48,15 @@ constexpr uint64_t kSweepItemWork = 1u << 20;  // target accepted wedges per wor
 // Hub items in list mode (see sweep_device.cuh) run in spans of at most
 // kListMaxWindows windows, with at most kListCapEntries list slots (8 bytes
 // each) per CTA. Longer spans re-queue fewer neighbours between spans: on the
-// 300M-edge polarized graph 128 windows and 2^24 slots (up to 19.5 GB of list
-// scratch over 152 CTAs) swept 2.6% faster than 64 and 2^22.
+// 300M-edge polarized graph 128 windows and 2^23 slots (up to 10 GB of list
+// scratch over 152 CTAs) swept 2.0% faster than 64 and 2^22; 2^24 slots gained
+// another 0.6% but held twice the scratch, which the memory pool then had to
+// map again for the next build.
 #ifndef DBBC_LIST_MAX_WINDOWS
 #define DBBC_LIST_MAX_WINDOWS 128
 #endif
 #ifndef DBBC_LIST_CAP_LOG
-#define DBBC_LIST_CAP_LOG 24
+#define DBBC_LIST_CAP_LOG 23
 #endif
 constexpr int kListMaxWindows = DBBC_LIST_MAX_WINDOWS;
 constexpr int64_t kListCapEntries = int64_t{1} << DBBC_LIST_CAP_LOG;
