@@ -26,8 +26,10 @@ constexpr int kMediumSlots = 8192;
 #ifndef DBBC_SWEEP_THREADS
 #define DBBC_SWEEP_THREADS 1024
 #endif
+// entries per lane per chunk of the per-vertex / per-edge window walks (4
+// measured 5% faster than 2 on GB300)
 #ifndef DBBC_SWEEP_UNROLL
-#define DBBC_SWEEP_UNROLL 2
+#define DBBC_SWEEP_UNROLL 4
 #endif
 constexpr uint32_t kSweepWindow16 = DBBC_SWEEP_WINDOW16;     // 32-bit counters packing two 16-bit halves
 constexpr uint32_t kSweepWindow32 = DBBC_SWEEP_WINDOW16 / 2;  // 64-bit counters packing two 32-bit halves
