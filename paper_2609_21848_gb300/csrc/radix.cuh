@@ -113,7 +113,10 @@ void exclusive_scan(const TI* in, TO* out, int64_t n, cudaStream_t s, Scratch& s
 // ------------------------------------------------------------------ radix sort
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 8;
+#ifndef DBBC_RS_ITEMS
+#define DBBC_RS_ITEMS 8
+#endif
+constexpr int kRsItems = DBBC_RS_ITEMS;         // keys per thread
 constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 keys per tile
 
 template <typename K>
@@ -121,19 +124,29 @@ __device__ __forceinline__ uint32_t rs_digit(K key, int shift) {
   return (uint32_t)(key >> shift) & 0xFFu;
 }
 
+// Per-tile digit counts, digit-major: hist[d * ntiles + tile]. Every thread
+// loads its kRsItems keys before counting any, so that each warp has kRsItems
+// loads in flight at once.
 template <typename K>
-__global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* keys, int64_t n, int shift,
+__global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* __restrict__ keys, int64_t n, int shift,
                                                                  uint32_t* hist, int64_t ntiles) {
   __shared__ uint32_t h[kRsWarps][256];
   const int w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kRsTile + threadIdx.x;
+  K key[kRsItems];
+#pragma unroll
+  for (int j = 0; j < kRsItems; j++) {
+    const int64_t k = base + j * kRsThreads;
+    key[j] = k < n ? keys[k] : K(0);
+  }
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&h[0][0])[i] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kRsTile;
-  for (int i = threadIdx.x; i < kRsTile; i += kRsThreads) {
-    const int64_t k = base + i;
-    const uint32_t d = k < n ? rs_digit(keys[k], shift) : 256u;
+#pragma unroll
+  for (int j = 0; j < kRsItems; j++) {
+    const uint32_t d = base + j * kRsThreads < n ? rs_digit(key[j], shift) : 256u;
     const unsigned peers = __match_any_sync(kFullMask, d);
     if (d < 256u && (int)lane_id() == 31 - __clz(peers)) h[w][d] += __popc(peers);
+    __syncwarp();
   }
   __syncthreads();
   uint32_t c = 0;
@@ -142,6 +155,12 @@ __global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* keys, i
   hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c;
 }
 
+// One digit pass of the stable sort. A tile's keys (and values) are loaded
+// first, all kRsItems per thread in flight together; each warp then ranks its
+// 256 keys in input order (warp match per key, per-warp digit counters), the
+// block turns the per-warp counts into tile positions, the tile is staged in
+// shared memory in digit order, and written out as whole digit runs at the
+// offsets of the scanned digit-major histogram.
 template <typename K, typename V, bool HAS_V>
 __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const K* __restrict__ kin, const V* __restrict__ vin,
                                                                     K* __restrict__ kout, V* __restrict__ vout,
@@ -157,31 +176,39 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const K* __re
 
   const int w = threadIdx.x >> 5;
   const unsigned lane = lane_id();
-  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) wh[i] = 0;
-  gofs[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
-  __syncthreads();
-
   const int64_t tile_base = (int64_t)blockIdx.x * kRsTile;
   const int64_t wbase = tile_base + (int64_t)w * (kRsItems * 32);
-  const unsigned lt_mask = (1u << lane) - 1u;
   K key[kRsItems];
   V val[kRsItems];
-  uint32_t loc[kRsItems];
-  uint32_t dg[kRsItems];
 #pragma unroll
   for (int j = 0; j < kRsItems; j++) {
     const int64_t i = wbase + j * 32 + lane;
     const bool valid = i < n;
     key[j] = valid ? kin[i] : K(0);
     if (HAS_V) val[j] = valid ? vin[i] : V(0);
-    const uint32_t d = valid ? rs_digit(key[j], shift) : 256u;
-    dg[j] = d;
-    const unsigned peers = __match_any_sync(kFullMask, d);
+  }
+  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) wh[i] = 0;
+  gofs[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  __syncthreads();
+
+  // digits (256 = past the end) and their warp peers, independent per item
+  unsigned peers[kRsItems];
+#pragma unroll
+  for (int j = 0; j < kRsItems; j++) {
+    const uint32_t d = wbase + j * 32 + lane < n ? rs_digit(key[j], shift) : 256u;
+    peers[j] = __match_any_sync(kFullMask, d);
+  }
+  // rank within the warp, item by item in input order
+  const unsigned lt_mask = (1u << lane) - 1u;
+  uint32_t loc[kRsItems];
+#pragma unroll
+  for (int j = 0; j < kRsItems; j++) {
+    const uint32_t d = wbase + j * 32 + lane < n ? rs_digit(key[j], shift) : 256u;
     uint32_t pre = 0;
     if (d < 256u) pre = wh[w * 256 + d];
     __syncwarp();
-    loc[j] = pre + __popc(peers & lt_mask);
-    if (d < 256u && (int)lane == 31 - __clz(peers)) wh[w * 256 + d] = pre + __popc(peers);
+    loc[j] = pre + __popc(peers[j] & lt_mask);
+    if (d < 256u && (int)lane == 31 - __clz(peers[j])) wh[w * 256 + d] = pre + __popc(peers[j]);
     __syncwarp();
   }
   __syncthreads();
@@ -200,9 +227,10 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const K* __re
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < kRsItems; j++) {
-    const uint32_t d = dg[j];
-    const uint32_t pos = d < 256u ? bstart[d] + wh[w * 256 + d] + loc[j] : 0u;
-    if (d < 256u && DBBC_CHECK(pos < (uint32_t)kRsTile)) {
+    const bool valid = wbase + j * 32 + lane < n;
+    const uint32_t d = valid ? rs_digit(key[j], shift) : 256u;
+    const uint32_t pos = valid ? bstart[d] + wh[w * 256 + d] + loc[j] : 0u;
+    if (valid && DBBC_CHECK(pos < (uint32_t)kRsTile)) {
       sk[pos] = key[j];
       if (HAS_V) sv[pos] = val[j];
     }
@@ -210,13 +238,18 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const K* __re
   __syncthreads();
   const int64_t rem = n - tile_base;
   const int cnt = rem < kRsTile ? (int)rem : kRsTile;
-  for (int i = threadIdx.x; i < cnt; i += kRsThreads) {
-    const K k = sk[i];
-    const uint32_t d = rs_digit(k, shift);
-    const int64_t g = (int64_t)gofs[d] + (i - (int64_t)bstart[d]);
-    if (!DBBC_CHECK(g >= 0 && g < n)) continue;
-    kout[g] = k;
-    if (HAS_V) vout[g] = sv[i];
+#pragma unroll
+  for (int j = 0; j < kRsItems; j++) {
+    const int i = threadIdx.x + j * kRsThreads;
+    if (i < cnt) {
+      const K k = sk[i];
+      const uint32_t d = rs_digit(k, shift);
+      const int64_t g = (int64_t)gofs[d] + (i - (int64_t)bstart[d]);
+      if (DBBC_CHECK(g >= 0 && g < n)) {
+        kout[g] = k;
+        if (HAS_V) vout[g] = sv[i];
+      }
+    }
   }
 }
 
