@@ -97,21 +97,40 @@ __global__ void compact_edges_kernel(const uint64_t* __restrict__ key, const uin
   }
 }
 
-// Degrees over unified ids; consecutive equal ids (edges are sorted by u) are
-// merged within a warp before the atomic.
+// deg[id] += 1 for every lane with ok, as one atomic per run of equal ids in
+// consecutive lanes (edges that arrive grouped by an endpoint form long runs).
+__device__ __forceinline__ void add_runs(int32_t* __restrict__ deg, int32_t id, bool ok) {
+  const unsigned lane = lane_id();
+  const int32_t x = ok ? id : -1;
+  const int32_t prev = __shfl_up_sync(kFullMask, x, 1);
+  const bool head = lane == 0 || prev != x;
+  const unsigned heads = __ballot_sync(kFullMask, head);
+  const unsigned later = lane == 31 ? 0u : heads & (~0u << (lane + 1));
+  const int len = (later ? __ffs(later) - 1 : 32) - (int)lane;
+  if (ok && head) atomicAdd(&deg[x], len);
+}
+
+// Degrees over unified ids (V ids follow the U ids).
 __global__ void degree_kernel(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev, int64_t m,
                               int32_t n_u, int32_t* __restrict__ deg) {
+  constexpr int kRound = 4;  // edges per thread per round, their loads in flight together
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t iters = (m + stride - 1) / stride;
-  for (int64_t it = 0; it < iters; it++) {
-    const int64_t i = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool ok = i < m;
-    const int32_t a = ok ? eu[i] : -1;
-    const int32_t b = ok ? n_u + ev[i] : -1;
-    unsigned peers = __match_any_sync(kFullMask, a);
-    if (ok && (int)lane_id() == 31 - __clz(peers)) atomicAdd(&deg[a], __popc(peers));
-    peers = __match_any_sync(kFullMask, b);
-    if (ok && (int)lane_id() == 31 - __clz(peers)) atomicAdd(&deg[b], __popc(peers));
+  const int64_t iters = (m + stride - 1) / stride;  // the same for every lane: the warp votes together
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t it = 0; it < iters; it += kRound) {
+    int32_t a[kRound], b[kRound];
+#pragma unroll
+    for (int j = 0; j < kRound; j++) {
+      const int64_t i = (it + j) * stride + t0;
+      a[j] = i < m ? eu[i] : 0;
+      b[j] = i < m ? n_u + ev[i] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kRound; j++) {
+      const bool ok = (it + j) * stride + t0 < m;
+      add_runs(deg, a[j], ok);
+      add_runs(deg, b[j], ok);
+    }
   }
 }
 
@@ -246,32 +265,53 @@ __global__ void lower_kernel(const int64_t* __restrict__ row_ptr, const uint32_t
 // U rows' go to their rows directly.
 __global__ void work_kernel(CsrKeys ck, const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ lower,
                             unsigned long long* __restrict__ work) {
+  constexpr int kRound = 4;  // edges per thread per round, their loads in flight together
   const int64_t m = ck.m;
   const uint64_t mask_u = (1ull << ck.bits_u) - 1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t iters = (m + stride - 1) / stride;  // the same for every lane: the warp shuffles together
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lane = lane_id();
-  for (int64_t it = 0; it < iters; it++) {
-    const int64_t k = it * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t v = -1;
-    uint64_t acc = 0;
-    if (k < m) {
-      const uint64_t key = ck.kv[k];
-      const int64_t ru = (int64_t)((key >> 1) & mask_u);
-      v = (int64_t)ck.n_u + (int64_t)(key >> (ck.bits_u + 1));
-      const uint64_t idx_v = (uint64_t)(m + k - row_ptr[v]);
-      const uint64_t idx_u = (uint64_t)((int64_t)ck.upos[k] - row_ptr[ru]);
-      if (idx_u < lower[ru] && idx_v) atomicAdd(&work[ru], (unsigned long long)idx_v);
-      if (idx_v < lower[v]) acc = idx_u;
+  for (int64_t it = 0; it < iters; it += kRound) {
+    uint64_t key[kRound];
+    uint32_t up[kRound];
+#pragma unroll
+    for (int j = 0; j < kRound; j++) {
+      const int64_t k = (it + j) * stride + t0;
+      key[j] = k < m ? ck.kv[k] : 0;
+      up[j] = k < m ? ck.upos[k] : 0;
+    }
+    int64_t v[kRound], ru[kRound];
+    uint64_t idx_v[kRound], idx_u[kRound];
+    uint32_t low_u[kRound], low_v[kRound];
+#pragma unroll
+    for (int j = 0; j < kRound; j++) {
+      const int64_t k = (it + j) * stride + t0;
+      ru[j] = (int64_t)((key[j] >> 1) & mask_u);
+      v[j] = -1;
+      idx_v[j] = idx_u[j] = 0;
+      low_u[j] = low_v[j] = 0;
+      if (k < m) {
+        v[j] = (int64_t)ck.n_u + (int64_t)(key[j] >> (ck.bits_u + 1));
+        idx_v[j] = (uint64_t)(m + k - row_ptr[v[j]]);
+        idx_u[j] = (uint64_t)((int64_t)up[j] - row_ptr[ru[j]]);
+        low_u[j] = lower[ru[j]];
+        low_v[j] = lower[v[j]];
+      }
     }
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t y = __shfl_down_sync(kFullMask, acc, o);
-      const int64_t v2 = __shfl_down_sync(kFullMask, v, o);
-      if (lane + o < 32 && v2 == v) acc += y;
+    for (int j = 0; j < kRound; j++) {
+      if (v[j] >= 0 && idx_u[j] < low_u[j] && idx_v[j]) atomicAdd(&work[ru[j]], (unsigned long long)idx_v[j]);
+      uint64_t acc = (v[j] >= 0 && idx_v[j] < low_v[j]) ? idx_u[j] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_down_sync(kFullMask, acc, o);
+        const int64_t v2 = __shfl_down_sync(kFullMask, v[j], o);
+        if (lane + o < 32 && v2 == v[j]) acc += y;
+      }
+      const int64_t vp = __shfl_up_sync(kFullMask, v[j], 1);
+      if (v[j] >= 0 && acc && (lane == 0 || vp != v[j])) atomicAdd(&work[v[j]], (unsigned long long)acc);
     }
-    const int64_t vp = __shfl_up_sync(kFullMask, v, 1);
-    if (v >= 0 && acc && (lane == 0 || vp != v)) atomicAdd(&work[v], (unsigned long long)acc);
   }
 }
 

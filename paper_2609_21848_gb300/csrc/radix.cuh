@@ -116,12 +116,34 @@ constexpr int kRsWarps = kRsThreads / 32;
 #ifndef DBBC_RS_ITEMS
 #define DBBC_RS_ITEMS 8
 #endif
+#ifndef DBBC_RS_MATCH
+#define DBBC_RS_MATCH 0
+#endif
 constexpr int kRsItems = DBBC_RS_ITEMS;         // keys per thread
 constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 keys per tile
 
 template <typename K>
 __device__ __forceinline__ uint32_t rs_digit(K key, int shift) {
   return (uint32_t)(key >> shift) & 0xFFu;
+}
+
+// The lanes of the warp whose d (a digit, or 256 for "no key") equals this
+// lane's: one ballot per bit of d, each lane keeping the lanes that agree with
+// it on that bit. Nine ballots and a few logic operations per key, against one
+// warp match instruction, whose issue cost bounded the digit passes.
+__device__ __forceinline__ unsigned rs_peers(uint32_t d) {
+#if DBBC_RS_MATCH
+  return __match_any_sync(kFullMask, d);
+#else
+  unsigned peers = kFullMask;
+#pragma unroll
+  for (int b = 0; b < 9; b++) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned bal = __ballot_sync(kFullMask, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+#endif
 }
 
 // Per-tile digit counts, digit-major: hist[d * ntiles + tile]. Every thread
@@ -144,7 +166,7 @@ __global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* __restr
 #pragma unroll
   for (int j = 0; j < kRsItems; j++) {
     const uint32_t d = base + j * kRsThreads < n ? rs_digit(key[j], shift) : 256u;
-    const unsigned peers = __match_any_sync(kFullMask, d);
+    const unsigned peers = rs_peers(d);
     if (d < 256u && (int)lane_id() == 31 - __clz(peers)) h[w][d] += __popc(peers);
     __syncwarp();
   }
@@ -196,7 +218,7 @@ __global__ void __launch_bounds__(kRsThreads) radix_scatter_kernel(const K* __re
 #pragma unroll
   for (int j = 0; j < kRsItems; j++) {
     const uint32_t d = wbase + j * 32 + lane < n ? rs_digit(key[j], shift) : 256u;
-    peers[j] = __match_any_sync(kFullMask, d);
+    peers[j] = rs_peers(d);
   }
   // rank within the warp, item by item in input order
   const unsigned lt_mask = (1u << lane) - 1u;
