@@ -1,5 +1,5 @@
 // In-repo device primitives: exclusive scan and a stable LSD radix sort
-// (8-bit digits, per-tile histograms, warp-match ranking, shared-memory staging
+// (8-bit digits, per-tile histograms, warp-ballot ranking, shared-memory staging
 // so that the scatter writes whole digit runs). Written for sm_103a; no CUB.
 #pragma once
 
@@ -129,8 +129,10 @@ __device__ __forceinline__ uint32_t rs_digit(K key, int shift) {
 
 // The lanes of the warp whose d (a digit, or 256 for "no key") equals this
 // lane's: one ballot per bit of d, each lane keeping the lanes that agree with
-// it on that bit. Nine ballots and a few logic operations per key, against one
-// warp match instruction, whose issue cost bounded the digit passes.
+// it on that bit. Nine ballots and a few logic operations per key run the
+// digit passes faster than one warp match instruction per key (the Chung-Lu
+// 1M x 200k x 20M build: 4.08 -> 3.70 ms). DBBC_RS_MATCH=1 builds the match
+// form.
 __device__ __forceinline__ unsigned rs_peers(uint32_t d) {
 #if DBBC_RS_MATCH
   return __match_any_sync(kFullMask, d);
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(kRsThreads) radix_hist_kernel(const K* __restr
 
 // One digit pass of the stable sort. A tile's keys (and values) are loaded
 // first, all kRsItems per thread in flight together; each warp then ranks its
-// 256 keys in input order (warp match per key, per-warp digit counters), the
+// 256 keys in input order (digit peers per key, per-warp digit counters), the
 // block turns the per-warp counts into tile positions, the tile is staged in
 // shared memory in digit order, and written out as whole digit runs at the
 // offsets of the scanned digit-major histogram.
