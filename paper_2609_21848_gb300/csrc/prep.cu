@@ -260,9 +260,9 @@ __global__ void lower_kernel(const int64_t* __restrict__ row_ptr, const uint32_t
 // upos[k] (row u, index idx_u); rows ascend by rank, so idx_v entries of
 // row(v) rank below u and idx_u entries of row(u) rank below v. A lower
 // neighbour v of u (idx_u < lower[u]) thus adds idx_v to work[u], and a lower
-// neighbour u of v (idx_v < lower[v]) adds idx_u to work[v]. One thread per
-// edge, in V order: the V rows' sums are merged by a segmented warp sum, the
-// U rows' go to their rows directly.
+// neighbour u of v (idx_v < lower[v]) adds idx_u to work[v]. Edges are taken
+// in V order, 32 consecutive ones per warp: the V rows' sums are merged by a
+// segmented warp sum, the U rows' go to their rows directly.
 __global__ void work_kernel(CsrKeys ck, const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ lower,
                             unsigned long long* __restrict__ work) {
   constexpr int kRound = 4;  // edges per thread per round, their loads in flight together
