@@ -120,7 +120,7 @@ constexpr int kRsWarps = kRsThreads / 32;
 #define DBBC_RS_MATCH 0
 #endif
 constexpr int kRsItems = DBBC_RS_ITEMS;         // keys per thread
-constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 keys per tile
+constexpr int kRsTile = kRsThreads * kRsItems;  // keys per tile (2048 by default)
 
 template <typename K>
 __device__ __forceinline__ uint32_t rs_digit(K key, int shift) {
